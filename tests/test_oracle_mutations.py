@@ -1,0 +1,53 @@
+"""Pin strength: plant plausible mistakes in a copy of the oracle (on the CPU)
+and check that the pins in test_oracle_pins.py catch every one of them."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "dropped two-body term of a single replacement":
+        ("if (((J >> K) & 1ULL) && K != p) v += va_so(n, eri, m, K, p, K);", ""),
+    "creators of a double replacement in the wrong order":
+        ("s *= op_cre(&t, o);\n    s *= op_cre(&t, m);", "s *= op_cre(&t, m);\n    s *= op_cre(&t, o);"),
+    "transposed integral index (pq|rs) for <pq|rs>":
+        ("return eri[(((size_t)p * n + r) * n + q) * n + s];",
+         "return eri[(((size_t)p * n + q) * n + r) * n + s];"),
+    "missing 1/2 on the diagonal two-body sum":
+        ("e += 0.5 * va_so(n, eri, P, Q, P, Q);", "e += 1.0 * va_so(n, eri, P, Q, P, Q);"),
+    "phase counts the orbital itself":
+        ("for (int Q = 0; Q < P; ++Q) c += (int)((d >> Q) & 1ULL);",
+         "for (int Q = 0; Q <= P; ++Q) c += (int)((d >> Q) & 1ULL);"),
+    "2-RDM with r and s exchanged":
+        ("s *= op_ann(&d, s_ + tg * n);\n                  if (!s) continue;\n                  s *= op_cre(&d, r + tg * n);",
+         "s *= op_ann(&d, r + tg * n);\n                  if (!s) continue;\n                  s *= op_cre(&d, s_ + tg * n);"),
+    "wrong sign of the one-body single element":
+        ("double v = h_so(n, h, m, p);", "double v = -h_so(n, h, m, p);"),
+    "exchange integral added instead of subtracted":
+        ("return v_so(n, eri, P, Q, R, S) - v_so(n, eri, P, Q, S, R);",
+         "return v_so(n, eri, P, Q, R, S) + v_so(n, eri, P, Q, S, R);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    src = open(os.path.join(ROOT, "oracle", "oracle_core.c")).read()
+    old, new = MUTATIONS[name]
+    assert old in src, "mutation anchor no longer present in oracle_core.c"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "__pycache__"))
+    (tmp_path / "oracle" / "oracle_core.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "synth_inputs.py"), tmp_path)
+    os.makedirs(tmp_path / "tests")
+    for f in ("conftest.py", "fock_ref.py", "test_oracle_pins.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=tmp_path, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"planted mistake not caught: {name}\n{r.stdout[-2000:]}"

@@ -1,0 +1,224 @@
+"""Pins of the CPU oracle against facts it does not compute itself.
+
+Each test names the passage or mathematical fact it rests on.  None of them
+retypes the oracle's own formulas: the Hamiltonian is rebuilt from sparse
+Fock-space operator products (tests/fock_ref.py), the string tables are checked
+through the gl(n) commutation relations, and the solvers against closed forms.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth_inputs as si
+import fock_ref
+
+
+# ---------------------------------------------------------------- strings
+@pytest.mark.parametrize("n,k", [(1, 0), (1, 1), (4, 2), (6, 3), (8, 4), (10, 3), (14, 7)])
+def test_strings_are_all_combinations_in_ascending_order(n, k):
+    # Sec. II.A.1: every string gets a gap-free index; our ordering is ascending mask value.
+    want = sorted(sum(1 << i for i in c) for c in itertools.combinations(range(n), k))
+    got = oracle.strings(n, k)
+    assert len(got) == math.comb(n, k)
+    assert list(map(int, got)) == want
+
+
+def _table_matrices(n, k):
+    J, s = oracle.single_table(n, k)
+    N = J.shape[0]
+    E = np.zeros((n, n, N, N))
+    for I in range(N):
+        for p in range(n):
+            for q in range(n):
+                if J[I, p, q] >= 0:
+                    E[p, q, J[I, p, q], I] = s[I, p, q]
+    return E
+
+
+@pytest.mark.parametrize("n,k", [(4, 2), (5, 2), (6, 3), (5, 4)])
+def test_single_table_obeys_gl_n_commutators(n, k):
+    # a+_p a_q of one spin satisfy [E_pq, E_rs] = d_qr E_ps - d_ps E_rq,
+    # E_pq^T = E_qp and E_pp = occupation.  A wrong phase or index breaks these.
+    E = _table_matrices(n, k)
+    for p, q, r, s in itertools.product(range(n), repeat=4):
+        lhs = E[p, q] @ E[r, s] - E[r, s] @ E[p, q]
+        rhs = (q == r) * E[p, s] - (p == s) * E[r, q]
+        assert np.array_equal(lhs, rhs), (p, q, r, s)
+    for p, q in itertools.product(range(n), repeat=2):
+        assert np.array_equal(E[p, q].T, E[q, p])
+    strs = oracle.strings(n, k)
+    for p in range(n):
+        assert np.array_equal(np.diag(E[p, p]), (strs >> p) & 1)
+
+
+def test_single_table_matches_fock_space_operators():
+    n, k = 5, 2
+    _, a = fock_ref.excitation_ops(n)
+    idx = fock_ref.sector_states(n, k, 0)  # alpha strings only (beta empty)
+    E = _table_matrices(n, k)
+    for p, q in itertools.product(range(n), repeat=2):
+        M = (a[p].T @ a[q])[idx][:, idx].toarray()
+        assert np.array_equal(M, E[p, q])
+
+
+# ---------------------------------------------------------------- Hamiltonian
+CASES = [(2, 1, 1), (3, 1, 1), (3, 2, 1), (4, 2, 2), (4, 3, 1), (4, 1, 0), (5, 2, 3)]
+
+
+@pytest.mark.parametrize("n,na,nb", CASES)
+def test_hamiltonian_equals_operator_form(n, na, nb):
+    # Eq. 1 (V = 0) written with spin-free generators: the oracle's Slater-Condon
+    # matrix must equal the operator-product matrix element by element.
+    h, eri = si.integrals(n, 2 * n, seed=11 + n + 7 * na + 3 * nb)
+    H_sc = oracle.hmat_dense(n, na, nb, h, eri)
+    H_op = fock_ref.sector_matrix(n, na, nb, h, eri)
+    assert np.abs(H_sc - H_op).max() < 1e-13
+
+
+def test_hamiltonian_is_symmetric():
+    h, eri = si.integrals(6, 12, seed=5)
+    H = oracle.hmat_dense(6, 3, 3, h, eri)
+    assert np.abs(H - H.T).max() < 1e-14
+
+
+@pytest.mark.parametrize("t,U", [(1.0, 4.0), (0.5, 1.0), (1.0, 0.0), (0.3, 8.0)])
+def test_hubbard_dimer_closed_form(t, U):
+    # Two-site Hubbard model at half filling: E0 = (U - sqrt(U^2 + 16 t^2)) / 2.
+    h, eri = si.hubbard_ring(2, t, U)
+    w, _ = oracle.solve_dense(2, 1, 1, h, eri, nroots=1)
+    assert abs(w[0] - (U - math.sqrt(U * U + 16 * t * t)) / 2) < 1e-14
+
+
+@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (6, 2, 3), (7, 3, 2)])
+def test_noninteracting_limit(n, na, nb):
+    # g = 0: ground energy = sum of the lowest na + lowest nb eigenvalues of h.
+    h, _ = si.integrals(n, 2, seed=3)
+    eri = np.zeros((n,) * 4)
+    eps = np.linalg.eigvalsh(h)
+    w, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=1)
+    assert abs(w[0] - (eps[:na].sum() + eps[:nb].sum())) < 1e-12
+
+
+@pytest.mark.parametrize("nsites", [4, 6])
+def test_hubbard_ring_matches_fock_space_diagonalisation(nsites):
+    h, eri = si.hubbard_ring(nsites, 1.0, 4.0)
+    k = nsites // 2
+    w_or, _ = oracle.solve_dense(nsites, k, k, h, eri, nroots=6)
+    H_op = fock_ref.sector_matrix(nsites, k, k, h, eri)
+    w_op = np.linalg.eigvalsh(H_op)[:6]
+    assert np.abs(w_or - w_op).max() < 1e-12
+
+
+def test_energy_invariant_under_orbital_rotation():
+    # Full CI in the active space is invariant under orthogonal orbital rotations.
+    n, na, nb = 6, 3, 3
+    h, eri = si.integrals(n, 12, seed=21)
+    Q = si.random_rotation(n, seed=4)
+    h2 = Q.T @ h @ Q
+    eri2 = np.einsum("pqrs,pa,qb,rc,sd->abcd", eri, Q, Q, Q, Q)
+    w1, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=3)
+    w2, _ = oracle.solve_dense(n, na, nb, h2, eri2, nroots=3)
+    assert np.abs(w1 - w2).max() < 1e-12
+
+
+# ---------------------------------------------------------------- sigma
+@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (5, 2, 3), (6, 1, 4)])
+def test_direct_sigma_equals_dense_product(n, na, nb):
+    h, eri = si.integrals(n, 2 * n, seed=8)
+    H = oracle.hmat_dense(n, na, nb, h, eri)
+    Na, Nb = math.comb(n, na), math.comb(n, nb)
+    C = si.random_vectors(3, Na, Nb, seed=2).reshape(3, -1)
+    S = oracle.sigma(n, na, nb, h, eri, C)
+    assert np.abs(S - C @ H.T).max() < 1e-13
+    rows = np.array([0, Na * Nb - 1, 7 % (Na * Nb), (Na * Nb) // 2])
+    Sr = oracle.sigma(n, na, nb, h, eri, C, rows=rows)
+    assert np.abs(Sr - S[:, rows]).max() < 1e-14
+
+
+# ---------------------------------------------------------------- Davidson
+def test_davidson_matches_dense_cas88():
+    cfg = si.CAS88
+    h, eri = si.integrals(cfg["norb"], cfg["n_l"], cfg["seed"])
+    w_d, V_d = oracle.solve_dense(8, 4, 4, h, eri, nroots=3)
+    w, V, rn, it = oracle.davidson(8, 4, 4, h, eri, nroots=3, tol=1e-10)
+    assert np.all(rn < 1e-10)
+    assert np.abs(w - w_d).max() < 1e-11
+    for k in range(3):
+        assert abs(abs(V[k] @ V_d[k]) - 1.0) < 1e-10
+
+
+# ---------------------------------------------------------------- RDMs
+def _ground(n, na, nb, seed, nroots=1):
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w, V = oracle.solve_dense(n, na, nb, h, eri, nroots=nroots)
+    return h, eri, w, V
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (4, 2, 1), (5, 3, 2)])
+def test_rdms_match_fock_space_expectations(n, na, nb):
+    h, eri, w, V = _ground(n, na, nb, seed=31)
+    g1, g2 = oracle.rdm12(n, na, nb, V[0])
+    f1, f2 = fock_ref.rdms(n, na, nb, V[0])
+    assert np.abs(g1 - f1).max() < 1e-13
+    assert np.abs(g2 - f2).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (6, 2, 3)])
+def test_rdm_invariants(n, na, nb):
+    h, eri, w, V = _ground(n, na, nb, seed=41)
+    N = na + nb
+    g1, g2 = oracle.rdm12(n, na, nb, V[0])
+    assert abs(np.trace(g1) - N) < 1e-12
+    assert abs(np.einsum("pprr->", g2) - N * (N - 1)) < 1e-11
+    assert np.abs(np.einsum("pqrr->pq", g2) - (N - 1) * g1).max() < 1e-12
+    # Energy from the RDMs (the Lagrangian's CI part in Sec. II.B)
+    E = np.einsum("pq,pq->", h, g1) + 0.5 * np.einsum("pqrs,pqrs->", eri, g2)
+    assert abs(E - w[0]) < 1e-12
+    # Hermiticity / particle exchange
+    assert np.abs(g1 - g1.T).max() < 1e-13
+    assert np.abs(g2 - g2.transpose(2, 3, 0, 1)).max() < 1e-13
+    assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-13
+
+
+def _s2_from_rdms(g1, g2, N):
+    # <S^2> = -1/2 sum_pq Gamma_pqqp + N (4 - N) / 4 for spin-free RDMs.
+    return -0.5 * np.einsum("pqqp->", g2) + N * (4 - N) / 4.0
+
+
+@pytest.mark.parametrize("n,na,nb", [(4, 2, 2), (5, 3, 2)])
+def test_s2_from_rdms_matches_spin_operators(n, na, nb):
+    h, eri, w, V = _ground(n, na, nb, seed=51, nroots=3)
+    for k in range(3):
+        g1, g2 = oracle.rdm12(n, na, nb, V[k])
+        assert abs(_s2_from_rdms(g1, g2, na + nb) - fock_ref.s2_expectation(n, na, nb, V[k])) < 1e-12
+
+
+def test_dimer_ground_state_is_singlet():
+    h, eri = si.hubbard_ring(2, 1.0, 4.0)
+    w, V = oracle.solve_dense(2, 1, 1, h, eri, nroots=1)
+    g1, g2 = oracle.rdm12(2, 1, 1, V[0])
+    assert abs(_s2_from_rdms(g1, g2, 2)) < 1e-13
+
+
+def test_rdm2_elements_agree_with_full_rdm():
+    n, na, nb = 6, 3, 3
+    h, eri, w, V = _ground(n, na, nb, seed=61)
+    _, g2 = oracle.rdm12(n, na, nb, V[0], one=False)
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, n, size=(40, 4))
+    got = oracle.rdm2_elements(n, na, nb, V[0], idx)
+    assert np.abs(got - g2[tuple(idx.T)]).max() < 1e-14
+
+
+def test_transition_rdm_matches_fock_space():
+    # One-body transition density matrix <Psi_a| a+_x a_u |Psi_b> (Sec. II.A.1).
+    n, na, nb = 4, 2, 2
+    h, eri, w, V = _ground(n, na, nb, seed=71, nroots=2)
+    t1, _ = oracle.rdm12(n, na, nb, V[0], V[1], two=False)
+    E, _ = fock_ref.excitation_ops(n)
+    bra, ket = fock_ref.embed(n, na, nb, V[0]), fock_ref.embed(n, na, nb, V[1])
+    want = np.array([[bra @ (E[p][q] @ ket) for q in range(n)] for p in range(n)])
+    assert np.abs(t1 - want).max() < 1e-13
