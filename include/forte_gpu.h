@@ -1,0 +1,151 @@
+/*
+ * forte_gpu.h -- C ABI of the GB300 CASCI engine: string-driven sigma build,
+ * Davidson-Liu eigensolver and spin-free 1-/2-RDMs for a complete active space.
+ *
+ * The problem statement follows arXiv 2405.10197 (Forte):
+ *   - Hamiltonian, Eq. 1 (Sec. II), with the scalar V omitted.  Integrals are
+ *     passed in chemist notation (pq|rs) = <pr|qs> (Sec. III "Integral
+ *     classes"), so H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs)(E_pq E_rs -
+ *     d_qr E_ps) with E_pq = sum_spin a+_p a_q.
+ *   - Determinants are alpha string x beta string and the CI vector is the
+ *     matrix C[I_alpha][I_beta] (Sec. II.A.1, string-based CI of Handy).
+ *   - Strings are n-bit occupation masks (the Determinant class bit layout,
+ *     Sec. III), numbered in ascending mask order, so the address of a string
+ *     is its colexicographic rank.
+ *   - Davidson-Liu diagonalisation (Sec. II.A.1) and the spin-free 1- and
+ *     2-RDMs built from the spinful ones of Eqs. (gamma_1), (gamma_2).
+ *
+ * Conventions for every entry point:
+ *   - Return value: FORTE_OK (0) or one of the FORTE_ERR_* codes; the reason
+ *     is kept in a thread-local string read by forte_last_error().
+ *   - "device" pointers are CUDA global-memory addresses on the context's
+ *     device; the caller owns them and they must stay valid until the work
+ *     queued on the context's stream has finished.  "host" pointers are plain
+ *     CPU memory, read or written before the call returns.
+ *   - All vectors are FP64, row-major [nvec][N_alpha][N_beta].
+ *   - Work is queued on the context's stream (forte_set_stream; default: the
+ *     legacy default stream).  Calls that return host data synchronise it.
+ *   - No call traps the GPU; every device-side wait is bounded.
+ */
+#ifndef FORTE_GPU_H
+#define FORTE_GPU_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct forte_ctx forte_ctx;
+
+enum {
+  FORTE_OK = 0,
+  FORTE_ERR_ARG = 1,           /* invalid argument (size, pointer, mode) */
+  FORTE_ERR_ALLOC = 2,         /* device or host allocation failed */
+  FORTE_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  FORTE_ERR_NOT_CONVERGED = 4, /* Davidson hit max_iter; best estimates kept */
+  FORTE_ERR_NUMERIC = 5,       /* NaN/Inf in inputs or in residual norms */
+  FORTE_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
+};
+
+/* Arithmetic of the sigma build (forte_set_precision). */
+enum {
+  FORTE_FP64 = 0,   /* every term in FP64 */
+  FORTE_TF32 = 1,   /* alpha-beta GEMM in TF32 on the tensor cores, FP32 accumulate;
+                       same-spin terms in FP32; Davidson vectors FP64 */
+  FORTE_BF16X2 = 2  /* alpha-beta GEMM with split hi+lo BF16 operands
+                       (hi*hi + hi*lo + lo*hi), FP32 accumulate; same-spin FP32 */
+};
+
+/* Build a CAS problem: string lists (a1), signed single-replacement tables
+ * (a2), the same-spin string Hamiltonians (a3) and the determinant diagonal
+ * H_II (a4).
+ *   norb   number of active orbitals n, 1 <= n <= 16
+ *   nalpha, nbeta  electron counts, 0 <= n_sigma <= n
+ *   h      host [n][n] row-major one-electron integrals, symmetric
+ *   eri    host [n][n][n][n] row-major chemist-notation (pq|rs) with the
+ *          8-fold permutational symmetry of real orbitals
+ * The inputs are copied; the caller keeps ownership.  Returns NULL on error
+ * (bad sizes, NULL pointers, NaN/Inf, integrals not symmetric to 1e-12,
+ * allocation or CUDA failure); forte_last_error() tells why.  The context
+ * uses the current CUDA device at the time of the call. */
+forte_ctx *forte_cas_create(int norb, int nalpha, int nbeta, const double *h, const double *eri);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void forte_destroy(forte_ctx *ctx);
+
+/* Thread-local description of the last error ("" when none). */
+const char *forte_last_error(void);
+
+/* Queue subsequent work on this CUDA stream (a cudaStream_t; NULL = legacy
+ * default stream). */
+int forte_set_stream(forte_ctx *ctx, void *cuda_stream);
+
+/* Select FORTE_FP64, FORTE_TF32 or FORTE_BF16X2 for forte_sigma and for the
+ * inner iterations of forte_davidson.  Default FORTE_FP64. */
+int forte_set_precision(forte_ctx *ctx, int mode);
+
+/* N_alpha = C(n, nalpha), N_beta = C(n, nbeta) (host outputs, either may be NULL). */
+int forte_get_sizes(const forte_ctx *ctx, long long *n_alpha_str, long long *n_beta_str);
+
+/* Dense single-replacement table of one spin (0 = alpha, 1 = beta), host outputs:
+ *   strings [N]        occupation masks, ascending (address = index)
+ *   J       [N][n][n]  address of E_pq|I> (a+_p a_q on string I), -1 if it vanishes
+ *   sgn     [N][n][n]  its phase (+1/-1), 0 if it vanishes
+ * Any output may be NULL.  Phase: (-1)^(occupied orbitals strictly between p and q). */
+int forte_get_string_tables(const forte_ctx *ctx, int spin, unsigned *strings, int *J,
+                            signed char *sgn);
+
+/* Determinant diagonal <I|H|I>, device output [N_alpha][N_beta]. */
+int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
+
+/* sigma = H C (Eq. 1 applied in the determinant basis), the hot step a5 + a6.
+ *   C  device [nvec][N_alpha][N_beta] FP64 input
+ *   S  device [nvec][N_alpha][N_beta] FP64 output, overwritten (not accumulated);
+ *      must not overlap C
+ *   nvec >= 0 (0 is a no-op)
+ * In FORTE_TF32 / FORTE_BF16X2 mode the result carries the reduced precision
+ * of that mode.  Asynchronous on the context stream. */
+int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
+
+/* Davidson-Liu solve for the nroots lowest eigenpairs of H in the determinant
+ * space (any total spin), to max_k ||H x_k - theta_k x_k||_2 < tol.
+ * Guess: unit vectors at the lowest H_II (ties: lowest index); preconditioner
+ * (theta - H_II)^-1 with |denominator| clamped to denom_guard; classical
+ * Gram-Schmidt applied twice; subspace collapse (forte_set_davidson_params).
+ * In a mixed mode the inner iterations use that mode's sigma and the final
+ * residuals and energies are refined with FP64 sigma builds until the FP64
+ * residual meets tol.  Results stay in the context (forte_get_roots).
+ * Returns FORTE_ERR_NOT_CONVERGED when max_iter is reached (results kept). */
+int forte_davidson(forte_ctx *ctx, int nroots, double tol);
+
+/* Davidson controls: subspace size and collapse size per root, iteration cap
+ * and preconditioner guard.  Defaults 12, 2, 200, 1e-8. */
+int forte_set_davidson_params(forte_ctx *ctx, int max_subspace_per_root, int collapse_per_root,
+                              int max_iter, double denom_guard);
+
+/* Results of the last forte_davidson: energies (host [nroots], may be NULL),
+ * eigenvectors (device [nroots][N_alpha][N_beta], may be NULL; normalised,
+ * largest-|c| component positive), final FP64 residual norms (host
+ * [nroots], may be NULL) and the iteration count (host, may be NULL). */
+int forte_get_roots(const forte_ctx *ctx, double *E, double *C, double *rnorm, int *iters);
+
+/* Restart: use the nvec device vectors [nvec][N_alpha][N_beta] as the initial
+ * Davidson subspace of the next forte_davidson call (copied; orthonormalised
+ * there).  nvec = 0 restores the unit-vector guess. */
+int forte_set_guess(forte_ctx *ctx, const double *C, int nvec);
+
+/* Spin-free RDMs of one normalised state C (device [N_alpha][N_beta]):
+ *   g1 device [n][n]        gamma_pq = sum_s <C|a+_ps a_qs|C>
+ *   g2 device [n][n][n][n]  Gamma_pqrs = sum_st <C|a+_ps a+_rt a_st a_qs|C>
+ *                           = <E_pq E_rs> - d_qr <E_ps>  (chemist order)
+ * Either output may be NULL.  Definitions: Sec. II.A.1, Eqs. (gamma_1),
+ * (gamma_2), summed over spin.  FP64. */
+int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2);
+
+/* One-body transition density matrix between two states (Sec. II.A.1):
+ *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
+int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FORTE_GPU_H */

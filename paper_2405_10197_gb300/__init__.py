@@ -1,0 +1,276 @@
+"""Python binding of libforte_gpu.so, the GB300 CASCI engine.
+
+The functions below carry the names of the C ABI in include/forte_gpu.h and
+only marshal arguments (torch tensors or integer addresses to pointers, status
+codes to exceptions).  Every step of the computation runs in the library's
+CUDA kernels; there is no CPU fallback: if the shared library is missing this
+module raises on first use.
+
+``CASProblem`` is a small convenience wrapper that allocates the outputs with
+torch (device memory only) and calls the same entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libforte_gpu.so")
+
+FORTE_OK = 0
+FORTE_ERR_ARG = 1
+FORTE_ERR_ALLOC = 2
+FORTE_ERR_CUDA = 3
+FORTE_ERR_NOT_CONVERGED = 4
+FORTE_ERR_NUMERIC = 5
+FORTE_ERR_TIMEOUT = 6
+
+FORTE_FP64 = 0
+FORTE_TF32 = 1
+FORTE_BF16X2 = 2
+
+_ERRNAMES = {1: "FORTE_ERR_ARG", 2: "FORTE_ERR_ALLOC", 3: "FORTE_ERR_CUDA",
+             4: "FORTE_ERR_NOT_CONVERGED", 5: "FORTE_ERR_NUMERIC", 6: "FORTE_ERR_TIMEOUT"}
+
+
+class ForteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library():
+    """Load libforte_gpu.so (built by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(the CUDA library is required; there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    L.forte_cas_create.restype = vp
+    L.forte_cas_create.argtypes = [i, i, i, vp, vp]
+    L.forte_destroy.restype = None
+    L.forte_destroy.argtypes = [vp]
+    L.forte_last_error.restype = ctypes.c_char_p
+    L.forte_last_error.argtypes = []
+    sigs = {
+        "forte_set_stream": [vp, vp],
+        "forte_set_precision": [vp, i],
+        "forte_get_sizes": [vp, vp, vp],
+        "forte_get_string_tables": [vp, i, vp, vp, vp],
+        "forte_get_hdiag": [vp, vp],
+        "forte_sigma": [vp, vp, vp, i],
+        "forte_davidson": [vp, i, d],
+        "forte_set_davidson_params": [vp, i, i, i, d],
+        "forte_get_roots": [vp, vp, vp, vp, vp],
+        "forte_set_guess": [vp, vp, i],
+        "forte_rdms": [vp, vp, vp, vp],
+        "forte_tdm1": [vp, vp, vp, vp],
+    }
+    for name, args in sigs.items():
+        f = getattr(L, name)
+        f.restype = i
+        f.argtypes = args
+    _ = ll
+    _lib = L
+    return L
+
+
+def _check(code, allow=()):
+    if code != FORTE_OK and code not in allow:
+        raise ForteError(code, forte_last_error())
+    return code
+
+
+def _ptr(x, numel=None, dtype="float64"):
+    """Device pointer of a torch tensor (dtype/contiguity/size checked) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    want = {"float64": torch.float64}[dtype]
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch tensor or an integer device address")
+    if x.dtype != want or not x.is_cuda or not x.is_contiguous():
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor, got {x.dtype} on {x.device}")
+    if numel is not None and x.numel() < numel:
+        raise ValueError(f"tensor has {x.numel()} elements, need {numel}")
+    return x.data_ptr()
+
+
+def _host_f64(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+# --------------------------------------------------------------- C ABI names
+
+def forte_last_error() -> str:
+    return library().forte_last_error().decode()
+
+
+def forte_cas_create(norb, nalpha, nbeta, h, eri):
+    """Return an opaque context handle (int).  h, eri: host arrays."""
+    h = _host_f64(h, (norb, norb))
+    eri = _host_f64(eri, (norb,) * 4)
+    ctx = library().forte_cas_create(norb, nalpha, nbeta, h.ctypes.data, eri.ctypes.data)
+    if not ctx:
+        raise ForteError(FORTE_ERR_ARG, forte_last_error())
+    return ctx
+
+
+def forte_destroy(ctx):
+    library().forte_destroy(ctx)
+
+
+def forte_set_stream(ctx, stream):
+    """stream: a torch.cuda.Stream, an integer cudaStream_t, or None (legacy default)."""
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(library().forte_set_stream(ctx, s))
+
+
+def forte_set_precision(ctx, mode):
+    return _check(library().forte_set_precision(ctx, int(mode)))
+
+
+def forte_get_sizes(ctx):
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(library().forte_get_sizes(ctx, ctypes.addressof(a), ctypes.addressof(b)))
+    return a.value, b.value
+
+
+def forte_get_string_tables(ctx, spin, norb):
+    na, nb = forte_get_sizes(ctx)
+    N = na if spin == 0 else nb
+    s = np.zeros(N, dtype=np.uint32)
+    J = np.zeros((N, norb, norb), dtype=np.int32)
+    g = np.zeros((N, norb, norb), dtype=np.int8)
+    _check(library().forte_get_string_tables(ctx, spin, s.ctypes.data, J.ctypes.data, g.ctypes.data))
+    return s, J, g
+
+
+def forte_get_hdiag(ctx, out):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_get_hdiag(ctx, _ptr(out, na * nb)))
+
+
+def forte_sigma(ctx, C, S, nvec):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_sigma(ctx, _ptr(C, nvec * na * nb), _ptr(S, nvec * na * nb), int(nvec)))
+
+
+def forte_davidson(ctx, nroots, tol, allow_not_converged=False):
+    allow = (FORTE_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+    return _check(library().forte_davidson(ctx, int(nroots), float(tol)), allow)
+
+
+def forte_set_davidson_params(ctx, max_subspace_per_root, collapse_per_root, max_iter, denom_guard):
+    return _check(library().forte_set_davidson_params(ctx, int(max_subspace_per_root),
+                                                      int(collapse_per_root), int(max_iter),
+                                                      float(denom_guard)))
+
+
+def forte_get_roots(ctx, nroots, C=None):
+    """Returns (E, rnorm, iters); copies eigenvectors into the device tensor C if given."""
+    na, nb = forte_get_sizes(ctx)
+    E = np.zeros(nroots)
+    rn = np.zeros(nroots)
+    it = ctypes.c_int()
+    _check(library().forte_get_roots(ctx, E.ctypes.data, _ptr(C, nroots * na * nb), rn.ctypes.data,
+                                     ctypes.addressof(it)))
+    return E, rn, it.value
+
+
+def forte_set_guess(ctx, C, nvec):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_set_guess(ctx, _ptr(C, nvec * na * nb) if nvec else None, int(nvec)))
+
+
+def forte_rdms(ctx, C, g1, g2, norb):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_rdms(ctx, _ptr(C, na * nb), _ptr(g1, norb * norb),
+                                       _ptr(g2, norb ** 4)))
+
+
+def forte_tdm1(ctx, bra, ket, t1, norb):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_tdm1(ctx, _ptr(bra, na * nb), _ptr(ket, na * nb),
+                                       _ptr(t1, norb * norb)))
+
+
+# --------------------------------------------------------------- convenience
+
+class CASProblem:
+    """One active-space problem on the current CUDA device."""
+
+    def __init__(self, norb, nalpha, nbeta, h, eri, precision=FORTE_FP64, stream=None):
+        import torch
+        self.norb, self.nalpha, self.nbeta = norb, nalpha, nbeta
+        self.ctx = forte_cas_create(norb, nalpha, nbeta, h, eri)
+        self.na, self.nb = forte_get_sizes(self.ctx)
+        self.ndet = self.na * self.nb
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is not None:
+            forte_set_stream(self.ctx, stream)
+        forte_set_precision(self.ctx, precision)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            forte_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, mode):
+        forte_set_precision(self.ctx, mode)
+
+    def sigma(self, C):
+        import torch
+        C = C.reshape(-1, self.na, self.nb)
+        S = torch.empty_like(C)
+        forte_sigma(self.ctx, C, S, C.shape[0])
+        return S
+
+    def hdiag(self):
+        import torch
+        out = torch.empty(self.na, self.nb, dtype=torch.float64, device=self.device)
+        forte_get_hdiag(self.ctx, out)
+        return out
+
+    def davidson(self, nroots=1, tol=1e-10, allow_not_converged=False):
+        import torch
+        forte_davidson(self.ctx, nroots, tol, allow_not_converged)
+        C = torch.empty(nroots, self.na, self.nb, dtype=torch.float64, device=self.device)
+        E, rn, it = forte_get_roots(self.ctx, nroots, C)
+        return E, C, rn, it
+
+    def rdms(self, C):
+        import torch
+        g1 = torch.empty(self.norb, self.norb, dtype=torch.float64, device=self.device)
+        g2 = torch.empty((self.norb,) * 4, dtype=torch.float64, device=self.device)
+        forte_rdms(self.ctx, C.contiguous(), g1, g2, self.norb)
+        return g1, g2
+
+    def tdm1(self, bra, ket):
+        import torch
+        t1 = torch.empty(self.norb, self.norb, dtype=torch.float64, device=self.device)
+        forte_tdm1(self.ctx, bra.contiguous(), ket.contiguous(), t1, self.norb)
+        return t1
+
+    def string_tables(self, spin):
+        return forte_get_string_tables(self.ctx, spin, self.norb)

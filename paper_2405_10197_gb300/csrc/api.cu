@@ -1,0 +1,572 @@
+// C ABI entry points: context life cycle, sigma dispatch, the Davidson-Liu
+// driver (step a7, with the mixed-precision refinement of step a8) and the
+// RDM calls (a9).  Every long-vector operation runs in this library's
+// kernels; the host only solves the small subspace eigenproblem and decides
+// convergence.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "forte_internal.h"
+
+namespace forte {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+// Cyclic Jacobi eigensolver for a small symmetric matrix (Golub & Van Loan,
+// Sec. 8.5): A row-major k x k; w ascending; U[i*k + j] = component i of
+// eigenvector j.
+void sym_eig(int k, const double *A, double *w, double *U) {
+  std::vector<double> a(A, A + (size_t)k * k), v((size_t)k * k, 0.0);
+  for (int i = 0; i < k; ++i) v[(size_t)i * k + i] = 1.0;
+  double fro = 0.0;
+  for (double x : a) fro += x * x;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) off += a[(size_t)p * k + q] * a[(size_t)p * k + q];
+    if (off <= 1e-32 * fro || off == 0.0) break;
+    for (int p = 0; p < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        double apq = a[(size_t)p * k + q];
+        if (apq == 0.0) continue;
+        double tau = (a[(size_t)q * k + q] - a[(size_t)p * k + p]) / (2.0 * apq);
+        double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+        for (int r = 0; r < k; ++r) {
+          double arp = a[(size_t)r * k + p], arq = a[(size_t)r * k + q];
+          a[(size_t)r * k + p] = c * arp - s * arq;
+          a[(size_t)r * k + q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < k; ++r) {
+          double apr = a[(size_t)p * k + r], aqr = a[(size_t)q * k + r];
+          a[(size_t)p * k + r] = c * apr - s * aqr;
+          a[(size_t)q * k + r] = s * apr + c * aqr;
+        }
+        for (int r = 0; r < k; ++r) {
+          double vrp = v[(size_t)r * k + p], vrq = v[(size_t)r * k + q];
+          v[(size_t)r * k + p] = c * vrp - s * vrq;
+          v[(size_t)r * k + q] = s * vrp + c * vrq;
+        }
+      }
+  }
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](int x, int y) { return a[(size_t)x * k + x] < a[(size_t)y * k + y]; });
+  for (int j = 0; j < k; ++j) {
+    w[j] = a[(size_t)ord[j] * k + ord[j]];
+    for (int i = 0; i < k; ++i) U[(size_t)i * k + j] = v[(size_t)i * k + ord[j]];
+  }
+}
+
+static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
+  if (nvec <= 0) return FORTE_OK;
+  if (mode == FORTE_FP64) return sigma_fp64(ctx, C, S, nvec);
+  return sigma_mixed(ctx, C, S, nvec, mode);
+}
+
+// ----------------------------------------------------------------- Davidson
+
+struct DvResult {
+  std::vector<double> E, rn;
+  int iters = 0;
+  bool converged = false;
+};
+
+// Index of the largest |x| (ties: lowest index) and the sign of that entry.
+__global__ void k_absmax(const double *__restrict__ x, long long n, double *bval, long long *bidx) {
+  __shared__ double sv[256];
+  __shared__ long long si[256];
+  double best = -1.0;
+  long long bi = -1;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    double v = fabs(x[j]);
+    if (v > best) { best = v; bi = j; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double v2 = sv[threadIdx.x + s];
+      long long i2 = si[threadIdx.x + s];
+      if (i2 >= 0 && (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x]))) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { bval[blockIdx.x] = sv[0]; bidx[blockIdx.x] = si[0]; }
+}
+
+static int fix_sign(forte_ctx *ctx, double *x, long long n) {
+  const unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 512);
+  int rc = ctx->sc_small.ensure(sizeof(double) * nb * 2 + 64);
+  if (rc) return rc;
+  double *bv = (double *)ctx->sc_small.ptr;
+  long long *bi = (long long *)(bv + nb);
+  k_absmax<<<nb, 256, 0, ctx->stream>>>(x, n, bv, bi);
+  FORTE_LAUNCH_CHECK();
+  std::vector<double> hv(nb);
+  std::vector<long long> hi(nb);
+  FORTE_CUDA_TRY(cudaMemcpyAsync(hv.data(), bv, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  FORTE_CUDA_TRY(cudaMemcpyAsync(hi.data(), bi, sizeof(long long) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  double best = -1;
+  long long b = -1;
+  for (unsigned i = 0; i < nb; ++i)
+    if (hi[i] >= 0 && (hv[i] > best || (hv[i] == best && hi[i] < b))) { best = hv[i]; b = hi[i]; }
+  if (b < 0) return FORTE_OK;
+  double val;
+  FORTE_CUDA_TRY(cudaMemcpy(&val, x + b, sizeof(double), cudaMemcpyDeviceToHost));
+  if (val < 0) return vk_scale(ctx, x, x, -1.0, n);
+  return FORTE_OK;
+}
+
+// Davidson-Liu with the sigma of `mode`; all vector arithmetic FP64.
+// guess: ng device vectors (may be 0 -> unit vectors at the lowest H_II).
+// On return the Ritz vectors are in out_roots [nroots][N].
+static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const double *guess, int ng,
+                        int max_iter, double *out_roots, DvResult &res) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->Ndet;
+  int maxsub = std::max(ctx->dv_max_sub * nroots, nroots + 1);
+  maxsub = (int)std::min<long long>(maxsub, N);
+  maxsub = std::min(maxsub, 63);
+  if (maxsub < nroots) { set_error("subspace limit below nroots"); return FORTE_ERR_ARG; }
+  int keep = std::max(nroots, std::min(ctx->dv_collapse * nroots, maxsub - 1));
+  keep = std::min(keep, maxsub);
+  // device layout: B[maxsub], S[maxsub], T[nroots], W[keep] vectors; then small arrays
+  size_t nvecs = (size_t)maxsub * 2 + nroots + keep;
+  size_t small_off = sizeof(double) * nvecs * N;
+  size_t small_bytes = sizeof(double) * (64 * 64 + 4 * 64 + 64);
+  int rc = ctx->sc_dv.ensure(small_off + small_bytes + 256);
+  if (rc) return rc;
+  double *B = (double *)ctx->sc_dv.ptr;
+  double *S = B + (size_t)maxsub * N;
+  double *T = S + (size_t)maxsub * N;
+  double *W = T + (size_t)nroots * N;
+  double *d_coef = (double *)((char *)ctx->sc_dv.ptr + small_off);  // [64*64]
+  double *d_u = d_coef + 64 * 64;                                    // [64]
+  double *d_d0 = d_u + 64;                                           // [65]
+  double *d_d1 = d_d0 + 65;                                          // [65]
+  double *d_d2 = d_d1 + 65;                                          // [65]
+
+  int k = 0;
+  if (ng > 0) {
+    // orthonormalise the supplied vectors into B
+    std::vector<double> h_d(65);
+    for (int i = 0; i < ng && k < maxsub; ++i) {
+      const double *t = guess + (size_t)i * N;
+      FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
+      if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, B + (size_t)k * N, d_d0, N))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      double n0 = h_d[k];
+      if ((rc = vk_orth_update(ctx, B, k, N, d_d0, B + (size_t)k * N, B + (size_t)k * N, d_d1, N))) return rc;
+      if ((rc = vk_orth_update(ctx, B, k, N, d_d1, B + (size_t)k * N, B + (size_t)k * N, d_d2, N))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d2, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      double n2 = h_d[k];
+      if (!(n2 > 1e-20 * n0) || !(n2 > 0)) continue;
+      if ((rc = vk_scale(ctx, B + (size_t)k * N, B + (size_t)k * N, 1.0 / sqrt(n2), N))) return rc;
+      ++k;
+    }
+  }
+  if (k < nroots) {
+    // unit vectors at the lowest diagonal elements not already spanned
+    int need = nroots - k;
+    std::vector<long long> idx(nroots + ng + 1);
+    if ((rc = vk_argmin_k(ctx, ctx->d_hdiag, N, std::min<long long>(N, need + k), idx.data()))) return rc;
+    int used = 0;
+    for (size_t c = 0; c < idx.size() && used < need && c < (size_t)std::min<long long>(N, need + k); ++c) {
+      double *b = B + (size_t)k * N;
+      FORTE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * N, st));
+      double one = 1.0;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(b + idx[c], &one, sizeof(double), cudaMemcpyHostToDevice, st));
+      if (k > 0) {
+        // orthogonalise against the supplied guesses
+        std::vector<double> h_d(65);
+        if ((rc = vk_multidot(ctx, B, k, N, b, N, d_d0))) return rc;
+        if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N))) return rc;
+        if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N))) return rc;
+        FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d2, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+        FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+        if (!(h_d[k] > 1e-12)) continue;
+        if ((rc = vk_scale(ctx, b, b, 1.0 / sqrt(h_d[k]), N))) return rc;
+      }
+      ++k;
+      ++used;
+    }
+    if (k < nroots) { set_error("could not build %d guess vectors", nroots); return FORTE_ERR_ARG; }
+  }
+  // sigma of the initial basis and the subspace matrix G = B^T H B
+  std::vector<double> G((size_t)64 * 64, 0.0);
+  auto Gat = [&](int i, int j) -> double & { return G[(size_t)i * 64 + j]; };
+  if ((rc = sigma_dispatch(ctx, B, S, k, mode))) return rc;
+  std::vector<double> h_dots(65);
+  for (int j = 0; j < k; ++j) {
+    if ((rc = vk_multidot(ctx, B, k, N, S + (size_t)j * N, N, d_d0))) return rc;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(h_dots.data(), d_d0, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < k; ++i) Gat(i, j) = h_dots[i];
+  }
+  std::vector<double> Gk, w, U, coef;
+  res.E.assign(nroots, 0.0);
+  res.rn.assign(nroots, INFINITY);
+  res.converged = false;
+  for (int it = 1;; ++it) {
+    // Rayleigh-Ritz on the symmetrised subspace matrix
+    Gk.assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Gk[(size_t)i * k + j] = 0.5 * (Gat(i, j) + Gat(j, i));
+    w.assign(k, 0.0);
+    U.assign((size_t)k * k, 0.0);
+    sym_eig(k, Gk.data(), w.data(), U.data());
+    // residuals and preconditioned corrections
+    std::vector<double> rn2(nroots);
+    for (int r = 0; r < nroots; ++r) {
+      std::vector<double> u(k);
+      for (int i = 0; i < k; ++i) u[i] = U[(size_t)i * k + r];
+      FORTE_CUDA_TRY(cudaMemcpyAsync(d_u, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+      if ((rc = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, T + (size_t)r * N,
+                                    d_d0 + r, N)))
+        return rc;
+    }
+    FORTE_CUDA_TRY(cudaMemcpyAsync(rn2.data(), d_d0, sizeof(double) * nroots, cudaMemcpyDeviceToHost, st));
+    FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+    bool all = true, bad = false;
+    for (int r = 0; r < nroots; ++r) {
+      res.E[r] = w[r];
+      res.rn[r] = sqrt(std::max(0.0, rn2[r]));
+      if (!isfinite(rn2[r]) || !isfinite(w[r])) bad = true;
+      if (!(res.rn[r] < tol)) all = false;
+    }
+    res.iters = it;
+    if (bad) { set_error("non-finite residual or eigenvalue in Davidson"); return FORTE_ERR_NUMERIC; }
+    bool stop = all || it >= max_iter || k >= N;
+    if (stop) {
+      coef.assign((size_t)k * nroots, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
+      FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
+      if ((rc = vk_combine(ctx, B, k, N, d_coef, nroots, out_roots, N, N))) return rc;
+      res.converged = all || (k >= N);
+      return FORTE_OK;
+    }
+    int nnew_want = 0;
+    for (int r = 0; r < nroots; ++r) nnew_want += (res.rn[r] < tol) ? 0 : 1;
+    if (k + nnew_want > maxsub) {
+      // collapse onto the lowest `keep` Ritz vectors
+      coef.assign((size_t)k * keep, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int c = 0; c < keep; ++c) coef[(size_t)i * keep + c] = U[(size_t)i * k + c];
+      FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
+      if ((rc = vk_combine(ctx, B, k, N, d_coef, keep, W, N, N))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(B, W, sizeof(double) * keep * N, cudaMemcpyDeviceToDevice, st));
+      if ((rc = vk_combine(ctx, S, k, N, d_coef, keep, W, N, N))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(S, W, sizeof(double) * keep * N, cudaMemcpyDeviceToDevice, st));
+      std::fill(G.begin(), G.end(), 0.0);
+      for (int c = 0; c < keep; ++c) Gat(c, c) = w[c];
+      k = keep;
+    }
+    const int k_old = k;
+    for (int r = 0; r < nroots; ++r) {
+      if (res.rn[r] < tol) continue;
+      if (k >= maxsub) break;
+      double *t = T + (size_t)r * N;
+      double *b = B + (size_t)k * N;
+      std::vector<double> h_d(65);
+      FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
+      if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, b, d_d0, N))) return rc;     // copy + B^T t + |t|^2
+      if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N))) return rc;    // CGS pass 1
+      if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N))) return rc;    // CGS pass 2
+      std::vector<double> n0(1);
+      FORTE_CUDA_TRY(cudaMemcpyAsync(n0.data(), d_d0 + k, sizeof(double), cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d2, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      double nn = h_d[k];
+      if (!(nn > 1e-24 * n0[0]) || !(nn > 0.0)) continue;  // linearly dependent: drop
+      if ((rc = vk_scale(ctx, b, b, 1.0 / sqrt(nn), N))) return rc;
+      ++k;
+    }
+    if (k == k_old) {
+      // no new direction: report the current Ritz vectors
+      coef.assign((size_t)k * nroots, 0.0);
+      for (int i = 0; i < k; ++i)
+        for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
+      FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
+      if ((rc = vk_combine(ctx, B, k, N, d_coef, nroots, out_roots, N, N))) return rc;
+      return FORTE_OK;
+    }
+    if ((rc = sigma_dispatch(ctx, B + (size_t)k_old * N, S + (size_t)k_old * N, k - k_old, mode))) return rc;
+    for (int j = k_old; j < k; ++j) {
+      if ((rc = vk_multidot(ctx, B, k, N, S + (size_t)j * N, N, d_d0))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h_dots.data(), d_d0, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int i = 0; i < k; ++i) { Gat(i, j) = h_dots[i]; Gat(j, i) = h_dots[i]; }
+    }
+  }
+}
+
+}  // namespace forte
+
+using namespace forte;
+
+extern "C" {
+
+const char *forte_last_error(void) { return g_err; }
+
+static bool sym_ok(double a, double b) { return fabs(a - b) <= 1e-12 * std::max(1.0, fabs(a)); }
+
+forte_ctx *forte_cas_create(int norb, int nalpha, int nbeta, const double *h, const double *eri) {
+  clear_error();
+  if (norb < 1 || norb > 16 || nalpha < 0 || nalpha > norb || nbeta < 0 || nbeta > norb) {
+    set_error("invalid sizes: norb=%d nalpha=%d nbeta=%d (need 1<=norb<=16, 0<=n<=norb)", norb, nalpha, nbeta);
+    return nullptr;
+  }
+  if (!h || !eri) {
+    set_error("h and eri must be non-NULL host pointers");
+    return nullptr;
+  }
+  const int n = norb;
+  for (int i = 0; i < n * n; ++i)
+    if (!isfinite(h[i])) { set_error("h contains NaN/Inf"); return nullptr; }
+  for (long i = 0; i < (long)n * n * n * n; ++i)
+    if (!isfinite(eri[i])) { set_error("eri contains NaN/Inf"); return nullptr; }
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      if (!sym_ok(h[p * n + q], h[q * n + p])) { set_error("h is not symmetric at (%d,%d)", p, q); return nullptr; }
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q)
+      for (int r = 0; r < n; ++r)
+        for (int s = 0; s < n; ++s) {
+          double v = eri[(((size_t)p * n + q) * n + r) * n + s];
+          if (!sym_ok(v, eri[(((size_t)q * n + p) * n + r) * n + s]) ||
+              !sym_ok(v, eri[(((size_t)p * n + q) * n + s) * n + r]) ||
+              !sym_ok(v, eri[(((size_t)r * n + s) * n + p) * n + q])) {
+            set_error("eri lacks 8-fold symmetry at (%d,%d|%d,%d)", p, q, r, s);
+            return nullptr;
+          }
+        }
+  forte_ctx *ctx = new (std::nothrow) forte_ctx();
+  if (!ctx) { set_error("host allocation failed"); return nullptr; }
+  ctx->n = n; ctx->na = nalpha; ctx->nb = nbeta;
+  ctx->npair = n * (n + 1) / 2;
+  ctx->same_strings = (nalpha == nbeta);
+  ctx->h.assign(h, h + n * n);
+  ctx->eri.assign(eri, eri + (size_t)n * n * n * n);
+  if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+    set_error("no CUDA device available");
+    delete ctx;
+    return nullptr;
+  }
+  int rc = build_spin_tables(ctx);
+  if (!rc) {
+    ctx->Na = ctx->sh[0].N;
+    ctx->Nb = ctx->same_strings ? ctx->sh[0].N : ctx->sh[1].N;
+    ctx->Ndet = ctx->Na * ctx->Nb;
+    if (ctx->same_strings) ctx->sh[1] = ctx->sh[0];
+    rc = upload_tables(ctx);
+  }
+  if (!rc) rc = hdiag_build(ctx);
+  if (rc) {
+    std::string msg = g_err;
+    forte_destroy(ctx);
+    set_error("%s", msg.c_str());
+    return nullptr;
+  }
+  return ctx;
+}
+
+void forte_destroy(forte_ctx *ctx) {
+  if (!ctx) return;
+  int nsp = ctx->same_strings ? 1 : 2;
+  for (int s = 0; s < nsp; ++s) {
+    SpinDev &D = ctx->sd[s];
+    cudaFree(D.list); cudaFree(D.csr_ptr); cudaFree(D.csr_col); cudaFree(D.csr_val);
+    cudaFree(D.csr_val32); cudaFree(D.str); cudaFree(D.diag); cudaFree(D.dense);
+  }
+  cudaFree(ctx->d_gpair); cudaFree(ctx->d_gpair32); cudaFree(ctx->d_hdiag);
+  cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
+  ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
+  ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release();
+  delete ctx;
+}
+
+int forte_set_stream(forte_ctx *ctx, void *s) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  ctx->stream = (cudaStream_t)s;
+  return FORTE_OK;
+}
+
+int forte_set_precision(forte_ctx *ctx, int mode) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (mode != FORTE_FP64 && mode != FORTE_TF32 && mode != FORTE_BF16X2) {
+    set_error("unknown precision mode %d", mode);
+    return FORTE_ERR_ARG;
+  }
+  ctx->precision = mode;
+  return FORTE_OK;
+}
+
+int forte_get_sizes(const forte_ctx *ctx, long long *na, long long *nb) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (na) *na = ctx->Na;
+  if (nb) *nb = ctx->Nb;
+  return FORTE_OK;
+}
+
+int forte_get_string_tables(const forte_ctx *ctx, int spin, unsigned *strings, int *J, signed char *sgn) {
+  if (!ctx || (spin != 0 && spin != 1)) { set_error("bad context or spin"); return FORTE_ERR_ARG; }
+  const SpinHost &S = ctx->sh[spin];
+  const int n = ctx->n, n2 = n * n;
+  if (strings) for (long long i = 0; i < S.N; ++i) strings[i] = S.str[i];
+  if (J) for (long long i = 0; i < S.N * n2; ++i) J[i] = -1;
+  if (sgn) memset(sgn, 0, (size_t)S.N * n2);
+  for (long long I = 0; I < S.N; ++I)
+    for (int e = 0; e < S.nk; ++e) {
+      const Repl &r = S.list[(size_t)I * S.nk + e];
+      if (J) J[(size_t)I * n2 + r.pq] = r.J;
+      if (sgn) sgn[(size_t)I * n2 + r.pq] = r.sgn;
+    }
+  return FORTE_OK;
+}
+
+int forte_get_hdiag(const forte_ctx *ctx, double *hd) {
+  if (!ctx || !hd) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  FORTE_CUDA_TRY(cudaMemcpyAsync(hd, ctx->d_hdiag, sizeof(double) * ctx->Ndet, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  return FORTE_OK;
+}
+
+int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (nvec < 0) { set_error("nvec < 0"); return FORTE_ERR_ARG; }
+  if (nvec == 0) return FORTE_OK;
+  if (!C || !S) { set_error("C and S must be device pointers"); return FORTE_ERR_ARG; }
+  const char *c0 = (const char *)C, *c1 = c0 + sizeof(double) * ctx->Ndet * nvec;
+  const char *s0 = (const char *)S, *s1 = s0 + sizeof(double) * ctx->Ndet * nvec;
+  if (c0 < s1 && s0 < c1) { set_error("S overlaps C"); return FORTE_ERR_ARG; }
+  return sigma_dispatch(ctx, C, S, nvec, ctx->precision);
+}
+
+int forte_set_davidson_params(forte_ctx *ctx, int max_sub, int collapse, int max_iter, double guard) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (max_sub < 2 || collapse < 1 || collapse >= max_sub || max_iter < 1 || !(guard > 0)) {
+    set_error("invalid Davidson parameters");
+    return FORTE_ERR_ARG;
+  }
+  ctx->dv_max_sub = max_sub;
+  ctx->dv_collapse = collapse;
+  ctx->dv_max_iter = max_iter;
+  ctx->dv_guard = guard;
+  return FORTE_OK;
+}
+
+int forte_set_guess(forte_ctx *ctx, const double *C, int nvec) {
+  if (!ctx || nvec < 0 || (nvec > 0 && !C)) { set_error("bad guess arguments"); return FORTE_ERR_ARG; }
+  cudaFree(ctx->d_guess);
+  ctx->d_guess = nullptr;
+  ctx->nguess = 0;
+  if (nvec == 0) return FORTE_OK;
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_guess, sizeof(double) * ctx->Ndet * nvec));
+  FORTE_CUDA_TRY(cudaMemcpyAsync(ctx->d_guess, C, sizeof(double) * ctx->Ndet * nvec, cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+  ctx->nguess = nvec;
+  return FORTE_OK;
+}
+
+static int ensure_roots(forte_ctx *ctx, int nroots) {
+  size_t want = sizeof(double) * ctx->Ndet * nroots;
+  if (want > ctx->d_roots_cap) {
+    cudaFree(ctx->d_roots);
+    ctx->d_roots = nullptr;
+    ctx->d_roots_cap = 0;
+    if (cudaMalloc(&ctx->d_roots, want) != cudaSuccess) {
+      set_error("cudaMalloc roots failed");
+      return FORTE_ERR_ALLOC;
+    }
+    ctx->d_roots_cap = want;
+  }
+  return FORTE_OK;
+}
+
+int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (nroots < 1 || nroots > ctx->Ndet || nroots > 31) { set_error("nroots out of range"); return FORTE_ERR_ARG; }
+  if (!(tol > 0)) { set_error("tol must be > 0"); return FORTE_ERR_ARG; }
+  clear_error();
+  int rc = ensure_roots(ctx, nroots);
+  if (rc) return rc;
+  DvResult res;
+  ctx->nroots_done = 0;
+  if (ctx->precision == FORTE_FP64) {
+    rc = davidson_run(ctx, nroots, tol, FORTE_FP64, ctx->d_guess, ctx->nguess, ctx->dv_max_iter, ctx->d_roots, res);
+    if (rc) return rc;
+    ctx->dv_iters = res.iters;
+  } else {
+    // inner solve with the reduced-precision sigma, then FP64 Davidson started
+    // from its Ritz vectors until the FP64 residual meets tol
+    double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 3e-3 : 1e-4);
+    rc = davidson_run(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
+                      ctx->d_roots, res);
+    if (rc) return rc;
+    int it_in = res.iters;
+    rc = davidson_run(ctx, nroots, tol, FORTE_FP64, ctx->d_roots, nroots, ctx->dv_max_iter, ctx->d_roots, res);
+    if (rc) return rc;
+    ctx->dv_iters = it_in + res.iters;
+  }
+  for (int r = 0; r < nroots; ++r)
+    if ((rc = fix_sign(ctx, ctx->d_roots + (size_t)r * ctx->Ndet, ctx->Ndet))) return rc;
+  ctx->roots_E = res.E;
+  ctx->roots_rnorm = res.rn;
+  ctx->nroots_done = nroots;
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (!res.converged) {
+    set_error("Davidson did not converge in %d iterations (max residual %.3e)", ctx->dv_iters,
+              *std::max_element(res.rn.begin(), res.rn.end()));
+    return FORTE_ERR_NOT_CONVERGED;
+  }
+  return FORTE_OK;
+}
+
+int forte_get_roots(const forte_ctx *ctx, double *E, double *C, double *rnorm, int *iters) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (ctx->nroots_done == 0) { set_error("no Davidson results"); return FORTE_ERR_ARG; }
+  if (E) for (int r = 0; r < ctx->nroots_done; ++r) E[r] = ctx->roots_E[r];
+  if (rnorm) for (int r = 0; r < ctx->nroots_done; ++r) rnorm[r] = ctx->roots_rnorm[r];
+  if (iters) *iters = ctx->dv_iters;
+  if (C)
+    FORTE_CUDA_TRY(cudaMemcpyAsync(C, ctx->d_roots, sizeof(double) * ctx->Ndet * ctx->nroots_done,
+                                   cudaMemcpyDeviceToDevice, ctx->stream));
+  return FORTE_OK;
+}
+
+int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2) {
+  if (!ctx || !C) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  if (!g1 && !g2) return FORTE_OK;
+  return rdm12_fp64(ctx, C, C, g1, g2);
+}
+
+int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1) {
+  if (!ctx || !bra || !ket || !t1) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  return rdm12_fp64(ctx, bra, ket, t1, nullptr);
+}
+
+}  // extern "C"

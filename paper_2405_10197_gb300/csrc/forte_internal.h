@@ -1,0 +1,153 @@
+// Internal declarations shared by the translation units of libforte_gpu.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/forte_gpu.h"
+
+namespace forte {
+
+// Thread-local error text behind forte_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define FORTE_CUDA_TRY(expr)                                                               \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      forte::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,   \
+                       __LINE__);                                                          \
+      return FORTE_ERR_CUDA;                                                               \
+    }                                                                                      \
+  } while (0)
+
+#define FORTE_LAUNCH_CHECK()                                                               \
+  do {                                                                                     \
+    cudaError_t e_ = cudaGetLastError();                                                   \
+    if (e_ != cudaSuccess) {                                                               \
+      forte::set_error("kernel launch failed: %s (%s:%d)", cudaGetErrorString(e_),         \
+                       __FILE__, __LINE__);                                                \
+      return FORTE_ERR_CUDA;                                                               \
+    }                                                                                      \
+  } while (0)
+
+// One entry of the compact single-replacement list of a string I:
+// E_pq |I> = sgn |J>,  valid when q is in I and (p not in I or p == q).
+struct Repl {
+  int J;          // address of the resulting string
+  int8_t sgn;     // +1 / -1
+  uint8_t pq;     // p * n + q
+  uint8_t pair;   // symmetric pair index of {p, q}: max*(max+1)/2 + min
+  uint8_t pad;
+};
+static_assert(sizeof(Repl) == 8, "Repl must pack into 8 bytes");
+
+// Host-side string data of one spin.
+struct SpinHost {
+  int nel = 0;
+  long long N = 0;
+  int nk = 0;                      // entries per string in the compact list
+  std::vector<uint32_t> str;       // masks, ascending
+  std::vector<Repl> list;          // [N][nk]
+  std::vector<int> csr_ptr;        // same-spin Hamiltonian, CSR [N+1]
+  std::vector<int> csr_col;
+  std::vector<double> csr_val;
+  std::vector<double> diag;        // H_ss[I][I]
+};
+
+// Device-side copies of one spin's tables.
+struct SpinDev {
+  Repl *list = nullptr;
+  int *csr_ptr = nullptr;
+  int *csr_col = nullptr;
+  double *csr_val = nullptr;
+  float *csr_val32 = nullptr;
+  uint32_t *str = nullptr;
+  double *diag = nullptr;
+  int *dense = nullptr;   // [N][n*n]: (J << 1) | (sgn < 0), or -1 when E_pq|I> = 0
+};
+
+// Scratch buffer that grows on demand and is owned by the context.
+struct Scratch {
+  void *ptr = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t want);
+  void release();
+};
+
+}  // namespace forte
+
+struct forte_ctx {
+  int n = 0, na = 0, nb = 0;
+  int npair = 0;
+  long long Na = 0, Nb = 0, Ndet = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = FORTE_FP64;
+  bool same_strings = false;  // alpha and beta tables identical (na == nb)
+
+  std::vector<double> h, eri, kmat;  // host copies; kmat = h - 1/2 sum_r (pr|rq)
+  forte::SpinHost sh[2];
+  forte::SpinDev sd[2];
+
+  double *d_gpair = nullptr;    // [npair][npair] (pq|rs) over symmetric pairs
+  double *d_hdiag = nullptr;    // [Na][Nb]
+  float *d_gpair32 = nullptr;   // FP32 copy for the mixed path
+
+  // Davidson controls and results
+  int dv_max_sub = 12, dv_collapse = 2, dv_max_iter = 200;
+  double dv_guard = 1e-8;
+  int nroots_done = 0;
+  int dv_iters = 0;
+  std::vector<double> roots_E, roots_rnorm;
+  double *d_roots = nullptr;    // [nroots][Ndet]
+  size_t d_roots_cap = 0;
+  double *d_guess = nullptr;    // restart vectors
+  int nguess = 0;
+
+  forte::Scratch sc_t1, sc_t2;     // sigma: transposes for the beta-beta term
+  forte::Scratch sc_dv;            // Davidson subspace and work vectors
+  forte::Scratch sc_small;         // small device arrays (dots, norms)
+  forte::Scratch sc_rdm;           // RDM intermediates
+  forte::Scratch sc_mixed;         // reduced-precision copies of vectors
+};
+
+namespace forte {
+
+// setup.cu
+int build_spin_tables(forte_ctx *ctx);
+int upload_tables(forte_ctx *ctx);
+
+// sigma_fp64.cu
+int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
+int hdiag_build(forte_ctx *ctx);
+
+// sigma_mixed.cu
+int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode);
+
+// vec_kernels.cu: Davidson building blocks (all FP64, HBM-bound).  Reductions
+// use the context's sc_small buffer for block partials.
+int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n,
+                double *out);
+int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb,
+               double *out, long long ldo, long long n);
+int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld,
+                        const double *u, double theta, double guard, double *t, double *rnorm2,
+                        long long n);
+int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c,
+                   const double *t_in, double *t_out, double *dots_out, long long n);
+int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n);
+int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out);
+int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host);
+
+// rdm.cu
+int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2);
+
+// Host Jacobi eigensolver for the small symmetric subspace matrix (ascending).
+void sym_eig(int k, const double *A, double *w, double *U);
+
+}  // namespace forte

@@ -1,0 +1,330 @@
+// Davidson-Liu building blocks on long FP64 vectors (step a7).  Each kernel
+// streams its operands once; reductions go through per-block partial sums
+// and a second pass, so results do not depend on atomic ordering.
+#include "forte_internal.h"
+
+namespace forte {
+
+constexpr int VK_THREADS = 256;
+constexpr int VK_EPT = 16;  // elements per thread per block
+constexpr long long VK_CHUNK = (long long)VK_THREADS * VK_EPT;
+constexpr int VK_MAXV = 64;  // vectors handled by one multidot / update launch
+
+static inline unsigned vk_blocks(long long n) { return (unsigned)((n + VK_CHUNK - 1) / VK_CHUNK); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; every thread returns the total.  red must hold 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  return red[0];
+}
+
+// part[b][m] -> out[m] (sum over b).  grid.x = m.
+__global__ void k_sum_partials(const double *__restrict__ part, int nblk, int m, double *__restrict__ out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(long long)b * m + blockIdx.x];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// part[block][i] = sum over the block's chunk of V_i . x   (i < nv)
+__global__ void __launch_bounds__(VK_THREADS) k_multidot(const double *__restrict__ V, int nv, long long ld,
+                                                         const double *__restrict__ x, long long n,
+                                                         double *__restrict__ part) {
+  __shared__ double red[32];
+  const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
+  double xr[VK_EPT];
+#pragma unroll
+  for (int k = 0; k < VK_EPT; ++k) {
+    long long j = base + (long long)k * VK_THREADS;
+    xr[k] = (j < n) ? x[j] : 0.0;
+  }
+  for (int i = 0; i < nv; ++i) {
+    const double *v = V + (long long)i * ld;
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < VK_EPT; ++k) {
+      long long j = base + (long long)k * VK_THREADS;
+      if (j < n) a += v[j] * xr[k];
+    }
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * nv + i] = a;
+  }
+}
+
+// out_j = sum_i coef[i*ncomb + j] V_i  (j < ncomb <= 32)
+__global__ void __launch_bounds__(VK_THREADS) k_combine(const double *__restrict__ V, int nv, long long ld,
+                                                        const double *__restrict__ coef, int ncomb,
+                                                        double *__restrict__ out, long long ldo, long long n) {
+  __shared__ double sc[VK_MAXV * 32];
+  for (int i = threadIdx.x; i < nv * ncomb; i += blockDim.x) sc[i] = coef[i];
+  __syncthreads();
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    double acc[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int i = 0; i < nv; ++i) {
+      double v = V[(long long)i * ld + j];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < ncomb) acc[c] += sc[i * ncomb + c] * v;
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < ncomb) out[(long long)c * ldo + j] = acc[c];
+  }
+}
+
+// r = sum_i u_i S_i - theta sum_i u_i B_i ;  t = r / (theta - hdiag) (guarded);
+// part[block] = sum r^2 over the block's chunk.
+__global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
+    const double *__restrict__ B, const double *__restrict__ S, int k, long long ld,
+    const double *__restrict__ u, double theta, const double *__restrict__ hd, double guard,
+    double *__restrict__ t, long long n, double *__restrict__ part) {
+  __shared__ double red[32];
+  __shared__ double su[VK_MAXV];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) su[i] = u[i];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
+  double rr = 0.0;
+#pragma unroll 4
+  for (int e = 0; e < VK_EPT; ++e) {
+    long long j = base + (long long)e * VK_THREADS;
+    if (j >= n) break;
+    double hx = 0.0, x = 0.0;
+    for (int i = 0; i < k; ++i) {
+      hx += su[i] * S[(long long)i * ld + j];
+      x += su[i] * B[(long long)i * ld + j];
+    }
+    double r = hx - theta * x;
+    rr += r * r;
+    double den = theta - hd[j];
+    if (fabs(den) < guard) den = (den >= 0.0) ? guard : -guard;
+    t[j] = r / den;
+  }
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+}
+
+// t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2
+__global__ void __launch_bounds__(VK_THREADS) k_orth_update(const double *__restrict__ Bm, int k,
+                                                            long long ld, const double *__restrict__ c,
+                                                            const double *t_in, double *t_out, long long n,
+                                                            double *__restrict__ part) {
+  __shared__ double red[32];
+  __shared__ double sc[VK_MAXV];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = c[i];
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
+  double tr[VK_EPT];
+#pragma unroll
+  for (int e = 0; e < VK_EPT; ++e) {
+    long long j = base + (long long)e * VK_THREADS;
+    tr[e] = (j < n) ? t_in[j] : 0.0;
+  }
+  for (int i = 0; i < k; ++i) {
+    const double *b = Bm + (long long)i * ld;
+#pragma unroll
+    for (int e = 0; e < VK_EPT; ++e) {
+      long long j = base + (long long)e * VK_THREADS;
+      if (j < n) tr[e] -= sc[i] * b[j];
+    }
+  }
+  double nn = 0.0;
+#pragma unroll
+  for (int e = 0; e < VK_EPT; ++e) {
+    long long j = base + (long long)e * VK_THREADS;
+    if (j < n) {
+      t_out[j] = tr[e];
+      nn += tr[e] * tr[e];
+    }
+  }
+  for (int i = 0; i < k; ++i) {
+    const double *b = Bm + (long long)i * ld;
+    double a = 0.0;
+#pragma unroll
+    for (int e = 0; e < VK_EPT; ++e) {
+      long long j = base + (long long)e * VK_THREADS;
+      if (j < n) a += b[j] * tr[e];
+    }
+    a = block_sum(a, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + i] = a;
+  }
+  nn = block_sum(nn, red);
+  if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nn;
+}
+
+__global__ void k_scale(double *__restrict__ x, const double *__restrict__ src, double alpha, long long n) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    x[j] = alpha * src[j];
+}
+
+// Block minimum of (value, index) over entries not in excl[0..nex); lexicographic.
+__global__ void k_argmin(const double *__restrict__ x, long long n, const long long *__restrict__ excl,
+                         int nex, double *__restrict__ bval, long long *__restrict__ bidx) {
+  __shared__ double sv[VK_THREADS];
+  __shared__ long long si[VK_THREADS];
+  double best = INFINITY;
+  long long bi = -1;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x) {
+    double v = x[j];
+    bool skip = false;
+    for (int e = 0; e < nex; ++e) skip |= (excl[e] == j);
+    if (skip) continue;
+    if (bi < 0 || v < best || (v == best && j < bi)) { best = v; bi = j; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double v2 = sv[threadIdx.x + s];
+      long long i2 = si[threadIdx.x + s];
+      double v1 = sv[threadIdx.x];
+      long long i1 = si[threadIdx.x];
+      bool take = (i2 >= 0) && (i1 < 0 || v2 < v1 || (v2 == v1 && i2 < i1));
+      if (take) { sv[threadIdx.x] = v2; si[threadIdx.x] = i2; }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { bval[blockIdx.x] = sv[0]; bidx[blockIdx.x] = si[0]; }
+}
+
+__global__ void k_nonfinite(const double *__restrict__ x, long long n, int *flag) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[j])) *flag = 1;
+}
+
+// ------------------------------------------------------------------ host wrappers
+
+static int part_buffer(forte_ctx *ctx, size_t doubles, double **p) {
+  int rc = ctx->sc_small.ensure(sizeof(double) * (doubles + 64));
+  if (rc) return rc;
+  *p = (double *)ctx->sc_small.ptr;
+  return FORTE_OK;
+}
+
+int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n,
+                double *out) {
+  if (nv <= 0) return FORTE_OK;
+  if (nv > VK_MAXV) { set_error("multidot: too many vectors (%d)", nv); return FORTE_ERR_ARG; }
+  unsigned nb = vk_blocks(n);
+  double *part;
+  int rc = part_buffer(ctx, (size_t)nb * nv, &part);
+  if (rc) return rc;
+  k_multidot<<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
+  FORTE_LAUNCH_CHECK();
+  k_sum_partials<<<nv, 256, 0, ctx->stream>>>(part, (int)nb, nv, out);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
+int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb,
+               double *out, long long ldo, long long n) {
+  if (nv > VK_MAXV || ncomb > 32) { set_error("combine: too many vectors"); return FORTE_ERR_ARG; }
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_combine<<<nb, 256, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, out, ldo, n);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
+int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld,
+                        const double *u, double theta, double guard, double *t, double *rnorm2,
+                        long long n) {
+  if (k > VK_MAXV) { set_error("residual: subspace too large (%d)", k); return FORTE_ERR_ARG; }
+  unsigned nb = vk_blocks(n);
+  double *part;
+  int rc = part_buffer(ctx, nb, &part);
+  if (rc) return rc;
+  k_residual_precond<<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
+                                                          n, part);
+  FORTE_LAUNCH_CHECK();
+  k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, rnorm2);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
+int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c,
+                   const double *t_in, double *t_out, double *dots_out, long long n) {
+  if (k + 1 > VK_MAXV) { set_error("orth: subspace too large (%d)", k); return FORTE_ERR_ARG; }
+  unsigned nb = vk_blocks(n);
+  double *part;
+  int rc = part_buffer(ctx, (size_t)nb * (k + 1), &part);
+  if (rc) return rc;
+  k_orth_update<<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+  FORTE_LAUNCH_CHECK();
+  k_sum_partials<<<k + 1, 256, 0, ctx->stream>>>(part, (int)nb, k + 1, dots_out);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
+int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n) {
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  k_scale<<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
+// k smallest entries (ties: lowest index), host output idx_out[k].
+int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out) {
+  const unsigned nb = (unsigned)std::min<long long>((n + VK_THREADS - 1) / VK_THREADS, 1024);
+  size_t need = sizeof(double) * nb + sizeof(long long) * nb + sizeof(long long) * (k + 1);
+  int rc = ctx->sc_small.ensure(need + 256);
+  if (rc) return rc;
+  double *bval = (double *)ctx->sc_small.ptr;
+  long long *bidx = (long long *)(bval + nb);
+  long long *excl = bidx + nb;
+  std::vector<double> hv(nb);
+  std::vector<long long> hi(nb);
+  for (int r = 0; r < k; ++r) {
+    if (r > 0)
+      FORTE_CUDA_TRY(cudaMemcpyAsync(excl, idx_out, sizeof(long long) * r, cudaMemcpyHostToDevice, ctx->stream));
+    k_argmin<<<nb, VK_THREADS, 0, ctx->stream>>>(x, n, excl, r, bval, bidx);
+    FORTE_LAUNCH_CHECK();
+    FORTE_CUDA_TRY(cudaMemcpyAsync(hv.data(), bval, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    FORTE_CUDA_TRY(cudaMemcpyAsync(hi.data(), bidx, sizeof(long long) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+    FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    double best = INFINITY;
+    long long bi = -1;
+    for (unsigned b = 0; b < nb; ++b) {
+      if (hi[b] < 0) continue;
+      if (bi < 0 || hv[b] < best || (hv[b] == best && hi[b] < bi)) { best = hv[b]; bi = hi[b]; }
+    }
+    if (bi < 0) { set_error("argmin: fewer than %d entries", k); return FORTE_ERR_ARG; }
+    idx_out[r] = bi;
+  }
+  return FORTE_OK;
+}
+
+int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host) {
+  int rc = ctx->sc_small.ensure(256);
+  if (rc) return rc;
+  int *flag = (int *)ctx->sc_small.ptr;
+  FORTE_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
+  k_nonfinite<<<nb, 256, 0, ctx->stream>>>(x, n, flag);
+  FORTE_LAUNCH_CHECK();
+  FORTE_CUDA_TRY(cudaMemcpyAsync(flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return FORTE_OK;
+}
+
+}  // namespace forte
