@@ -108,7 +108,10 @@ int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
 
 /* Davidson-Liu solve for the nroots lowest eigenpairs of H in the determinant
  * space (any total spin), to max_k ||H x_k - theta_k x_k||_2 < tol.
- * Guess: unit vectors at the lowest H_II (ties: lowest index); preconditioner
+ * Guess: unit vectors at the lowest H_II (ties: lowest index), each plus a
+ * deterministic perturbation of norm ~0.02 (entries from the splitmix64
+ * counter generator) so that closed-shell guesses still reach roots of every
+ * spin-flip symmetry sector, orthonormalised; preconditioner
  * (theta - H_II)^-1 with |denominator| clamped to denom_guard; classical
  * Gram-Schmidt applied twice; subspace collapse (forte_set_davidson_params).
  * In a mixed mode the inner iterations use that mode's sigma and the final
@@ -144,6 +147,25 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2);
 /* One-body transition density matrix between two states (Sec. II.A.1):
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
+
+/* Kernel tracing.  While enabled, every kernel this library launches for the
+ * context is bracketed by CUDA events on the context stream (on = 1 also
+ * clears earlier records; on = 0 stops recording and keeps them). */
+int forte_profile_enable(forte_ctx *ctx, int on);
+
+/* Launch count and summed device time (ms) of the recorded launches whose
+ * kernel name equals `kernel` (NULL: all kernels).  Synchronises the stream.
+ * Host outputs; either may be NULL. */
+int forte_profile_query(forte_ctx *ctx, const char *kernel, int *launches, double *total_ms);
+
+/* Name of the i-th distinct recorded kernel (NULL when i is out of range);
+ * the string lives as long as the library. */
+const char *forte_profile_kernel_name(forte_ctx *ctx, int i);
+
+/* Number of vectors pushed through the sigma build since the context was
+ * created, in FP64 and in a reduced-precision mode (host outputs, may be NULL). */
+int forte_get_counters(const forte_ctx *ctx, long long *sigma_vectors_fp64,
+                       long long *sigma_vectors_mixed);
 
 #ifdef __cplusplus
 }

@@ -155,11 +155,37 @@ def solve_dense(norb, nalpha, nbeta, h, eri, nroots=1):
     return w[:nroots], vecs
 
 
+_SM_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _splitmix64(x):
+    """splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014) on uint64 arrays."""
+    with np.errstate(over="ignore"):
+        z = x + _SM_GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def guess_perturbation(nd, k, amp=0.02):
+    """Deterministic symmetry-breaking perturbation of guess vector k: entries
+    amp * sqrt(12/nd) * (u - 1/2), u uniform in [0, 1) from splitmix64 of
+    (i + (k+1) * golden gamma).  Its norm is about amp.  Without it a
+    closed-shell guess keeps the subspace inside one spin-flip symmetry sector
+    and roots of the other sector are never found."""
+    with np.errstate(over="ignore"):
+        x = np.arange(nd, dtype=np.uint64) + np.uint64(k + 1) * _SM_GAMMA
+    u = (_splitmix64(x) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return amp * np.sqrt(12.0 / nd) * (u - 0.5)
+
+
 def davidson(norb, nalpha, nbeta, h, eri, nroots=1, tol=1e-10, max_iter=200,
              max_sub_per_root=12, collapse_per_root=2, guard=1e-8, verbose=False):
     """Textbook Davidson-Liu with the oracle's direct sigma (all FP64).
 
-    Guess: unit vectors at the lowest diagonal elements (ties: lowest index).
+    Guess: unit vectors at the lowest diagonal elements (ties: lowest index)
+    plus the small deterministic perturbation of ``guess_perturbation``,
+    orthonormalised.
     Preconditioner: (theta - H_II)^-1, denominators below ``guard`` in size
     replaced by +-guard.  Orthogonalisation: classical Gram-Schmidt applied
     twice.  Converged when every root's residual 2-norm is below ``tol``.
@@ -171,7 +197,10 @@ def davidson(norb, nalpha, nbeta, h, eri, nroots=1, tol=1e-10, max_iter=200,
     nguess = min(nroots, Nd)
     B = np.zeros((nguess, Nd))
     for k in range(nguess):
-        B[k, order[k]] = 1.0
+        B[k] = guess_perturbation(Nd, k)
+        B[k, order[k]] += 1.0
+    q, _ = np.linalg.qr(B.T)
+    B = np.ascontiguousarray(q.T)
     S = sigma(norb, nalpha, nbeta, h, eri, B)
     max_sub = max(max_sub_per_root * nroots, nroots + 1)
     it = 0

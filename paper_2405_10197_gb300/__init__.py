@@ -74,7 +74,12 @@ def library():
         "forte_set_guess": [vp, vp, i],
         "forte_rdms": [vp, vp, vp, vp],
         "forte_tdm1": [vp, vp, vp, vp],
+        "forte_profile_enable": [vp, i],
+        "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
+        "forte_get_counters": [vp, vp, vp],
     }
+    L.forte_profile_kernel_name.restype = ctypes.c_char_p
+    L.forte_profile_kernel_name.argtypes = [vp, i]
     for name, args in sigs.items():
         f = getattr(L, name)
         f.restype = i
@@ -207,6 +212,43 @@ def forte_tdm1(ctx, bra, ket, t1, norb):
     na, nb = forte_get_sizes(ctx)
     return _check(library().forte_tdm1(ctx, _ptr(bra, na * nb), _ptr(ket, na * nb),
                                        _ptr(t1, norb * norb)))
+
+
+def forte_profile_enable(ctx, on):
+    return _check(library().forte_profile_enable(ctx, int(on)))
+
+
+def forte_profile_query(ctx, kernel=None):
+    """(launches, total_ms) of the recorded launches of `kernel` (None: all)."""
+    n = ctypes.c_int()
+    ms = ctypes.c_double()
+    k = kernel.encode() if kernel else None
+    _check(library().forte_profile_query(ctx, k, ctypes.addressof(n), ctypes.addressof(ms)))
+    return n.value, ms.value
+
+
+def forte_profile_kernel_name(ctx, i):
+    r = library().forte_profile_kernel_name(ctx, int(i))
+    return r.decode() if r else None
+
+
+def forte_get_counters(ctx):
+    """(sigma vectors built in FP64, sigma vectors built in a reduced-precision mode)."""
+    a, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(library().forte_get_counters(ctx, ctypes.addressof(a), ctypes.addressof(b)))
+    return a.value, b.value
+
+
+def profile_table(ctx):
+    """{kernel name: (launches, total_ms)} of the recorded launches."""
+    out = {}
+    i = 0
+    while True:
+        name = forte_profile_kernel_name(ctx, i)
+        if name is None:
+            return out
+        out[name] = forte_profile_query(ctx, name)
+        i += 1
 
 
 # --------------------------------------------------------------- convenience

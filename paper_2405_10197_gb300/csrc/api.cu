@@ -25,6 +25,30 @@ void set_error(const char *fmt, ...) {
 }
 void clear_error() { g_err[0] = 0; }
 
+static cudaEvent_t prof_event(forte_ctx *ctx) {
+  if (!ctx->prof_pool.empty()) {
+    cudaEvent_t e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(forte_ctx *c, const char *name) : ctx(c) {
+  if (!ctx || !ctx->prof_on) return;
+  cudaEvent_t a = prof_event(ctx), e = prof_event(ctx);
+  if (!a || !e) return;
+  cudaEventRecord(a, ctx->stream);
+  ctx->prof.push_back(ProfRecord{name, a, e});
+  b = e;
+}
+
+ProfScope::~ProfScope() {
+  if (b) cudaEventRecord(b, ctx->stream);
+}
+
 // Cyclic Jacobi eigensolver for a small symmetric matrix (Golub & Van Loan,
 // Sec. 8.5): A row-major k x k; w ascending; U[i*k + j] = component i of
 // eigenvector j.
@@ -74,7 +98,11 @@ void sym_eig(int k, const double *A, double *w, double *U) {
 
 static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
-  if (mode == FORTE_FP64) return sigma_fp64(ctx, C, S, nvec);
+  if (mode == FORTE_FP64) {
+    ctx->n_sigma_fp64 += nvec;
+    return sigma_fp64(ctx, C, S, nvec);
+  }
+  ctx->n_sigma_mixed += nvec;
   return sigma_mixed(ctx, C, S, nvec, mode);
 }
 
@@ -114,14 +142,40 @@ __global__ void k_absmax(const double *__restrict__ x, long long n, double *bval
   if (threadIdx.x == 0) { bval[blockIdx.x] = sv[0]; bidx[blockIdx.x] = si[0]; }
 }
 
+// splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Guess vector k: unit vector at idx plus a deterministic perturbation of norm
+// ~amp, entries amp*sqrt(12/n)*(u-1/2) with u = splitmix64(i + (k+1)*gamma)
+// in [0,1).  The perturbation couples the spin-flip symmetry sectors so that
+// roots of every total spin are reachable from closed-shell guesses.
+__global__ void k_guess(double *__restrict__ x, long long n, long long idx, int k, double amp) {
+  const double scale = amp * sqrt(12.0 / (double)n);
+  const unsigned long long key = (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ull;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = splitmix64((unsigned long long)i + key);
+    double u = (double)(z >> 11) * 0x1.0p-53;
+    x[i] = scale * (u - 0.5) + (i == idx ? 1.0 : 0.0);
+  }
+}
+
 static int fix_sign(forte_ctx *ctx, double *x, long long n) {
   const unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 512);
   int rc = ctx->sc_small.ensure(sizeof(double) * nb * 2 + 64);
   if (rc) return rc;
   double *bv = (double *)ctx->sc_small.ptr;
   long long *bi = (long long *)(bv + nb);
-  k_absmax<<<nb, 256, 0, ctx->stream>>>(x, n, bv, bi);
+  {
+    FORTE_PROF(ctx, "absmax");
+    k_absmax<<<nb, 256, 0, ctx->stream>>>(x, n, bv, bi);
   FORTE_LAUNCH_CHECK();
+  }
   std::vector<double> hv(nb);
   std::vector<long long> hi(nb);
   FORTE_CUDA_TRY(cudaMemcpyAsync(hv.data(), bv, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
@@ -196,9 +250,14 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     int used = 0;
     for (size_t c = 0; c < idx.size() && used < need && c < (size_t)std::min<long long>(N, need + k); ++c) {
       double *b = B + (size_t)k * N;
-      FORTE_CUDA_TRY(cudaMemsetAsync(b, 0, sizeof(double) * N, st));
-      double one = 1.0;
-      FORTE_CUDA_TRY(cudaMemcpyAsync(b + idx[c], &one, sizeof(double), cudaMemcpyHostToDevice, st));
+      {
+        unsigned nbk = (unsigned)std::min<long long>((N + 255) / 256, 152LL * 16);
+        {
+          FORTE_PROF(ctx, "guess");
+          k_guess<<<nbk, 256, 0, st>>>(b, N, idx[c], k, 0.02);
+        FORTE_LAUNCH_CHECK();
+        }
+      }
       if (k > 0) {
         // orthogonalise against the supplied guesses
         std::vector<double> h_d(65);
@@ -209,6 +268,12 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
         FORTE_CUDA_TRY(cudaStreamSynchronize(st));
         if (!(h_d[k] > 1e-12)) continue;
         if ((rc = vk_scale(ctx, b, b, 1.0 / sqrt(h_d[k]), N))) return rc;
+      } else {
+        std::vector<double> h_d(2);
+        if ((rc = vk_multidot(ctx, b, 1, N, b, N, d_d0))) return rc;
+        FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d0, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+        if ((rc = vk_scale(ctx, b, b, 1.0 / sqrt(h_d[0]), N))) return rc;
       }
       ++k;
       ++used;
@@ -406,6 +471,8 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release();
+  for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -567,6 +634,55 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2) {
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1) {
   if (!ctx || !bra || !ket || !t1) { set_error("NULL argument"); return FORTE_ERR_ARG; }
   return rdm12_fp64(ctx, bra, ket, t1, nullptr);
+}
+
+int forte_get_counters(const forte_ctx *ctx, long long *fp64, long long *mixed) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (fp64) *fp64 = ctx->n_sigma_fp64;
+  if (mixed) *mixed = ctx->n_sigma_mixed;
+  return FORTE_OK;
+}
+
+int forte_profile_enable(forte_ctx *ctx, int on) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (on) {
+    FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (auto &r : ctx->prof) {
+      ctx->prof_pool.push_back(r.a);
+      ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+  }
+  ctx->prof_on = (on != 0);
+  return FORTE_OK;
+}
+
+int forte_profile_query(forte_ctx *ctx, const char *kernel, int *launches, double *total_ms) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  int cnt = 0;
+  double tot = 0.0;
+  for (auto &r : ctx->prof) {
+    if (kernel && strcmp(kernel, r.name) != 0) continue;
+    float ms = 0.f;
+    FORTE_CUDA_TRY(cudaEventElapsedTime(&ms, r.a, r.b));
+    ++cnt;
+    tot += ms;
+  }
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = tot;
+  return FORTE_OK;
+}
+
+const char *forte_profile_kernel_name(forte_ctx *ctx, int i) {
+  if (!ctx || i < 0) return nullptr;
+  std::vector<const char *> seen;
+  for (auto &r : ctx->prof) {
+    bool dup = false;
+    for (auto *s : seen) dup |= (strcmp(s, r.name) == 0);
+    if (!dup) seen.push_back(r.name);
+  }
+  return i < (int)seen.size() ? seen[i] : nullptr;
 }
 
 }  // extern "C"

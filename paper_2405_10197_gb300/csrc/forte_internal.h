@@ -79,6 +79,12 @@ struct Scratch {
   void release();
 };
 
+// One traced launch: events recorded before and after it on the context stream.
+struct ProfRecord {
+  const char *name;
+  cudaEvent_t a, b;
+};
+
 }  // namespace forte
 
 struct forte_ctx {
@@ -114,7 +120,26 @@ struct forte_ctx {
   forte::Scratch sc_small;         // small device arrays (dots, norms)
   forte::Scratch sc_rdm;           // RDM intermediates
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
+
+  long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
+  bool prof_on = false;
+  std::vector<forte::ProfRecord> prof;
+  std::vector<cudaEvent_t> prof_pool;
 };
+
+namespace forte {
+
+// Brackets one kernel launch with CUDA events when tracing is enabled.
+struct ProfScope {
+  forte_ctx *ctx;
+  cudaEvent_t b = nullptr;
+  ProfScope(forte_ctx *c, const char *name);
+  ~ProfScope();
+};
+
+}  // namespace forte
+
+#define FORTE_PROF(ctx, name) forte::ProfScope forte_prof_scope_(ctx, name)
 
 namespace forte {
 

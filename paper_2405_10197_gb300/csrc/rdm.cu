@@ -193,42 +193,69 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
   double *g1w = g1 ? g1 : (double *)(w + off_g1);
 
   // gamma: alpha rows, then beta rows on the transposed vectors
-  k_g1_part<<<(unsigned)NA, 256, 0, st>>>(ctx->sd[0].list, ctx->sh[0].nk, bra, ket, NB, n2, P);
+  {
+    FORTE_PROF(ctx, "g1_part");
+    k_g1_part<<<(unsigned)NA, 256, 0, st>>>(ctx->sd[0].list, ctx->sh[0].nk, bra, ket, NB, n2, P);
   FORTE_LAUNCH_CHECK();
+  }
   dim3 tb(32, 8), tg((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32));
-  k_transpose_r<double><<<tg, tb, 0, st>>>(ket, Tk, NA, NB);
+  {
+    FORTE_PROF(ctx, "transpose_r");
+    k_transpose_r<double><<<tg, tb, 0, st>>>(ket, Tk, NA, NB);
   FORTE_LAUNCH_CHECK();
+  }
   const double *TbraP = Tk;
   if (!same) {
-    k_transpose_r<double><<<tg, tb, 0, st>>>(bra, Tb, NA, NB);
+    {
+      FORTE_PROF(ctx, "transpose_r");
+      k_transpose_r<double><<<tg, tb, 0, st>>>(bra, Tb, NA, NB);
     FORTE_LAUNCH_CHECK();
+    }
     TbraP = Tb;
   }
   const int nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
-  k_g1_part<<<(unsigned)NB, 256, 0, st>>>(ctx->sd[1].list, nkB, TbraP, Tk, NA, n2, P + NA * n2);
+  {
+    FORTE_PROF(ctx, "g1_part");
+    k_g1_part<<<(unsigned)NB, 256, 0, st>>>(ctx->sd[1].list, nkB, TbraP, Tk, NA, n2, P + NA * n2);
   FORTE_LAUNCH_CHECK();
-  k_sum_cols2<<<n2, 256, 0, st>>>(P, NA, P + NA * n2, NB, n2, g1w);
+  }
+  {
+    FORTE_PROF(ctx, "sum_cols2");
+    k_sum_cols2<<<n2, 256, 0, st>>>(P, NA, P + NA * n2, NB, n2, g1w);
   FORTE_LAUNCH_CHECK();
+  }
   if (!g2) return FORTE_OK;
 
   double *Dk = (double *)(w + off_D);
   double *Db = same ? Dk : Dk + (size_t)n2 * ND;
   unsigned nbD = (unsigned)std::min<long long>((ND + 255) / 256, 152LL * 32);
-  k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, ket, NA, NB, Dk);
+  {
+    FORTE_PROF(ctx, "build_D");
+    k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, ket, NA, NB, Dk);
   FORTE_LAUNCH_CHECK();
+  }
   if (!same) {
-    k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, bra, NA, NB, Db);
+    {
+      FORTE_PROF(ctx, "build_D");
+      k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, bra, NA, NB, Db);
     FORTE_LAUNCH_CHECK();
+    }
   }
   double *G = (double *)(w + off_G);
   const int ntile = (n2 + GT - 1) / GT;
   long long kper = (ND + nsplit - 1) / nsplit;
   dim3 gg(ntile * ntile, nsplit);
   // M[a][b] = <D_bra^a, D_ket^b>, where D_bra^{qp} = E_qp bra
-  k_gram<<<gg, 256, 0, st>>>(Db, Dk, n2, ND, kper, G);
+  {
+    FORTE_PROF(ctx, "gram");
+    k_gram<<<gg, 256, 0, st>>>(Db, Dk, n2, ND, kper, G);
   FORTE_LAUNCH_CHECK();
-  k_finish_g2<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(G, nsplit, n, g1w, g2);
+  }
+  {
+    FORTE_PROF(ctx, "finish_g2");
+    k_finish_g2<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(G, nsplit, n, g1w, g2);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 

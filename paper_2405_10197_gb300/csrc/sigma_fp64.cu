@@ -154,9 +154,12 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
   {
     int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
     dim3 grid((unsigned)(NA * nchunk), nvec);
-    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
+    {
+      FORTE_PROF(ctx, "ss_spmm");
+      k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
                                                    ctx->sd[0].csr_val, C, S, NA, NB, nchunk, ND, 0);
     FORTE_LAUNCH_CHECK();
+    }
   }
   // beta-beta: T1 = C^T, T2 = H_bb T1, S += T2^T
   {
@@ -167,16 +170,25 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
     double *T1 = (double *)ctx->sc_t1.ptr, *T2 = (double *)ctx->sc_t2.ptr;
     dim3 tb(32, 8);
     dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
-    k_transpose<double><<<g1, tb, 0, st>>>(C, T1, NA, NB, ND, 0);
+    {
+      FORTE_PROF(ctx, "transpose");
+      k_transpose<double><<<g1, tb, 0, st>>>(C, T1, NA, NB, ND, 0);
     FORTE_LAUNCH_CHECK();
+    }
     int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
     dim3 grid((unsigned)(NB * nchunk), nvec);
-    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
+    {
+      FORTE_PROF(ctx, "ss_spmm");
+      k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
                                                    ctx->sd[1].csr_val, T1, T2, NB, NA, nchunk, ND, 0);
     FORTE_LAUNCH_CHECK();
+    }
     dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
-    k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
+    {
+      FORTE_PROF(ctx, "transpose");
+      k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
     FORTE_LAUNCH_CHECK();
+    }
   }
   // alpha-beta
   const int nkA = ctx->sh[0].nk, nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
@@ -197,9 +209,12 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
     }
     FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)NA, nvec);
-    k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
+    {
+      FORTE_PROF(ctx, "ab_fp64");
+      k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
                                               ctx->d_gpair, ctx->npair, C, S, ND, TJ);
     FORTE_LAUNCH_CHECK();
+    }
   }
   return FORTE_OK;
 }

@@ -230,10 +230,16 @@ int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const dou
   double *part;
   int rc = part_buffer(ctx, (size_t)nb * nv, &part);
   if (rc) return rc;
-  k_multidot<<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
+  {
+    FORTE_PROF(ctx, "multidot");
+    k_multidot<<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
   FORTE_LAUNCH_CHECK();
-  k_sum_partials<<<nv, 256, 0, ctx->stream>>>(part, (int)nb, nv, out);
+  }
+  {
+    FORTE_PROF(ctx, "sum_partials");
+    k_sum_partials<<<nv, 256, 0, ctx->stream>>>(part, (int)nb, nv, out);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 
@@ -241,8 +247,11 @@ int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const doub
                double *out, long long ldo, long long n) {
   if (nv > VK_MAXV || ncomb > 32) { set_error("combine: too many vectors"); return FORTE_ERR_ARG; }
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
-  k_combine<<<nb, 256, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, out, ldo, n);
+  {
+    FORTE_PROF(ctx, "combine");
+    k_combine<<<nb, 256, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, out, ldo, n);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 
@@ -254,11 +263,17 @@ int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k,
   double *part;
   int rc = part_buffer(ctx, nb, &part);
   if (rc) return rc;
-  k_residual_precond<<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
+  {
+    FORTE_PROF(ctx, "residual_precond");
+    k_residual_precond<<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
                                                           n, part);
   FORTE_LAUNCH_CHECK();
-  k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, rnorm2);
+  }
+  {
+    FORTE_PROF(ctx, "sum_partials");
+    k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, rnorm2);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 
@@ -269,17 +284,26 @@ int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const d
   double *part;
   int rc = part_buffer(ctx, (size_t)nb * (k + 1), &part);
   if (rc) return rc;
-  k_orth_update<<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+  {
+    FORTE_PROF(ctx, "orth_update");
+    k_orth_update<<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
   FORTE_LAUNCH_CHECK();
-  k_sum_partials<<<k + 1, 256, 0, ctx->stream>>>(part, (int)nb, k + 1, dots_out);
+  }
+  {
+    FORTE_PROF(ctx, "sum_partials");
+    k_sum_partials<<<k + 1, 256, 0, ctx->stream>>>(part, (int)nb, k + 1, dots_out);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n) {
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
-  k_scale<<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
+  {
+    FORTE_PROF(ctx, "scale");
+    k_scale<<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
   FORTE_LAUNCH_CHECK();
+  }
   return FORTE_OK;
 }
 
@@ -297,8 +321,11 @@ int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *
   for (int r = 0; r < k; ++r) {
     if (r > 0)
       FORTE_CUDA_TRY(cudaMemcpyAsync(excl, idx_out, sizeof(long long) * r, cudaMemcpyHostToDevice, ctx->stream));
-    k_argmin<<<nb, VK_THREADS, 0, ctx->stream>>>(x, n, excl, r, bval, bidx);
+    {
+      FORTE_PROF(ctx, "argmin");
+      k_argmin<<<nb, VK_THREADS, 0, ctx->stream>>>(x, n, excl, r, bval, bidx);
     FORTE_LAUNCH_CHECK();
+    }
     FORTE_CUDA_TRY(cudaMemcpyAsync(hv.data(), bval, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
     FORTE_CUDA_TRY(cudaMemcpyAsync(hi.data(), bidx, sizeof(long long) * nb, cudaMemcpyDeviceToHost, ctx->stream));
     FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -320,8 +347,11 @@ int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_hos
   int *flag = (int *)ctx->sc_small.ptr;
   FORTE_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 8);
-  k_nonfinite<<<nb, 256, 0, ctx->stream>>>(x, n, flag);
+  {
+    FORTE_PROF(ctx, "nonfinite");
+    k_nonfinite<<<nb, 256, 0, ctx->stream>>>(x, n, flag);
   FORTE_LAUNCH_CHECK();
+  }
   FORTE_CUDA_TRY(cudaMemcpyAsync(flag_host, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return FORTE_OK;

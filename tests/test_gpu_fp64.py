@@ -205,3 +205,27 @@ def test_not_converged_status():
     E, rn, it = fg.forte_get_roots(prob.ctx, 1)
     assert it == 1 and np.isfinite(E[0])
     prob.close()
+
+
+@pytest.mark.parametrize("n,na,nb,seed,nroots", [(6, 3, 3, 0, 2), (4, 2, 2, 5, 1), (4, 2, 2, 12, 3),
+                                                 (6, 2, 4, 3, 3)])
+def test_davidson_finds_roots_of_both_spin_flip_sectors(n, na, nb, seed, nroots):
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=nroots)
+    prob = fg.CASProblem(n, na, nb, h, eri)
+    E, C, rn, it = prob.davidson(nroots=nroots, tol=1e-10)
+    assert np.abs(E - w).max() < 1e-10
+    prob.close()
+
+
+def test_profile_counts_launches():
+    h, eri = si.integrals(6, 12, seed=0)
+    prob = fg.CASProblem(6, 3, 3, h, eri)
+    C = torch.tensor(si.random_vectors(1, prob.na, prob.nb), device="cuda")
+    fg.forte_profile_enable(prob.ctx, 1)
+    prob.sigma(C)
+    fg.forte_profile_enable(prob.ctx, 0)
+    table = fg.profile_table(prob.ctx)
+    assert table["ab_fp64"][0] == 1 and table["ss_spmm"][0] == 2
+    assert fg.forte_get_counters(prob.ctx)[0] == 1
+    prob.close()

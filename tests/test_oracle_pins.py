@@ -222,3 +222,20 @@ def test_transition_rdm_matches_fock_space():
     bra, ket = fock_ref.embed(n, na, nb, V[0]), fock_ref.embed(n, na, nb, V[1])
     want = np.array([[bra @ (E[p][q] @ ket) for q in range(n)] for p in range(n)])
     assert np.abs(t1 - want).max() < 1e-13
+
+
+def test_splitmix64_published_value():
+    # splitmix64 seeded with 0 gives 0xE220A8397B1DCDAF as its first output
+    # (the reference generator of Steele, Lea & Flood 2014).
+    from oracle.driver import _splitmix64
+    assert int(_splitmix64(np.array([0], dtype=np.uint64))[0]) == 0xE220A8397B1DCDAF
+
+
+@pytest.mark.parametrize("n,na,nb,seed,nroots", [(6, 3, 3, 0, 2), (4, 2, 2, 5, 1), (4, 2, 2, 12, 3)])
+def test_davidson_finds_roots_of_both_spin_flip_sectors(n, na, nb, seed, nroots):
+    # With closed-shell guesses the subspace would stay in one spin-flip sector;
+    # the lowest roots of the determinant space (any S) must all be found.
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w_d, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=nroots)
+    w, V, rn, it = oracle.davidson(n, na, nb, h, eri, nroots=nroots, tol=1e-10)
+    assert np.abs(w - w_d).max() < 1e-10
