@@ -112,13 +112,13 @@ def oracle_sigma_rate(cfg, seconds=10.0, seed=21):
     rng = np.random.default_rng(seed)
     # calibrate: per-call set-up cost + per-row cost from two probe sizes
     t = []
-    for m in (64, 512):
+    for m in (256, 4096):
         probe = rng.integers(0, Na * Nb, size=m)
         t0 = time.perf_counter()
         oracle.sigma(n, na, nb, h, eri, C, rows=probe)
         t.append(time.perf_counter() - t0)
-    per_row = max((t[1] - t[0]) / 448.0, 1e-7)
-    nrows = int(max(512, min(5_000_000, max(seconds - t[0], 0.5) / per_row)))
+    per_row = max((t[1] - t[0]) / 3840.0, t[1] / 4096.0 * 0.5, 1e-7)
+    nrows = int(max(4096, min(5_000_000, max(seconds - t[0], 0.5) / per_row)))
     rows = rng.integers(0, Na * Nb, size=nrows)
     t0 = time.perf_counter()
     oracle.sigma(n, na, nb, h, eri, C, rows=rows)

@@ -171,13 +171,17 @@ typedef struct {
   int n, na, nb;
   long Na, Nb;
   uint32_t *sa, *sb;
-  /* strings within two replacements of each string (including itself) */
+  /* strings within two replacements of each string (including itself), listed
+   * by replacement degree: the string itself, then single, then double
+   * replacements; near_*_end1[i] marks the end of the degree <= 1 part */
   long *near_a_ptr, *near_b_ptr;
   long *near_a, *near_b;
+  long *near_a_end1, *near_b_end1;
 } space_t;
 
-static void build_near(const uint32_t *s, long N, long **ptr, long **idx) {
+static void build_near(const uint32_t *s, long N, long **ptr, long **idx, long **end1) {
   long *p = (long *)malloc(sizeof(long) * (N + 1));
+  long *e1 = (long *)malloc(sizeof(long) * (N > 0 ? N : 1));
   p[0] = 0;
   for (long i = 0; i < N; ++i) {
     long c = 0;
@@ -188,11 +192,15 @@ static void build_near(const uint32_t *s, long N, long **ptr, long **idx) {
   long *x = (long *)malloc(sizeof(long) * (p[N] > 0 ? p[N] : 1));
   for (long i = 0; i < N; ++i) {
     long c = p[i];
-    for (long j = 0; j < N; ++j)
-      if (popc64((uint64_t)(s[i] ^ s[j])) <= 4) x[c++] = j;
+    for (int deg2 = 0; deg2 <= 4; deg2 += 2) {
+      for (long j = 0; j < N; ++j)
+        if (popc64((uint64_t)(s[i] ^ s[j])) == deg2) x[c++] = j;
+      if (deg2 == 2) e1[i] = c;
+    }
   }
   *ptr = p;
   *idx = x;
+  *end1 = e1;
 }
 
 static void space_init(space_t *sp, int n, int na, int nb) {
@@ -203,14 +211,15 @@ static void space_init(space_t *sp, int n, int na, int nb) {
   sp->sb = (uint32_t *)malloc(sizeof(uint32_t) * sp->Nb);
   ora_strings(n, na, sp->sa);
   ora_strings(n, nb, sp->sb);
-  build_near(sp->sa, sp->Na, &sp->near_a_ptr, &sp->near_a);
-  build_near(sp->sb, sp->Nb, &sp->near_b_ptr, &sp->near_b);
+  build_near(sp->sa, sp->Na, &sp->near_a_ptr, &sp->near_a, &sp->near_a_end1);
+  build_near(sp->sb, sp->Nb, &sp->near_b_ptr, &sp->near_b, &sp->near_b_end1);
 }
 
 static void space_free(space_t *sp) {
   free(sp->sa); free(sp->sb);
   free(sp->near_a_ptr); free(sp->near_b_ptr);
   free(sp->near_a); free(sp->near_b);
+  free(sp->near_a_end1); free(sp->near_b_end1);
 }
 
 static uint64_t det_of(const space_t *sp, long ia, long ib) {
@@ -267,7 +276,10 @@ void ora_sigma(int n, int na, int nb, const double *h, const double *eri, int nv
       for (long x = sp.near_a_ptr[ia]; x < sp.near_a_ptr[ia + 1]; ++x) {
         long ja = sp.near_a[x];
         int da = popc64((uint64_t)(sp.sa[ia] ^ sp.sa[ja])) / 2;
-        for (long y = sp.near_b_ptr[ib]; y < sp.near_b_ptr[ib + 1]; ++y) {
+        /* a determinant at most two replacements away: beta part limited to 2 - da */
+        long y_end = (da == 0) ? sp.near_b_ptr[ib + 1]
+                   : (da == 1) ? sp.near_b_end1[ib] : sp.near_b_ptr[ib] + 1;
+        for (long y = sp.near_b_ptr[ib]; y < y_end; ++y) {
           long jb = sp.near_b[y];
           int db = popc64((uint64_t)(sp.sb[ib] ^ sp.sb[jb])) / 2;
           if (da + db > 2) continue;

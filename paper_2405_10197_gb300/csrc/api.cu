@@ -389,6 +389,148 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
   }
 }
 
+// FP64 refinement of Ritz vectors computed with a reduced-precision sigma
+// (step a8).  Outer loop in FP64: Rayleigh-Ritz over V = [X, T] with exact
+// sigma vectors, exact residuals R = H x - theta x.  Corrections T solve the
+// projected equation  P (H~ - theta) P t = -R,  t orthogonal to X, by
+// preconditioned conjugate gradients whose operator H~ is the reduced-precision
+// sigma and whose preconditioner is |theta - H_II|^-1 (Jacobi-Davidson with an
+// inexact inner solve).  Each outer step costs one FP64 sigma per root.
+static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, const double *X0, double *out,
+                     int max_outer, DvResult &res) {
+  cudaStream_t st = ctx->stream;
+  const long long N = ctx->Ndet;
+  const int kmax = std::min(63, nroots * (max_outer + 1));
+  // vectors: V[kmax], HV[kmax], W[nroots] (combine target), PCG: x r z p q
+  size_t nvec = (size_t)2 * kmax + nroots + 5;
+  size_t small_off = sizeof(double) * nvec * N;
+  int rc = ctx->sc_dv.ensure(small_off + sizeof(double) * (64 * 64 + 4 * 66) + 256);
+  if (rc) return rc;
+  double *V = (double *)ctx->sc_dv.ptr;
+  double *HV = V + (size_t)kmax * N;
+  double *W = HV + (size_t)kmax * N;
+  double *px = W + (size_t)nroots * N, *pr = px + N, *pz = pr + N, *pp = pz + N, *pq = pp + N;
+  double *d_coef = (double *)((char *)ctx->sc_dv.ptr + small_off);
+  double *d_a = d_coef + 64 * 64, *d_b = d_a + 66, *d_s = d_b + 66;
+  auto fetch = [&](const double *src, int cnt, double *dst) -> int {
+    FORTE_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+    return FORTE_OK;
+  };
+  // project v onto the complement of V[0..nk): two classical Gram-Schmidt passes
+  auto project = [&](double *v, int nk) -> int {
+    int r2;
+    if ((r2 = vk_multidot(ctx, V, nk, N, v, N, d_a))) return r2;
+    if ((r2 = vk_orth_update(ctx, V, nk, N, d_a, v, v, d_b, N))) return r2;
+    return vk_orth_update(ctx, V, nk, N, d_b, v, v, d_a, N);
+  };
+  FORTE_CUDA_TRY(cudaMemcpyAsync(V, X0, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+  if ((rc = sigma_dispatch(ctx, V, HV, nroots, FORTE_FP64))) return rc;
+  int k = nroots;
+  std::vector<double> G, Gk, w, U, coef, h(66);
+  res.E.assign(nroots, 0.0);
+  res.rn.assign(nroots, INFINITY);
+  res.converged = false;
+  for (int outer = 0;; ++outer) {
+    // Rayleigh-Ritz over V[0..k)
+    G.assign((size_t)k * k, 0.0);
+    for (int j = 0; j < k; ++j) {
+      if ((rc = vk_multidot(ctx, V, k, N, HV + (size_t)j * N, N, d_a))) return rc;
+      if ((rc = fetch(d_a, k, h.data()))) return rc;
+      for (int i = 0; i < k; ++i) G[(size_t)i * k + j] = h[i];
+    }
+    Gk.assign((size_t)k * k, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Gk[(size_t)i * k + j] = 0.5 * (G[(size_t)i * k + j] + G[(size_t)j * k + i]);
+    w.assign(k, 0.0);
+    U.assign((size_t)k * k, 0.0);
+    sym_eig(k, Gk.data(), w.data(), U.data());
+    coef.assign((size_t)k * nroots, 0.0);
+    for (int i = 0; i < k; ++i)
+      for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
+    FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
+    if ((rc = vk_combine(ctx, V, k, N, d_coef, nroots, W, N, N))) return rc;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(V, W, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+    if ((rc = vk_combine(ctx, HV, k, N, d_coef, nroots, W, N, N))) return rc;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(HV, W, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+    k = nroots;
+    // exact residuals R_r = HV_r - theta_r V_r (kept in W)
+    bool all = true;
+    for (int r = 0; r < nroots; ++r) {
+      double *R = W + (size_t)r * N;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(R, HV + (size_t)r * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      if ((rc = vk_axpby(ctx, -w[r], V + (size_t)r * N, 1.0, R, N))) return rc;
+      if ((rc = vk_multidot(ctx, R, 1, N, R, N, d_a))) return rc;
+      if ((rc = fetch(d_a, 1, h.data()))) return rc;
+      res.E[r] = w[r];
+      res.rn[r] = sqrt(std::max(0.0, h[0]));
+      if (!isfinite(h[0]) || !isfinite(w[r])) { set_error("non-finite residual in refinement"); return FORTE_ERR_NUMERIC; }
+      if (!(res.rn[r] < tol)) all = false;
+    }
+    res.iters = outer;
+    if (all || outer >= max_outer) {
+      FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+      res.converged = all;
+      return FORTE_OK;
+    }
+    const int k0 = k;
+    for (int r = 0; r < nroots; ++r) {
+      if (res.rn[r] < tol || k >= kmax) continue;
+      const double theta = w[r];
+      const double bnorm = res.rn[r];
+      // PCG on P (H~ - theta) P x = -R_r, starting from x = 0
+      FORTE_CUDA_TRY(cudaMemsetAsync(px, 0, sizeof(double) * N, st));
+      if ((rc = vk_scale(ctx, pr, W + (size_t)r * N, -1.0, N))) return rc;
+      if ((rc = vk_precond_dot(ctx, pr, theta, ctx->dv_guard, pz, d_s, N))) return rc;
+      if ((rc = fetch(d_s, 1, h.data()))) return rc;
+      double rz = h[0];
+      if ((rc = project(pz, nroots))) return rc;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(pp, pz, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      const int max_inner = 25;
+      for (int it = 0; it < max_inner; ++it) {
+        if ((rc = sigma_dispatch(ctx, pp, pq, 1, inner_mode))) return rc;
+        if ((rc = vk_axpby(ctx, -theta, pp, 1.0, pq, N))) return rc;
+        if ((rc = project(pq, nroots))) return rc;
+        if ((rc = vk_multidot(ctx, pp, 1, N, pq, N, d_s))) return rc;
+        if ((rc = fetch(d_s, 1, h.data()))) return rc;
+        const double pAp = h[0];
+        if (!(pAp > 0.0) || !(rz > 0.0)) break;  // lost positive definiteness
+        const double alpha = rz / pAp;
+        if ((rc = vk_axpby(ctx, alpha, pp, 1.0, px, N))) return rc;
+        if ((rc = vk_axpby(ctx, -alpha, pq, 1.0, pr, N))) return rc;
+        if ((rc = vk_multidot(ctx, pr, 1, N, pr, N, d_s))) return rc;
+        if ((rc = fetch(d_s, 1, h.data()))) return rc;
+        if (sqrt(std::max(0.0, h[0])) < 0.02 * bnorm) break;
+        if ((rc = vk_precond_dot(ctx, pr, theta, ctx->dv_guard, pz, d_s, N))) return rc;
+        if ((rc = fetch(d_s, 1, h.data()))) return rc;
+        const double rz_new = h[0];
+        if ((rc = project(pz, nroots))) return rc;
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        if ((rc = vk_axpby(ctx, 1.0, pz, beta, pp, N))) return rc;
+      }
+      // append the correction: orthonormalise against V[0..k)
+      double *vk = V + (size_t)k * N;
+      FORTE_CUDA_TRY(cudaMemcpyAsync(vk, px, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      FORTE_CUDA_TRY(cudaMemsetAsync(d_a, 0, sizeof(double) * 64, st));
+      if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
+      if ((rc = fetch(d_b + k, 1, h.data()))) return rc;
+      const double n0 = h[0];
+      if ((rc = vk_orth_update(ctx, V, k, N, d_b, vk, vk, d_a, N))) return rc;
+      if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
+      if ((rc = fetch(d_b + k, 1, h.data()))) return rc;
+      if (!(h[0] > 1e-24 * n0) || !(h[0] > 0.0)) continue;
+      if ((rc = vk_scale(ctx, vk, vk, 1.0 / sqrt(h[0]), N))) return rc;
+      ++k;
+    }
+    if (k == k0) {
+      FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+      return FORTE_OK;
+    }
+    if ((rc = sigma_dispatch(ctx, V + (size_t)k0 * N, HV + (size_t)k0 * N, k - k0, FORTE_FP64))) return rc;
+  }
+}
+
 }  // namespace forte
 
 using namespace forte;
@@ -588,15 +730,18 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     if (rc) return rc;
     ctx->dv_iters = res.iters;
   } else {
-    // inner solve with the reduced-precision sigma, then FP64 Davidson started
-    // from its Ritz vectors until the FP64 residual meets tol
-    double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 3e-3 : 1e-4);
+    // Davidson with the reduced-precision sigma down to a residual the mixed
+    // operator can still resolve, then FP64 Jacobi-Davidson refinement whose
+    // inner solves use the mixed sigma
+    double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 1e-2 : 1e-3);
     rc = davidson_run(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                       ctx->d_roots, res);
     if (rc) return rc;
+    if ((rc = mixed_status(ctx))) return rc;
     int it_in = res.iters;
-    rc = davidson_run(ctx, nroots, tol, FORTE_FP64, ctx->d_roots, nroots, ctx->dv_max_iter, ctx->d_roots, res);
+    rc = refine_jd(ctx, nroots, tol, ctx->precision, ctx->d_roots, ctx->d_roots, 30, res);
     if (rc) return rc;
+    if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = it_in + res.iters;
   }
   for (int r = 0; r < nroots; ++r)

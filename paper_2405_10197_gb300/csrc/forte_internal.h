@@ -103,6 +103,11 @@ struct forte_ctx {
   double *d_gpair = nullptr;    // [npair][npair] (pq|rs) over symmetric pairs
   double *d_hdiag = nullptr;    // [Na][Nb]
   float *d_gpair32 = nullptr;   // FP32 copy for the mixed path
+  // tensor-core operands of the integrals, [128][npair] (rows >= npair zero):
+  // gT[rs][pq] = (pq|rs) split into BF16 hi + lo, and rounded to TF32
+  uint16_t *d_gT_hi = nullptr, *d_gT_lo = nullptr;
+  float *d_gT_t32 = nullptr;
+  int *d_err = nullptr;         // device status word of bounded waits (0 = ok)
 
   // Davidson controls and results
   int dv_max_sub = 12, dv_collapse = 2, dv_max_iter = 200;
@@ -151,8 +156,12 @@ int upload_tables(forte_ctx *ctx);
 int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
 int hdiag_build(forte_ctx *ctx);
 
+int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec);
+
 // sigma_mixed.cu
 int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode);
+int mixed_setup(forte_ctx *ctx);
+int mixed_status(forte_ctx *ctx);
 
 // vec_kernels.cu: Davidson building blocks (all FP64, HBM-bound).  Reductions
 // use the context's sc_small buffer for block partials.
@@ -166,6 +175,9 @@ int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k,
 int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c,
                    const double *t_in, double *t_out, double *dots_out, long long n);
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n);
+int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n);
+int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, double *z, double *dot_out,
+                   long long n);
 int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out);
 int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host);
 

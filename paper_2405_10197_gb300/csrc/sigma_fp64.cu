@@ -219,6 +219,45 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
   return FORTE_OK;
 }
 
+// FP32 same-spin term for the reduced-precision path:
+//   S32 = H_aa C32  then  S32 += (H_bb C32^T)^T,  via the scratch buffers T1/T2.
+int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec) {
+  cudaStream_t st = ctx->stream;
+  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
+  {
+    int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NA * nchunk), nvec);
+    {
+      FORTE_PROF(ctx, "ss_spmm_f32");
+      k_ss_spmm<float><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
+                                                    ctx->sd[0].csr_val32, C32, S32, NA, NB, nchunk, ND, 0);
+      FORTE_LAUNCH_CHECK();
+    }
+  }
+  dim3 tb(32, 8);
+  dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
+  {
+    FORTE_PROF(ctx, "transpose_f32");
+    k_transpose<float><<<g1, tb, 0, st>>>(C32, T1, NA, NB, ND, 0);
+    FORTE_LAUNCH_CHECK();
+  }
+  {
+    int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NB * nchunk), nvec);
+    FORTE_PROF(ctx, "ss_spmm_f32");
+    k_ss_spmm<float><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
+                                                  ctx->sd[1].csr_val32, T1, T2, NB, NA, nchunk, ND, 0);
+    FORTE_LAUNCH_CHECK();
+  }
+  dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
+  {
+    FORTE_PROF(ctx, "transpose_f32");
+    k_transpose<float><<<g2, tb, 0, st>>>(T2, S32, NB, NA, ND, 1);
+    FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
 // H_II = H_aa[Ia,Ia] + H_bb[Ib,Ib] + sum_{i in Ia, j in Ib} (ii|jj)
 __global__ void k_hdiag(const double *__restrict__ dA, const double *__restrict__ dB,
                         const double *__restrict__ W, const uint32_t *__restrict__ strB, int n,

@@ -1,13 +1,525 @@
-// Reduced-precision sigma build (TF32 / split BF16 alpha-beta GEMM on the
-// tensor cores, FP32 same-spin terms).
+// Reduced-precision sigma build (steps a5, a6, a8 of the hot path).
+//
+//   same-spin terms: FP32 CSR gathers (the FP64 kernels instantiated in FP32);
+//   alpha-beta term: per alpha string Ia, on the 5th-generation tensor cores
+//       F[rs][Jb] = sum_k  A[rs][k] * B[Jb][k]
+//       A[rs][k]  = s_k (pq_k|rs)            k over L(Ia), the replacements of Ia
+//       B[Jb][k]  = C[J_k][Jb]               gathered rows of C
+//     followed by the signed scatter  sigma[Ia][E_rs Jb] += s F[rs][Jb]  over the
+//     replacement list L(Jb).  A is M=128 (symmetric pairs rs, zero padded),
+//     B is N=128 (a tile of beta strings), K=64 (n_kl <= 64, zero padded).
+//
+// Operands: FORTE_BF16X2 splits x = hi + lo (hi = RNE_bf16(x), lo = RNE_bf16(x - hi))
+// and forms hi*hi + hi*lo + lo*hi (kind::f16, FP32 accumulate); FORTE_TF32 rounds to
+// TF32 with round-to-nearest-even before the MMA (kind::tf32, FP32 accumulate).
+//
+// Kernel structure (one CTA per (Ia, vector), 8 warps):
+//   * A is built once in shared memory (K-major, 128-byte swizzle);
+//   * for each beta tile t, all warps gather and transpose the 56 C rows into the
+//     K-major swizzled B stage t%2; one thread issues the tcgen05.mma chain into the
+//     TMEM accumulator t%2 and commits it to an mbarrier;
+//   * while that MMA runs, the warps drain accumulator (t-1)%2 (tcgen05.ld into a
+//     padded shared tile) and scatter it into the FP32 sigma row held in shared memory.
+// Every mbarrier wait is bounded by a clock budget; on expiry the kernel raises the
+// context's device status word, waits (bounded) for its own MMAs, frees TMEM and exits.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
 #include "forte_internal.h"
 
 namespace forte {
 
+constexpr int MX_THREADS = 256;
+constexpr int MX_TILE_N = 128;
+constexpr int MX_TMEM_COLS = 256;             // two 128-column FP32 accumulators
+constexpr int MX_OFF_B = 32768;               // A: 32 KB
+constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
+constexpr int MX_OFF_F = MX_OFF_B + 2 * MX_STAGE;
+constexpr int MX_FLD = 129;                   // padded row of the F tile (floats)
+constexpr int MX_OFF_ROW = MX_OFF_F + 128 * MX_FLD * 4;
+constexpr unsigned long long MX_WAIT_CYCLES = 4000000000ull;
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the clock budget runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if ((unsigned long long)(clock64() - t0) > MX_WAIT_CYCLES) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+template <int MODE>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  if (MODE == FORTE_BF16X2) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (SBO), descriptor version 1.
+__device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // SBO
+  d |= (uint64_t)1 << 46;              // version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Byte offset of (row, byte-in-row) inside a K-major 128B-swizzled block of rows.
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t b) {
+  return (row >> 3) * 1024u + (row & 7u) * 128u + ((((b >> 4) ^ (row & 7u)) & 7u) << 4) + (b & 15u);
+}
+
+// Round-to-nearest-even of an FP64 value to `drop` fewer mantissa bits
+// (IEEE-754 binary64 layout; drop = 45 gives a BF16 value, 42 a TF32 value).
+__device__ __forceinline__ double rne_drop(double x, int drop) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long lsb = (b >> drop) & 1ull;
+  b += ((1ull << (drop - 1)) - 1ull) + lsb;
+  b &= ~((1ull << drop) - 1ull);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ uint16_t bf16_bits(double exact_bf16) {
+  return __bfloat16_as_ushort(__double2bfloat16(exact_bf16));
+}
+
+// ------------------------------------------------------------ conversion kernels
+
+// C (FP64 [v][NA][NB]) -> C32 (FP32, same layout) and the tensor-core copy in a
+// row-padded layout [v][NA][NBp] (NBp multiple of 16, zero padding).
+template <int MODE>
+__global__ void k_split(const double *__restrict__ C, float *__restrict__ C32, uint16_t *__restrict__ hi,
+                        uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA, long long NB,
+                        long long NBp, int nvec) {
+  const long long total = (long long)nvec * NA * NBp;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i % NBp, row = i / NBp;  // row = v*NA + a
+    double x = 0.0;
+    if (b < NB) {
+      x = C[row * NB + b];
+      C32[row * NB + b] = (float)x;
+    }
+    if (MODE == FORTE_BF16X2) {
+      const double h = rne_drop(x, 45);
+      const double l = rne_drop(x - h, 45);
+      hi[i] = bf16_bits(h);
+      lo[i] = bf16_bits(l);
+    } else {
+      t32[i] = (float)rne_drop(x, 42);
+    }
+  }
+}
+
+// gT[rs][pq] = (pq|rs) for rs < 128 (zero rows beyond npair), split/rounded.
+__global__ void k_split_g(const double *__restrict__ gpair, int npair, uint16_t *__restrict__ hi,
+                          uint16_t *__restrict__ lo, float *__restrict__ t32) {
+  const int total = 128 * npair;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int rs = i / npair, pq = i % npair;
+    const double x = (rs < npair) ? gpair[(size_t)pq * npair + rs] : 0.0;
+    const double h = rne_drop(x, 45);
+    hi[i] = bf16_bits(h);
+    lo[i] = bf16_bits(rne_drop(x - h, 45));
+    t32[i] = (float)rne_drop(x, 42);
+  }
+}
+
+__global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+// ------------------------------------------------------------ the alpha-beta MMA kernel
+
+template <int MODE>
+__global__ void __launch_bounds__(MX_THREADS, 1)
+    k_ab_mma(const Repl *__restrict__ listA, int nkA, const Repl *__restrict__ listB, int nkB, long long NA,
+             long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
+             const float *__restrict__ gT_t32, int npair, const uint16_t *__restrict__ Chi,
+             const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32, const float *__restrict__ Sss,
+             double *__restrict__ S, int *__restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  // the swizzle pattern is a function of the shared-space address: align there
+  uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t *sA = sm;
+  uint8_t *sB = sm + MX_OFF_B;
+  float *sF = (float *)(sm + MX_OFF_F);
+  float *srow = (float *)(sm + MX_OFF_ROW);
+  int *sJ = (int *)(srow + ((NB + 3) & ~3LL));
+  uint8_t *sPair = (uint8_t *)(sJ + 64);
+  int8_t *sSgn = (int8_t *)(sPair + 64);
+  uint64_t *mbar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
+  uint32_t *sTmem = (uint32_t *)(mbar + 2);
+  volatile int *sAbort = (volatile int *)(sTmem + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long Ia = blockIdx.x;
+  const long long v = blockIdx.y;
+  const long long vpad = NA * NBp, v64 = NA * NB;
+
+  if (warp == 0) tmem_alloc(sTmem, MX_TMEM_COLS);
+  if (tid == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    *sAbort = 0;
+    fence_mbar_init();
+  }
+  if (tid < 64) {
+    if (tid < nkA) {
+      const Repl r = listA[Ia * nkA + tid];
+      sJ[tid] = r.J;
+      sPair[tid] = r.pair;
+      sSgn[tid] = r.sgn;
+    } else {
+      sJ[tid] = 0;
+      sPair[tid] = 0;
+      sSgn[tid] = 0;
+    }
+  }
+  for (long long i = tid; i < NB; i += MX_THREADS) srow[i] = 0.f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
+
+  // ---- A operand: A[rs][k] = s_k (pq_k|rs), K-major swizzled
+  if (MODE == FORTE_BF16X2) {
+    const int kp = lane;  // k = 2kp, 2kp+1
+    const int k0 = 2 * kp, k1 = 2 * kp + 1;
+    for (int rs = warp; rs < 128; rs += 8) {
+      uint32_t wh = 0, wl = 0;
+      if (rs < npair) {
+        if (k0 < nkA) {
+          uint16_t h = gT_hi[rs * npair + sPair[k0]], l = gT_lo[rs * npair + sPair[k0]];
+          if (sSgn[k0] < 0) { h ^= 0x8000u; l ^= 0x8000u; }
+          wh |= h;
+          wl |= l;
+        }
+        if (k1 < nkA) {
+          uint16_t h = gT_hi[rs * npair + sPair[k1]], l = gT_lo[rs * npair + sPair[k1]];
+          if (sSgn[k1] < 0) { h ^= 0x8000u; l ^= 0x8000u; }
+          wh |= (uint32_t)h << 16;
+          wl |= (uint32_t)l << 16;
+        }
+      }
+      *(uint32_t *)(sA + swz(rs, 4 * kp)) = wh;
+      *(uint32_t *)(sA + 16384 + swz(rs, 4 * kp)) = wl;
+    }
+  } else {
+    for (int idx = tid; idx < 128 * 64; idx += MX_THREADS) {
+      const int k = idx & 63, rs = idx >> 6;
+      float val = 0.f;
+      if (rs < npair && k < nkA) {
+        val = gT_t32[rs * npair + sPair[k]];
+        if (sSgn[k] < 0) val = -val;
+      }
+      *(float *)(sA + (k >> 5) * 16384 + swz(rs, (k & 31) * 4)) = val;
+    }
+  }
+
+  const int ntiles = (int)((NB + MX_TILE_N - 1) / MX_TILE_N);
+  const uint32_t idesc = (MODE == FORTE_BF16X2)
+                             ? ((1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
+                             : ((1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24));
+  int issued = 0;  // tiles whose MMA chain was committed (thread 0's view)
+
+  for (int t = 0; t <= ntiles; ++t) {
+    // ---- produce B stage t%2: B[j][k] = C[J_k][j0 + j]
+    if (t < ntiles) {
+      uint8_t *stg = sB + (t & 1) * MX_STAGE;
+      const long long col = (long long)t * MX_TILE_N + 16 * warp;  // this warp's 16 columns
+      if (MODE == FORTE_BF16X2) {
+        const int k0 = 2 * lane, k1 = 2 * lane + 1;
+        for (int part = 0; part < 2; ++part) {
+          const uint16_t *src = part ? Clo : Chi;
+          uint8_t *dst = stg + part * 16384;
+          uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+          if (col < NBp) {
+            if (k0 < nkA) {
+              const uint4 *p = (const uint4 *)(src + v * vpad + (long long)sJ[k0] * NBp + col);
+              a0 = __ldg(p);
+              a1 = __ldg(p + 1);
+            }
+            if (k1 < nkA) {
+              const uint4 *p = (const uint4 *)(src + v * vpad + (long long)sJ[k1] * NBp + col);
+              b0 = __ldg(p);
+              b1 = __ldg(p + 1);
+            }
+          }
+          const uint32_t ea[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const uint32_t eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
+            const uint32_t hi16 = (i & 1) ? (eb[i >> 1] >> 16) : (eb[i >> 1] & 0xFFFFu);
+            *(uint32_t *)(dst + swz(16 * warp + i, 4 * lane)) = lo16 | (hi16 << 16);
+          }
+        }
+      } else {
+        for (int atom = 0; atom < 2; ++atom) {
+          const int k = 32 * atom + lane;
+          float4 q[4] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0),
+                         make_float4(0, 0, 0, 0)};
+          if (col < NBp && k < nkA) {
+            const float4 *p = (const float4 *)(Ct32 + v * vpad + (long long)sJ[k] * NBp + col);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) q[i] = __ldg(p + i);
+          }
+          uint8_t *dst = stg + atom * 16384;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            *(float *)(dst + swz(16 * warp + 4 * i + 0, 4 * lane)) = q[i].x;
+            *(float *)(dst + swz(16 * warp + 4 * i + 1, 4 * lane)) = q[i].y;
+            *(float *)(dst + swz(16 * warp + 4 * i + 2, 4 * lane)) = q[i].z;
+            *(float *)(dst + swz(16 * warp + 4 * i + 3, 4 * lane)) = q[i].w;
+          }
+        }
+      }
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    if (*sAbort) break;
+    tc_fence_after();
+    // ---- issue the MMA chain of tile t
+    if (t < ntiles && tid == 0) {
+      const uint32_t d = tmem + (uint32_t)((t & 1) * MX_TILE_N);
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + (t & 1) * MX_STAGE);
+      if (MODE == FORTE_BF16X2) {
+        // hi*hi + hi*lo + lo*hi
+        const uint32_t aoff[3] = {0u, 0u, 16384u}, boff[3] = {0u, 16384u, 0u};
+        for (int p = 0; p < 3; ++p)
+          for (int ks = 0; ks < 4; ++ks)
+            mma_issue<MODE>(d, desc_kmajor_sw128(a0 + aoff[p] + 32u * ks), desc_kmajor_sw128(b0 + boff[p] + 32u * ks),
+                            idesc, (p | ks) != 0);
+      } else {
+        for (int ks = 0; ks < 8; ++ks) {
+          const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
+          mma_issue<MODE>(d, desc_kmajor_sw128(a0 + off), desc_kmajor_sw128(b0 + off), idesc, ks != 0);
+        }
+      }
+      mma_commit(&mbar[t & 1]);
+      issued = t + 1;
+    }
+    // ---- drain tile t-1 and scatter it
+    if (t > 0) {
+      const int tp = t - 1, b = tp & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&mbar[b], (uint32_t)((tp >> 1) & 1)));
+      if (!ok) {
+        *sAbort = 1;
+        atomicExch(err, 1);
+      }
+      tc_fence_after();
+      if (ok) {
+        const int lg = warp & 3, half = warp >> 2;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * 64 + c * 32);
+          tmem_ld32(taddr, r);
+          float *frow = sF + (lg * 32 + lane) * MX_FLD + half * 64 + c * 32;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) frow[i] = __uint_as_float(r[i]);
+        }
+      }
+      tc_fence_before();
+      __syncthreads();
+      if (*sAbort) break;
+      const long long j0 = (long long)tp * MX_TILE_N;
+      const int tj = (int)min((long long)MX_TILE_N, NB - j0);
+      const int npairs = tj * nkB;
+      const Repl *lb = listB + j0 * nkB;
+      for (int w = tid; w < npairs; w += MX_THREADS) {
+        const int j = w / nkB;
+        const Repl r = lb[w];
+        const float f = sF[r.pair * MX_FLD + j];
+        atomicAdd(&srow[r.J], r.sgn > 0 ? f : -f);
+      }
+    }
+  }
+  __syncthreads();
+  if (*sAbort) {
+    // wait (bounded) for this CTA's MMAs still in flight before TMEM is released
+    if (tid == 0) {
+      for (int tt = (issued >= 2 ? issued - 2 : 0); tt < issued; ++tt) mbar_wait(&mbar[tt & 1], (uint32_t)((tt >> 1) & 1));
+    }
+  } else {
+    const float *ss = Sss + v * v64 + Ia * NB;
+    double *out = S + v * v64 + Ia * NB;
+    for (long long i = tid; i < NB; i += MX_THREADS) out[i] = (double)ss[i] + (double)srow[i];
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, MX_TMEM_COLS);
+}
+
+// ------------------------------------------------------------ host side
+
+static size_t mx_smem_bytes(long long NB) {
+  return 1024 + MX_OFF_ROW + sizeof(float) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 + 16 + 16 + 64;
+}
+
+int mixed_setup(forte_ctx *ctx) {
+  const int np = ctx->npair;
+  if (ctx->d_gT_hi) return FORTE_OK;
+  size_t cnt = (size_t)128 * np;
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_hi, cnt * sizeof(uint16_t)));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_lo, cnt * sizeof(uint16_t)));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_t32, cnt * sizeof(float)));
+  if (!ctx->d_err) {
+    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_err, sizeof(int)));
+    FORTE_CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  }
+  k_split_g<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_gpair, np, ctx->d_gT_hi, ctx->d_gT_lo,
+                                                                    ctx->d_gT_t32);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+
 int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
-  (void)ctx; (void)C; (void)S; (void)nvec;
-  set_error("precision mode %d is not available in this build", mode);
-  return FORTE_ERR_ARG;
+  if (mode != FORTE_BF16X2 && mode != FORTE_TF32) {
+    set_error("unknown precision mode %d", mode);
+    return FORTE_ERR_ARG;
+  }
+  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[1].nk;
+  if (nkA > 64 || ctx->npair > 128) {
+    set_error("reduced-precision sigma supports n_kl <= 64 and n(n+1)/2 <= 128 (norb <= 15); use FORTE_FP64");
+    return FORTE_ERR_ARG;
+  }
+  int rc = mixed_setup(ctx);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
+  const long long NBp = (NB + 15) & ~15LL;
+  const size_t nf = (size_t)nvec * ND, np = (size_t)nvec * NA * NBp;
+  // scratch: C32, T1, T2, S32 (FP32, ND each) + tensor-core copy (2 x u16 or 1 x f32 per padded element)
+  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + 1024;
+  if ((rc = ctx->sc_mixed.ensure(bytes))) return rc;
+  float *C32 = (float *)ctx->sc_mixed.ptr;
+  float *T1 = C32 + nf, *T2 = T1 + nf, *S32 = T2 + nf;
+  uint8_t *tc = (uint8_t *)(((uintptr_t)(S32 + nf) + 255) & ~(uintptr_t)255);
+  uint16_t *Chi = (uint16_t *)tc, *Clo = Chi + np;
+  float *Ct32 = (float *)tc;
+  {
+    unsigned nb = (unsigned)std::min<long long>(((long long)np + 255) / 256, 152LL * 32);
+    FORTE_PROF(ctx, "split");
+    if (mode == FORTE_BF16X2)
+      k_split<FORTE_BF16X2><<<nb, 256, 0, st>>>(C, C32, Chi, Clo, nullptr, NA, NB, NBp, nvec);
+    else
+      k_split<FORTE_TF32><<<nb, 256, 0, st>>>(C, C32, nullptr, nullptr, Ct32, NA, NB, NBp, nvec);
+    FORTE_LAUNCH_CHECK();
+  }
+  if ((rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec))) return rc;
+  if (nkA > 0 && nkB > 0) {
+    const size_t smem = mx_smem_bytes(NB);
+    if (smem > 232448) {
+      set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
+      return FORTE_ERR_ARG;
+    }
+    dim3 grid((unsigned)NA, (unsigned)nvec);
+    if (mode == FORTE_BF16X2) {
+      FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FORTE_PROF(ctx, "ab_mma_bf16x2");
+      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NA, NB, NBp,
+                                                             ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
+                                                             Chi, Clo, Ct32, S32, S, ctx->d_err);
+      FORTE_LAUNCH_CHECK();
+    } else {
+      FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FORTE_PROF(ctx, "ab_mma_tf32");
+      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NA, NB, NBp,
+                                                           ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
+                                                           Chi, Clo, Ct32, S32, S, ctx->d_err);
+      FORTE_LAUNCH_CHECK();
+    }
+  } else {
+    FORTE_PROF(ctx, "f32_to_f64");
+    k_f32_to_f64<<<(unsigned)std::min<size_t>((nf + 255) / 256, 152 * 32), 256, 0, st>>>(S32, S, (long long)nf);
+    FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
+// Device status of bounded waits: FORTE_OK, or FORTE_ERR_TIMEOUT (and reset).
+int mixed_status(forte_ctx *ctx) {
+  if (!ctx->d_err) return FORTE_OK;
+  int h = 0;
+  FORTE_CUDA_TRY(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (h) {
+    cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
+    set_error("a bounded device wait in the alpha-beta MMA kernel expired");
+    return FORTE_ERR_TIMEOUT;
+  }
+  return FORTE_OK;
 }
 
 }  // namespace forte

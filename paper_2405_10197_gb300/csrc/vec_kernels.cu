@@ -169,6 +169,36 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const double *__rest
   if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nn;
 }
 
+// y = a x + b y
+__global__ void k_axpby(double a, const double *__restrict__ x, double b, double *__restrict__ y, long long n) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    y[j] = a * x[j] + b * y[j];
+}
+
+// z = r / |theta - hdiag| with the magnitude clamped below at guard; part[block] = r . z
+__global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__restrict__ r, double theta,
+                                                            const double *__restrict__ hd, double guard,
+                                                            double *__restrict__ z, long long n,
+                                                            double *__restrict__ part) {
+  __shared__ double red[32];
+  const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
+  double acc = 0.0;
+#pragma unroll 4
+  for (int e = 0; e < VK_EPT; ++e) {
+    long long j = base + (long long)e * VK_THREADS;
+    if (j >= n) break;
+    double den = fabs(theta - hd[j]);
+    if (den < guard) den = guard;
+    const double rv = r[j];
+    const double zv = rv / den;
+    z[j] = zv;
+    acc += rv * zv;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
 __global__ void k_scale(double *__restrict__ x, const double *__restrict__ src, double alpha, long long n) {
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x)
@@ -303,6 +333,35 @@ int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long lo
     FORTE_PROF(ctx, "scale");
     k_scale<<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
   FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
+int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n) {
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  {
+    FORTE_PROF(ctx, "axpby");
+    k_axpby<<<nb, 256, 0, ctx->stream>>>(a, x, b, y, n);
+    FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
+int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, double *z, double *dot_out,
+                   long long n) {
+  unsigned nb = vk_blocks(n);
+  double *part;
+  int rc = part_buffer(ctx, nb, &part);
+  if (rc) return rc;
+  {
+    FORTE_PROF(ctx, "precond_dot");
+    k_precond_dot<<<nb, VK_THREADS, 0, ctx->stream>>>(r, theta, ctx->d_hdiag, guard, z, n, part);
+    FORTE_LAUNCH_CHECK();
+  }
+  {
+    FORTE_PROF(ctx, "sum_partials");
+    k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, dot_out);
+    FORTE_LAUNCH_CHECK();
   }
   return FORTE_OK;
 }

@@ -1,0 +1,53 @@
+"""Write the stored expected values of the GPU tests using the CPU oracle only.
+
+Run from the repository root:  python tests/golden/make_golden.py [name ...]
+Each entry is computed by oracle.davidson (direct Slater-Condon sigma) on the
+seeded synthetic inputs of synth_inputs; nothing here touches the CUDA path.
+Residual tolerance 1e-6 bounds each energy error by |r|^2/gap < 1e-10 Eh for
+the gaps of these problems (the gap is recorded)."""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+import synth_inputs as si  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+JOBS = {
+    "cas1212_seed1_4roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=1, nroots=4),
+    "hubbard12_t1_U4": dict(kind="hubbard", norb=12, nalpha=6, nbeta=6, t=1.0, U=4.0, nroots=2),
+    "cas1212_seed3_3roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=3, nroots=3),
+    "cas1010_seed5_3roots": dict(kind="integrals", norb=10, nalpha=5, nbeta=5, n_l=20, seed=5, nroots=3),
+}
+
+
+def run(name):
+    job = JOBS[name]
+    if job["kind"] == "hubbard":
+        h, eri = si.hubbard_ring(job["norb"], job["t"], job["U"])
+    else:
+        h, eri = si.integrals(job["norb"], job["n_l"], job["seed"])
+    nr = job["nroots"]
+    t0 = time.time()
+    # one extra root so that the gap above the last requested root is known
+    E, V, rn, it = oracle.davidson(job["norb"], job["nalpha"], job["nbeta"], h, eri, nroots=nr + 1,
+                                   tol=1e-6, max_iter=400)
+    out = dict(job)
+    out.update(energies=[float(e) for e in E[:nr]], next_energy=float(E[nr]),
+               residuals=[float(r) for r in rn], iterations=int(it), seconds=time.time() - t0,
+               threads=oracle.num_threads(), source="oracle.davidson (tests/golden/make_golden.py)")
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, out["energies"], it, out["seconds"])
+
+
+if __name__ == "__main__":
+    for name in (sys.argv[1:] or list(JOBS)):
+        run(name)
