@@ -69,6 +69,12 @@ struct SpinDev {
   uint32_t *str = nullptr;
   double *diag = nullptr;
   int *dense = nullptr;   // [N][n*n]: (J << 1) | (sgn < 0), or -1 when E_pq|I> = 0
+  uint32_t *list4 = nullptr;  // [N][nk]: J | pair << 16 | (sgn < 0) << 31
+  // [128][Np] (Np = N rounded up to 16): scatter target of symmetric pair rs
+  // applied to string J: I | (sgn < 0) << 14 for E_rs J = sgn I (r != s: the
+  // one of E_rs, E_sr that does not vanish), 0xFFFF when neither applies
+  uint16_t *tabT = nullptr;
+  long long Np = 0;
 };
 
 // Scratch buffer that grows on demand and is owned by the context.
@@ -108,6 +114,7 @@ struct forte_ctx {
   uint16_t *d_gT_hi = nullptr, *d_gT_lo = nullptr;
   float *d_gT_t32 = nullptr;
   int *d_err = nullptr;         // device status word of bounded waits (0 = ok)
+  float gmax = 0.f;             // max |(pq|rs)| (bounds the alpha-beta fixed-point scale)
 
   // Davidson controls and results
   int dv_max_sub = 12, dv_collapse = 2, dv_max_iter = 200;

@@ -210,6 +210,24 @@ int upload_tables(forte_ctx *ctx) {
         dense[(size_t)I * n2 + r.pq] = (r.J << 1) | (r.sgn < 0 ? 1 : 0);
       }
     if ((st = upload(&D.dense, dense.data(), dense.size()))) return st;
+    if (H.N <= 65536) {
+      std::vector<uint32_t> l4(H.list.size());
+      for (size_t i = 0; i < l4.size(); ++i) {
+        const Repl &r = H.list[i];
+        l4[i] = (uint32_t)r.J | ((uint32_t)r.pair << 16) | (r.sgn < 0 ? 0x80000000u : 0u);
+      }
+      if ((st = upload(&D.list4, l4.data(), l4.size()))) return st;
+    }
+    if (H.N < 16384 && ctx->npair <= 128) {
+      D.Np = (H.N + 15) & ~15LL;
+      std::vector<uint16_t> tab((size_t)128 * D.Np, 0xFFFFu);
+      for (long long J = 0; J < H.N; ++J)
+        for (int e = 0; e < H.nk; ++e) {
+          const Repl &r = H.list[(size_t)J * H.nk + e];
+          tab[(size_t)r.pair * D.Np + J] = (uint16_t)(r.J | (r.sgn < 0 ? 0x4000 : 0));
+        }
+      if ((st = upload(&D.tabT, tab.data(), tab.size()))) return st;
+    }
   }
   if (ctx->same_strings) ctx->sd[1] = ctx->sd[0];
   // (pq|rs) over symmetric pairs

@@ -30,14 +30,12 @@
 
 namespace forte {
 
-constexpr int MX_THREADS = 256;
+constexpr int MX_THREADS = 512;
 constexpr int MX_TILE_N = 128;
 constexpr int MX_TMEM_COLS = 256;             // two 128-column FP32 accumulators
 constexpr int MX_OFF_B = 32768;               // A: 32 KB
 constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
-constexpr int MX_OFF_F = MX_OFF_B + 2 * MX_STAGE;
-constexpr int MX_FLD = 129;                   // padded row of the F tile (floats)
-constexpr int MX_OFF_ROW = MX_OFF_F + 128 * MX_FLD * 4;
+constexpr int MX_OFF_ROW = MX_OFF_B + 2 * MX_STAGE;
 constexpr unsigned long long MX_WAIT_CYCLES = 4000000000ull;
 
 // ------------------------------------------------------------ PTX helpers
@@ -151,28 +149,45 @@ __device__ __forceinline__ uint16_t bf16_bits(double exact_bf16) {
 // ------------------------------------------------------------ conversion kernels
 
 // C (FP64 [v][NA][NB]) -> C32 (FP32, same layout) and the tensor-core copy in a
-// row-padded layout [v][NA][NBp] (NBp multiple of 16, zero padding).
+// row-padded layout [v][NA][NBp] (NBp multiple of 16, zero padding); also the
+// per-vector bound cmax_bits[v] = bits of max |C| (non-negative floats order as
+// their bit patterns).  grid.y = vector.
 template <int MODE>
 __global__ void k_split(const double *__restrict__ C, float *__restrict__ C32, uint16_t *__restrict__ hi,
                         uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA, long long NB,
-                        long long NBp, int nvec) {
-  const long long total = (long long)nvec * NA * NBp;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+                        long long NBp, unsigned *__restrict__ cmax_bits) {
+  __shared__ unsigned red[32];
+  const long long v = blockIdx.y;
+  const long long per = NA * NBp;
+  const double *Cv = C + v * NA * NB;
+  float *C32v = C32 + v * NA * NB;
+  unsigned mx = 0u;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long b = i % NBp, row = i / NBp;  // row = v*NA + a
+    const long long b = i % NBp, row = i / NBp;
     double x = 0.0;
     if (b < NB) {
-      x = C[row * NB + b];
-      C32[row * NB + b] = (float)x;
+      x = Cv[row * NB + b];
+      C32v[row * NB + b] = (float)x;
     }
+    mx = max(mx, __float_as_uint(fabsf((float)x)));
     if (MODE == FORTE_BF16X2) {
       const double h = rne_drop(x, 45);
       const double l = rne_drop(x - h, 45);
-      hi[i] = bf16_bits(h);
-      lo[i] = bf16_bits(l);
+      hi[v * per + i] = bf16_bits(h);
+      lo[v * per + i] = bf16_bits(l);
     } else {
-      t32[i] = (float)rne_drop(x, 42);
+      t32[v * per + i] = (float)rne_drop(x, 42);
     }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, red[w]);
+    atomicMax(cmax_bits + v, m);
   }
 }
 
@@ -197,22 +212,32 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 }
 
 // ------------------------------------------------------------ the alpha-beta MMA kernel
+//
+// Scatter accumulation.  Every contribution f is turned into the fixed-point
+// integer V = rint(f 2^S) with |V| < 2^44 (S per vector from the bound
+// |f| <= n_kl * max|g| * max|C|, with 2% slack for the operand splits) and
+// added exactly with two 32-bit integer reductions into shared memory:
+// hi = V >> 20 (signed) and lo = V mod 2^20 (unsigned).  At most n_kl <= 64
+// contributions reach one output, so neither word can overflow.  Integer
+// shared-memory reductions are native on the SM, FP32 ones are not; the sum is
+// exact and independent of the order of the atomics.
 
 template <int MODE>
 __global__ void __launch_bounds__(MX_THREADS, 1)
-    k_ab_mma(const Repl *__restrict__ listA, int nkA, const Repl *__restrict__ listB, int nkB, long long NA,
+    k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabT, long long Npt, long long NA,
              long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
-             const float *__restrict__ gT_t32, int npair, const uint16_t *__restrict__ Chi,
-             const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32, const float *__restrict__ Sss,
-             double *__restrict__ S, int *__restrict__ err) {
+             const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
+             const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
+             const float *__restrict__ Sss, double *__restrict__ S, int *__restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   // the swizzle pattern is a function of the shared-space address: align there
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sA = sm;
   uint8_t *sB = sm + MX_OFF_B;
-  float *sF = (float *)(sm + MX_OFF_F);
-  float *srow = (float *)(sm + MX_OFF_ROW);
-  int *sJ = (int *)(srow + ((NB + 3) & ~3LL));
+  const long long NB4 = (NB + 3) & ~3LL;
+  int *acc_hi = (int *)(sm + MX_OFF_ROW);
+  unsigned *acc_lo = (unsigned *)(acc_hi + NB4);
+  int *sJ = (int *)(acc_lo + NB4);
   uint8_t *sPair = (uint8_t *)(sJ + 64);
   int8_t *sSgn = (int8_t *)(sPair + 64);
   uint64_t *mbar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
@@ -223,6 +248,13 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   const long long Ia = blockIdx.x;
   const long long v = blockIdx.y;
   const long long vpad = NA * NBp, v64 = NA * NB;
+
+  // fixed-point exponent of this vector
+  const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
+  int eb = 0;
+  if (bound > 0.f) frexpf(bound, &eb);
+  const int Sx = (bound > 0.f) ? min(100, 44 - eb) : 0;
+  const float fscale = ldexpf(1.f, Sx);
 
   if (warp == 0) tmem_alloc(sTmem, MX_TMEM_COLS);
   if (tid == 0) {
@@ -243,7 +275,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       sSgn[tid] = 0;
     }
   }
-  for (long long i = tid; i < NB; i += MX_THREADS) srow[i] = 0.f;
+  for (long long i = tid; i < NB; i += MX_THREADS) {
+    acc_hi[i] = 0;
+    acc_lo[i] = 0u;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -253,7 +288,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   if (MODE == FORTE_BF16X2) {
     const int kp = lane;  // k = 2kp, 2kp+1
     const int k0 = 2 * kp, k1 = 2 * kp + 1;
-    for (int rs = warp; rs < 128; rs += 8) {
+    for (int rs = warp; rs < 128; rs += MX_THREADS / 32) {
       uint32_t wh = 0, wl = 0;
       if (rs < npair) {
         if (k0 < nkA) {
@@ -290,59 +325,67 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
                              : ((1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24));
   int issued = 0;  // tiles whose MMA chain was committed (thread 0's view)
 
-  for (int t = 0; t <= ntiles; ++t) {
-    // ---- produce B stage t%2: B[j][k] = C[J_k][j0 + j]
-    if (t < ntiles) {
-      uint8_t *stg = sB + (t & 1) * MX_STAGE;
-      const long long col = (long long)t * MX_TILE_N + 16 * warp;  // this warp's 16 columns
-      if (MODE == FORTE_BF16X2) {
-        const int k0 = 2 * lane, k1 = 2 * lane + 1;
-        for (int part = 0; part < 2; ++part) {
-          const uint16_t *src = part ? Clo : Chi;
-          uint8_t *dst = stg + part * 16384;
-          uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-          if (col < NBp) {
-            if (k0 < nkA) {
-              const uint4 *p = (const uint4 *)(src + v * vpad + (long long)sJ[k0] * NBp + col);
-              a0 = __ldg(p);
-              a1 = __ldg(p + 1);
-            }
-            if (k1 < nkA) {
-              const uint4 *p = (const uint4 *)(src + v * vpad + (long long)sJ[k1] * NBp + col);
-              b0 = __ldg(p);
-              b1 = __ldg(p + 1);
-            }
-          }
-          const uint32_t ea[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const uint32_t eb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  // Register staging of the next tile's gathered C rows: each of the 16 warps
+  // owns 8 beta columns; each lane one K pair (BF16) or one K index per atom (TF32).
+  uint4 pf[4];
+  auto load_B = [&](int t) {
+    const long long col = (long long)t * MX_TILE_N + 8 * warp;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
-            const uint32_t hi16 = (i & 1) ? (eb[i >> 1] >> 16) : (eb[i >> 1] & 0xFFFFu);
-            *(uint32_t *)(dst + swz(16 * warp + i, 4 * lane)) = lo16 | (hi16 << 16);
-          }
+    for (int i = 0; i < 4; ++i) pf[i] = make_uint4(0, 0, 0, 0);
+    if (col >= NBp) return;
+    if (MODE == FORTE_BF16X2) {
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const uint16_t *src = (part ? Clo : Chi) + v * vpad + col;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int k = 2 * lane + r;
+          if (k < nkA) pf[part * 2 + r] = __ldg((const uint4 *)(src + (long long)sJ[k] * NBp));
         }
-      } else {
-        for (int atom = 0; atom < 2; ++atom) {
-          const int k = 32 * atom + lane;
-          float4 q[4] = {make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0), make_float4(0, 0, 0, 0),
-                         make_float4(0, 0, 0, 0)};
-          if (col < NBp && k < nkA) {
-            const float4 *p = (const float4 *)(Ct32 + v * vpad + (long long)sJ[k] * NBp + col);
+      }
+    } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) q[i] = __ldg(p + i);
-          }
-          uint8_t *dst = stg + atom * 16384;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            *(float *)(dst + swz(16 * warp + 4 * i + 0, 4 * lane)) = q[i].x;
-            *(float *)(dst + swz(16 * warp + 4 * i + 1, 4 * lane)) = q[i].y;
-            *(float *)(dst + swz(16 * warp + 4 * i + 2, 4 * lane)) = q[i].z;
-            *(float *)(dst + swz(16 * warp + 4 * i + 3, 4 * lane)) = q[i].w;
-          }
+      for (int atom = 0; atom < 2; ++atom) {
+        const int k = 32 * atom + lane;
+        if (k < nkA) {
+          const uint4 *p = (const uint4 *)(Ct32 + v * vpad + (long long)sJ[k] * NBp + col);
+          pf[atom * 2 + 0] = __ldg(p);
+          pf[atom * 2 + 1] = __ldg(p + 1);
         }
       }
     }
+  };
+  // B[j][k] = C[J_k][j0 + j] written K-major into stage t%2
+  auto store_B = [&](int t) {
+    uint8_t *stg = sB + (t & 1) * MX_STAGE;
+    if (MODE == FORTE_BF16X2) {
+#pragma unroll
+      for (int part = 0; part < 2; ++part) {
+        const uint32_t ea[4] = {pf[part * 2].x, pf[part * 2].y, pf[part * 2].z, pf[part * 2].w};
+        const uint32_t eb[4] = {pf[part * 2 + 1].x, pf[part * 2 + 1].y, pf[part * 2 + 1].z, pf[part * 2 + 1].w};
+        uint8_t *dst = stg + part * 16384;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
+          const uint32_t hi16 = (i & 1) ? (eb[i >> 1] >> 16) : (eb[i >> 1] & 0xFFFFu);
+          *(uint32_t *)(dst + swz(8 * warp + i, 4 * lane)) = lo16 | (hi16 << 16);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int atom = 0; atom < 2; ++atom) {
+        uint8_t *dst = stg + atom * 16384;
+        const uint32_t e[8] = {pf[atom * 2].x, pf[atom * 2].y, pf[atom * 2].z, pf[atom * 2].w,
+                               pf[atom * 2 + 1].x, pf[atom * 2 + 1].y, pf[atom * 2 + 1].z, pf[atom * 2 + 1].w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) *(uint32_t *)(dst + swz(8 * warp + i, 4 * lane)) = e[i];
+      }
+    }
+  };
+
+  if (ntiles > 0) load_B(0);
+  for (int t = 0; t <= ntiles; ++t) {
+    if (t < ntiles) store_B(t);
     fence_proxy_async();
     tc_fence_before();
     __syncthreads();
@@ -368,9 +411,21 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       mma_commit(&mbar[t & 1]);
       issued = t + 1;
     }
-    // ---- drain tile t-1 and scatter it
+    // ---- prefetch the next tile's rows while this one multiplies
+    if (t + 1 < ntiles) load_B(t + 1);
+    // ---- drain tile t-1 straight from TMEM and scatter it: thread = row rs of
+    //      the accumulator, 32 beta columns; targets from the pair table
     if (t > 0) {
       const int tp = t - 1, b = tp & 1;
+      const int lg = warp & 3, quarter = warp >> 2;
+      const int rs = lg * 32 + lane;
+      const long long cbase = (long long)tp * MX_TILE_N + quarter * 32;
+      uint4 tg[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        if (rs < npair && cbase + 8 * q < Npt) tg[q] = __ldg((const uint4 *)(tabT + (long long)rs * Npt + cbase) + q);
+      }
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&mbar[b], (uint32_t)((tp >> 1) & 1)));
       if (!ok) {
         *sAbort = 1;
@@ -378,30 +433,26 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       }
       tc_fence_after();
       if (ok) {
-        const int lg = warp & 3, half = warp >> 2;
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + quarter * 32);
+        tmem_ld32(taddr, r);
+        if (rs < npair) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          uint32_t r[32];
-          const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * 64 + c * 32);
-          tmem_ld32(taddr, r);
-          float *frow = sF + (lg * 32 + lane) * MX_FLD + half * 64 + c * 32;
-#pragma unroll
-          for (int i = 0; i < 32; ++i) frow[i] = __uint_as_float(r[i]);
+          for (int i = 0; i < 32; ++i) {
+            const uint4 q = tg[i >> 3];
+            const int w2 = (i & 7) >> 1;
+            const uint32_t w = w2 == 0 ? q.x : w2 == 1 ? q.y : w2 == 2 ? q.z : q.w;
+            const uint32_t e = (i & 1) ? (w >> 16) : (w & 0xFFFFu);
+            if (e != 0xFFFFu) {
+              const float f = __uint_as_float(r[i]) * fscale;
+              const long long V = __float2ll_rn((e & 0x4000u) ? -f : f);
+              atomicAdd(&acc_hi[e & 0x3FFFu], (int)(V >> 20));
+              atomicAdd(&acc_lo[e & 0x3FFFu], (unsigned)(V & 0xFFFFFLL));
+            }
+          }
         }
       }
       tc_fence_before();
-      __syncthreads();
-      if (*sAbort) break;
-      const long long j0 = (long long)tp * MX_TILE_N;
-      const int tj = (int)min((long long)MX_TILE_N, NB - j0);
-      const int npairs = tj * nkB;
-      const Repl *lb = listB + j0 * nkB;
-      for (int w = tid; w < npairs; w += MX_THREADS) {
-        const int j = w / nkB;
-        const Repl r = lb[w];
-        const float f = sF[r.pair * MX_FLD + j];
-        atomicAdd(&srow[r.J], r.sgn > 0 ? f : -f);
-      }
     }
   }
   __syncthreads();
@@ -413,7 +464,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   } else {
     const float *ss = Sss + v * v64 + Ia * NB;
     double *out = S + v * v64 + Ia * NB;
-    for (long long i = tid; i < NB; i += MX_THREADS) out[i] = (double)ss[i] + (double)srow[i];
+    for (long long i = tid; i < NB; i += MX_THREADS) {
+      const long long tot = (long long)acc_hi[i] * 1048576LL + (long long)acc_lo[i];
+      out[i] = (double)ss[i] + ldexp((double)tot, -Sx);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -424,12 +478,15 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // ------------------------------------------------------------ host side
 
 static size_t mx_smem_bytes(long long NB) {
-  return 1024 + MX_OFF_ROW + sizeof(float) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 + 16 + 16 + 64;
+  return 1024 + MX_OFF_ROW + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 + 16 + 16 + 64;
 }
 
 int mixed_setup(forte_ctx *ctx) {
   const int np = ctx->npair;
   if (ctx->d_gT_hi) return FORTE_OK;
+  double gm = 0.0;
+  for (double x : ctx->eri) gm = std::max(gm, fabs(x));
+  ctx->gmax = (float)(gm * (1.0 + 1e-6));
   size_t cnt = (size_t)128 * np;
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_hi, cnt * sizeof(uint16_t)));
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_lo, cnt * sizeof(uint16_t)));
@@ -460,21 +517,25 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
   const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
   const long long NBp = (NB + 15) & ~15LL;
   const size_t nf = (size_t)nvec * ND, np = (size_t)nvec * NA * NBp;
-  // scratch: C32, T1, T2, S32 (FP32, ND each) + tensor-core copy (2 x u16 or 1 x f32 per padded element)
-  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + 1024;
+  // scratch: C32, T1, T2, S32 (FP32, ND each) + tensor-core copy (2 x u16 or 1 x f32 per
+  // padded element) + per-vector max |C|
+  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + 1024 + 256 + sizeof(unsigned) * nvec;
   if ((rc = ctx->sc_mixed.ensure(bytes))) return rc;
   float *C32 = (float *)ctx->sc_mixed.ptr;
   float *T1 = C32 + nf, *T2 = T1 + nf, *S32 = T2 + nf;
   uint8_t *tc = (uint8_t *)(((uintptr_t)(S32 + nf) + 255) & ~(uintptr_t)255);
   uint16_t *Chi = (uint16_t *)tc, *Clo = Chi + np;
   float *Ct32 = (float *)tc;
+  unsigned *cmax = (unsigned *)(((uintptr_t)(tc + np * 4) + 255) & ~(uintptr_t)255);
+  FORTE_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned) * nvec, st));
   {
-    unsigned nb = (unsigned)std::min<long long>(((long long)np + 255) / 256, 152LL * 32);
+    const long long per = NA * NBp;
+    dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
     if (mode == FORTE_BF16X2)
-      k_split<FORTE_BF16X2><<<nb, 256, 0, st>>>(C, C32, Chi, Clo, nullptr, NA, NB, NBp, nvec);
+      k_split<FORTE_BF16X2><<<grid, 256, 0, st>>>(C, C32, Chi, Clo, nullptr, NA, NB, NBp, cmax);
     else
-      k_split<FORTE_TF32><<<nb, 256, 0, st>>>(C, C32, nullptr, nullptr, Ct32, NA, NB, NBp, nvec);
+      k_split<FORTE_TF32><<<grid, 256, 0, st>>>(C, C32, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
     FORTE_LAUNCH_CHECK();
   }
   if ((rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec))) return rc;
@@ -488,16 +549,16 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
     if (mode == FORTE_BF16X2) {
       FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
-      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NA, NB, NBp,
+      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabT, ctx->sd[1].Np, NA, NB, NBp,
                                                              ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                             Chi, Clo, Ct32, S32, S, ctx->d_err);
+                                                             ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
       FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       FORTE_PROF(ctx, "ab_mma_tf32");
-      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NA, NB, NBp,
+      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabT, ctx->sd[1].Np, NA, NB, NBp,
                                                            ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                           Chi, Clo, Ct32, S32, S, ctx->d_err);
+                                                           ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     }
   } else {
