@@ -607,7 +607,7 @@ void forte_destroy(forte_ctx *ctx) {
   for (int s = 0; s < nsp; ++s) {
     SpinDev &D = ctx->sd[s];
     cudaFree(D.list); cudaFree(D.csr_ptr); cudaFree(D.csr_col); cudaFree(D.csr_val);
-    cudaFree(D.csr_val32); cudaFree(D.str); cudaFree(D.diag); cudaFree(D.dense); cudaFree(D.list4); cudaFree(D.tabT);
+    cudaFree(D.csr_val32); cudaFree(D.str); cudaFree(D.diag); cudaFree(D.dense); cudaFree(D.list4); cudaFree(D.tabJ);
   }
   cudaFree(ctx->d_gpair); cudaFree(ctx->d_gpair32); cudaFree(ctx->d_hdiag);
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);

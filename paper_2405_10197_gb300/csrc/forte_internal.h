@@ -70,11 +70,10 @@ struct SpinDev {
   double *diag = nullptr;
   int *dense = nullptr;   // [N][n*n]: (J << 1) | (sgn < 0), or -1 when E_pq|I> = 0
   uint32_t *list4 = nullptr;  // [N][nk]: J | pair << 16 | (sgn < 0) << 31
-  // [128][Np] (Np = N rounded up to 16): scatter target of symmetric pair rs
-  // applied to string J: I | (sgn < 0) << 14 for E_rs J = sgn I (r != s: the
-  // one of E_rs, E_sr that does not vanish), 0xFFFF when neither applies
-  uint16_t *tabT = nullptr;
-  long long Np = 0;
+  // [N][128]: scatter target of symmetric pair rs applied to string J:
+  // I | (sgn < 0) << 14 for E_rs J = sgn I (r != s: the one of E_rs, E_sr that
+  // does not vanish), 0xFFFF when neither applies or rs >= n(n+1)/2
+  uint16_t *tabJ = nullptr;
 };
 
 // Scratch buffer that grows on demand and is owned by the context.

@@ -219,14 +219,13 @@ int upload_tables(forte_ctx *ctx) {
       if ((st = upload(&D.list4, l4.data(), l4.size()))) return st;
     }
     if (H.N < 16384 && ctx->npair <= 128) {
-      D.Np = (H.N + 15) & ~15LL;
-      std::vector<uint16_t> tab((size_t)128 * D.Np, 0xFFFFu);
+      std::vector<uint16_t> tab((size_t)H.N * 128, 0xFFFFu);
       for (long long J = 0; J < H.N; ++J)
         for (int e = 0; e < H.nk; ++e) {
           const Repl &r = H.list[(size_t)J * H.nk + e];
-          tab[(size_t)r.pair * D.Np + J] = (uint16_t)(r.J | (r.sgn < 0 ? 0x4000 : 0));
+          tab[(size_t)J * 128 + r.pair] = (uint16_t)(r.J | (r.sgn < 0 ? 0x4000 : 0));
         }
-      if ((st = upload(&D.tabT, tab.data(), tab.size()))) return st;
+      if ((st = upload(&D.tabJ, tab.data(), tab.size()))) return st;
     }
   }
   if (ctx->same_strings) ctx->sd[1] = ctx->sd[0];

@@ -13,15 +13,20 @@
 // and forms hi*hi + hi*lo + lo*hi (kind::f16, FP32 accumulate); FORTE_TF32 rounds to
 // TF32 with round-to-nearest-even before the MMA (kind::tf32, FP32 accumulate).
 //
-// Kernel structure (one CTA per (Ia, vector), 8 warps):
-//   * A is built once in shared memory (K-major, 128-byte swizzle);
-//   * for each beta tile t, all warps gather and transpose the 56 C rows into the
-//     K-major swizzled B stage t%2; one thread issues the tcgen05.mma chain into the
-//     TMEM accumulator t%2 and commits it to an mbarrier;
-//   * while that MMA runs, the warps drain accumulator (t-1)%2 (tcgen05.ld into a
-//     padded shared tile) and scatter it into the FP32 sigma row held in shared memory.
+// Kernel structure (one CTA per (Ia, vector), 16 warps, warp-specialised):
+//   * all warps build A once in shared memory (K-major, 128-byte swizzle);
+//   * warps 0-3 (producers) gather the n_kl C rows of each 128-column beta tile,
+//     transpose them into a K-major swizzled stage of a 3-deep ring and arrive on
+//     its `full` mbarrier;
+//   * one thread of warp 4 issues the tcgen05.mma chain of the tile into one of
+//     four 128-column TMEM accumulators and commits to the stage's `empty` and the
+//     accumulator's `tfull` mbarriers;
+//   * warps 8-15 (epilogue) read the accumulator with tcgen05.ld, convert each
+//     valid element to fixed point and add it to the sigma row in shared memory
+//     with integer reductions, then arrive on the accumulator's `tempty` mbarrier.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel raises the
-// context's device status word, waits (bounded) for its own MMAs, frees TMEM and exits.
+// context's device status word, the other roles stop, the MMA thread waits
+// (bounded) for its own MMAs, TMEM is freed and the CTA exits.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -32,10 +37,8 @@ namespace forte {
 
 constexpr int MX_THREADS = 512;
 constexpr int MX_TILE_N = 128;
-constexpr int MX_TMEM_COLS = 256;             // two 128-column FP32 accumulators
 constexpr int MX_OFF_B = 32768;               // A: 32 KB
 constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
-constexpr int MX_OFF_ROW = MX_OFF_B + 2 * MX_STAGE;
 constexpr unsigned long long MX_WAIT_CYCLES = 4000000000ull;
 
 // ------------------------------------------------------------ PTX helpers
@@ -214,17 +217,36 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 // ------------------------------------------------------------ the alpha-beta MMA kernel
 //
 // Scatter accumulation.  Every contribution f is turned into the fixed-point
-// integer V = rint(f 2^S) with |V| < 2^44 (S per vector from the bound
-// |f| <= n_kl * max|g| * max|C|, with 2% slack for the operand splits) and
-// added exactly with two 32-bit integer reductions into shared memory:
-// hi = V >> 20 (signed) and lo = V mod 2^20 (unsigned).  At most n_kl <= 64
-// contributions reach one output, so neither word can overflow.  Integer
+// value V = f 2^S with |V| < 2^41 (S per vector from the bound
+// |f| <= n_kl * max|g| * max|C|, with 2% slack for the operand splits), split
+// as V = hi 2^20 + lo with hi = rint(V 2^-20) and lo = rint(V - hi 2^20) in
+// [-2^19, 2^19], and added with two 32-bit integer reductions into shared
+// memory.  At most n_kl <= 64 contributions reach one output, so neither word
+// can overflow.  Integer
 // shared-memory reductions are native on the SM, FP32 ones are not; the sum is
 // exact and independent of the order of the atomics.
 
+constexpr int WS_STAGES = 3;                              // B operand ring
+constexpr int WS_ACC = 4;                                 // TMEM accumulators of 128 columns
+constexpr int WS_OFF_ACC = MX_OFF_B + WS_STAGES * MX_STAGE;
+// warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 8-15 epilogue
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait that also gives up once another warp raised the abort flag.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if ((unsigned long long)(clock64() - t0) > MX_WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(MX_THREADS, 1)
-    k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabT, long long Npt, long long NA,
+    k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabJ, int nN, long long NA,
              long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
@@ -235,13 +257,14 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   uint8_t *sA = sm;
   uint8_t *sB = sm + MX_OFF_B;
   const long long NB4 = (NB + 3) & ~3LL;
-  int *acc_hi = (int *)(sm + MX_OFF_ROW);
-  unsigned *acc_lo = (unsigned *)(acc_hi + NB4);
+  int *acc_hi = (int *)(sm + WS_OFF_ACC);
+  int *acc_lo = acc_hi + NB4;
   int *sJ = (int *)(acc_lo + NB4);
   uint8_t *sPair = (uint8_t *)(sJ + 64);
   int8_t *sSgn = (int8_t *)(sPair + 64);
-  uint64_t *mbar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
-  uint32_t *sTmem = (uint32_t *)(mbar + 2);
+  uint64_t *bar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
+  uint64_t *full = bar, *empty = bar + WS_STAGES, *tfull = bar + 2 * WS_STAGES, *tempty = tfull + WS_ACC;
+  uint32_t *sTmem = (uint32_t *)(tempty + WS_ACC);
   volatile int *sAbort = (volatile int *)(sTmem + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -253,13 +276,19 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
   int eb = 0;
   if (bound > 0.f) frexpf(bound, &eb);
-  const int Sx = (bound > 0.f) ? min(100, 44 - eb) : 0;
+  const int Sx = (bound > 0.f) ? min(100, 41 - eb) : 0;
   const float fscale = ldexpf(1.f, Sx);
 
-  if (warp == 0) tmem_alloc(sTmem, MX_TMEM_COLS);
+  if (warp == 4) tmem_alloc(sTmem, WS_ACC * MX_TILE_N);
   if (tid == 0) {
-    mbar_init(&mbar[0], 1);
-    mbar_init(&mbar[1], 1);
+    for (int i = 0; i < WS_STAGES; ++i) {
+      mbar_init(&full[i], 4);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < WS_ACC; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 8);
+    }
     *sAbort = 0;
     fence_mbar_init();
   }
@@ -277,12 +306,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   }
   for (long long i = tid; i < NB; i += MX_THREADS) {
     acc_hi[i] = 0;
-    acc_lo[i] = 0u;
+    acc_lo[i] = 0;
   }
-  tc_fence_before();
   __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *sTmem;
 
   // ---- A operand: A[rs][k] = s_k (pq_k|rs), K-major swizzled
   if (MODE == FORTE_BF16X2) {
@@ -318,148 +344,187 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       *(float *)(sA + (k >> 5) * 16384 + swz(rs, (k & 31) * 4)) = val;
     }
   }
-
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *sTmem;
   const int ntiles = (int)((NB + MX_TILE_N - 1) / MX_TILE_N);
-  const uint32_t idesc = (MODE == FORTE_BF16X2)
-                             ? ((1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24))
-                             : ((1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24));
-  int issued = 0;  // tiles whose MMA chain was committed (thread 0's view)
+  int issued = 0;  // tiles committed by the MMA thread
 
-  // Register staging of the next tile's gathered C rows: each of the 16 warps
-  // owns 8 beta columns; each lane one K pair (BF16) or one K index per atom (TF32).
-  uint4 pf[4];
-  auto load_B = [&](int t) {
-    const long long col = (long long)t * MX_TILE_N + 8 * warp;
+  if (warp < 4) {
+    // ================= producers: B[j][k] = C[J_k][j0 + j], warp p owns columns 32p..32p+31
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = t % WS_STAGES, u = t / WS_STAGES;
+      const long long col0 = (long long)t * MX_TILE_N + 32 * warp;
+      uint4 g[16];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) pf[i] = make_uint4(0, 0, 0, 0);
-    if (col >= NBp) return;
-    if (MODE == FORTE_BF16X2) {
-#pragma unroll
-      for (int part = 0; part < 2; ++part) {
-        const uint16_t *src = (part ? Clo : Chi) + v * vpad + col;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int k = 2 * lane + r;
-          if (k < nkA) pf[part * 2 + r] = __ldg((const uint4 *)(src + (long long)sJ[k] * NBp));
-        }
-      }
-    } else {
-#pragma unroll
-      for (int atom = 0; atom < 2; ++atom) {
-        const int k = 32 * atom + lane;
-        if (k < nkA) {
-          const uint4 *p = (const uint4 *)(Ct32 + v * vpad + (long long)sJ[k] * NBp + col);
-          pf[atom * 2 + 0] = __ldg(p);
-          pf[atom * 2 + 1] = __ldg(p + 1);
-        }
-      }
-    }
-  };
-  // B[j][k] = C[J_k][j0 + j] written K-major into stage t%2
-  auto store_B = [&](int t) {
-    uint8_t *stg = sB + (t & 1) * MX_STAGE;
-    if (MODE == FORTE_BF16X2) {
-#pragma unroll
-      for (int part = 0; part < 2; ++part) {
-        const uint32_t ea[4] = {pf[part * 2].x, pf[part * 2].y, pf[part * 2].z, pf[part * 2].w};
-        const uint32_t eb[4] = {pf[part * 2 + 1].x, pf[part * 2 + 1].y, pf[part * 2 + 1].z, pf[part * 2 + 1].w};
-        uint8_t *dst = stg + part * 16384;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
-          const uint32_t hi16 = (i & 1) ? (eb[i >> 1] >> 16) : (eb[i >> 1] & 0xFFFFu);
-          *(uint32_t *)(dst + swz(8 * warp + i, 4 * lane)) = lo16 | (hi16 << 16);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int atom = 0; atom < 2; ++atom) {
-        uint8_t *dst = stg + atom * 16384;
-        const uint32_t e[8] = {pf[atom * 2].x, pf[atom * 2].y, pf[atom * 2].z, pf[atom * 2].w,
-                               pf[atom * 2 + 1].x, pf[atom * 2 + 1].y, pf[atom * 2 + 1].z, pf[atom * 2 + 1].w};
-#pragma unroll
-        for (int i = 0; i < 8; ++i) *(uint32_t *)(dst + swz(8 * warp + i, 4 * lane)) = e[i];
-      }
-    }
-  };
-
-  if (ntiles > 0) load_B(0);
-  for (int t = 0; t <= ntiles; ++t) {
-    if (t < ntiles) store_B(t);
-    fence_proxy_async();
-    tc_fence_before();
-    __syncthreads();
-    if (*sAbort) break;
-    tc_fence_after();
-    // ---- issue the MMA chain of tile t
-    if (t < ntiles && tid == 0) {
-      const uint32_t d = tmem + (uint32_t)((t & 1) * MX_TILE_N);
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + (t & 1) * MX_STAGE);
+      for (int i = 0; i < 16; ++i) g[i] = make_uint4(0, 0, 0, 0);
       if (MODE == FORTE_BF16X2) {
-        // hi*hi + hi*lo + lo*hi
-        const uint32_t aoff[3] = {0u, 0u, 16384u}, boff[3] = {0u, 16384u, 0u};
-        for (int p = 0; p < 3; ++p)
-          for (int ks = 0; ks < 4; ++ks)
-            mma_issue<MODE>(d, desc_kmajor_sw128(a0 + aoff[p] + 32u * ks), desc_kmajor_sw128(b0 + boff[p] + 32u * ks),
-                            idesc, (p | ks) != 0);
+#pragma unroll
+        for (int part = 0; part < 2; ++part)
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int k = 2 * lane + r;
+            if (k < nkA) {
+              const uint16_t *src = (part ? Clo : Chi) + v * vpad + (long long)sJ[k] * NBp;
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (col0 + 8 * c < NBp) g[part * 8 + r * 4 + c] = __ldg((const uint4 *)(src + col0 + 8 * c));
+            }
+          }
       } else {
-        for (int ks = 0; ks < 8; ++ks) {
-          const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
-          mma_issue<MODE>(d, desc_kmajor_sw128(a0 + off), desc_kmajor_sw128(b0 + off), idesc, ks != 0);
+#pragma unroll
+        for (int atom = 0; atom < 2; ++atom) {
+          const int k = 32 * atom + lane;
+          if (k < nkA) {
+            const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBp;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (col0 + 4 * c < NBp) g[atom * 8 + c] = __ldg((const uint4 *)(src + col0 + 4 * c));
+          }
         }
       }
-      mma_commit(&mbar[t & 1]);
-      issued = t + 1;
-    }
-    // ---- prefetch the next tile's rows while this one multiplies
-    if (t + 1 < ntiles) load_B(t + 1);
-    // ---- drain tile t-1 straight from TMEM and scatter it: thread = row rs of
-    //      the accumulator, 32 beta columns; targets from the pair table
-    if (t > 0) {
-      const int tp = t - 1, b = tp & 1;
-      const int lg = warp & 3, quarter = warp >> 2;
-      const int rs = lg * 32 + lane;
-      const long long cbase = (long long)tp * MX_TILE_N + quarter * 32;
-      uint4 tg[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        if (rs < npair && cbase + 8 * q < Npt) tg[q] = __ldg((const uint4 *)(tabT + (long long)rs * Npt + cbase) + q);
-      }
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&mbar[b], (uint32_t)((tp >> 1) & 1)));
-      if (!ok) {
+      if (t >= WS_STAGES && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
         *sAbort = 1;
         atomicExch(err, 1);
+        break;
+      }
+      uint8_t *stg = sB + s * MX_STAGE;
+      if (MODE == FORTE_BF16X2) {
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          uint8_t *dst = stg + part * 16384;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 qa = g[part * 8 + c], qb = g[part * 8 + 4 + c];
+            const uint32_t ea[4] = {qa.x, qa.y, qa.z, qa.w}, ebb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
+              const uint32_t hi16 = (i & 1) ? (ebb[i >> 1] >> 16) : (ebb[i >> 1] & 0xFFFFu);
+              *(uint32_t *)(dst + swz(32 * warp + 8 * c + i, 4 * lane)) = lo16 | (hi16 << 16);
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int atom = 0; atom < 2; ++atom) {
+          uint8_t *dst = stg + atom * 16384;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint4 q = g[atom * 8 + c];
+            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 0, 4 * lane)) = q.x;
+            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 1, 4 * lane)) = q.y;
+            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 2, 4 * lane)) = q.z;
+            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 3, 4 * lane)) = q.w;
+          }
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+    }
+  } else if (warp == 4) {
+    // ================= MMA issuer
+    if (lane == 0) {
+      // D[j][rs] = sum_k B[j][k] A[rs][k]: the gathered C tile is the M=128 operand,
+      // the integral block the N=nN operand, so TMEM lanes are beta strings
+      const uint32_t idesc = (MODE == FORTE_BF16X2)
+                                 ? ((1u << 4) | (1u << 7) | (1u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24))
+                                 : ((1u << 4) | (2u << 7) | (2u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24));
+      const uint32_t a0 = smem_u32(sA);
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % WS_STAGES, u = t / WS_STAGES, b = t % WS_ACC, ub = t / WS_ACC;
+        if (!mbar_wait_ab(&full[s], (uint32_t)(u & 1), sAbort) ||
+            (t >= WS_ACC && !mbar_wait_ab(&tempty[b], (uint32_t)((ub - 1) & 1), sAbort))) {
+          *sAbort = 1;
+          atomicExch(err, 1);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * MX_TILE_N);
+        const uint32_t b0 = smem_u32(sB + s * MX_STAGE);
+        if (MODE == FORTE_BF16X2) {
+          // hi*hi + lo*hi + hi*lo  (C part first, integral part second)
+          const uint32_t coff[3] = {0u, 16384u, 0u}, goff[3] = {0u, 0u, 16384u};
+          for (int p = 0; p < 3; ++p)
+            for (int ks = 0; ks < 4; ++ks)
+              mma_issue<MODE>(d, desc_kmajor_sw128(b0 + coff[p] + 32u * ks),
+                              desc_kmajor_sw128(a0 + goff[p] + 32u * ks), idesc, (p | ks) != 0);
+        } else {
+          for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
+            mma_issue<MODE>(d, desc_kmajor_sw128(b0 + off), desc_kmajor_sw128(a0 + off), idesc, ks != 0);
+          }
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&tfull[b]);
+        issued = t + 1;
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 8) {
+    // ================= epilogue: thread = beta string j0 + j (accumulator lane),
+    //                   64 pairs rs per warp half (accumulator columns)
+    const int e = warp - 8, lg = e & 3, half = e >> 2;
+    const int j = lg * 32 + lane;
+    for (int t = 0; t < ntiles; ++t) {
+      const int b = t % WS_ACC, ub = t / WS_ACC;
+      const long long Jb = (long long)t * MX_TILE_N + j;
+      uint4 tg[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+      if (Jb < NB) {
+        const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * 64);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tg[q] = __ldg(row + q);
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
+        *sAbort = 1;
+        atomicExch(err, 1);
+        break;
       }
       tc_fence_after();
-      if (ok) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + quarter * 32);
-        tmem_ld32(taddr, r);
-        if (rs < npair) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const uint4 q = tg[i >> 3];
-            const int w2 = (i & 7) >> 1;
-            const uint32_t w = w2 == 0 ? q.x : w2 == 1 ? q.y : w2 == 2 ? q.z : q.w;
-            const uint32_t e = (i & 1) ? (w >> 16) : (w & 0xFFFFu);
-            if (e != 0xFFFFu) {
-              const float f = __uint_as_float(r[i]) * fscale;
-              const long long V = __float2ll_rn((e & 0x4000u) ? -f : f);
-              atomicAdd(&acc_hi[e & 0x3FFFu], (int)(V >> 20));
-              atomicAdd(&acc_lo[e & 0x3FFFu], (unsigned)(V & 0xFFFFFLL));
-            }
+      for (int c = 0; c < 2; ++c) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * 64 + c * 32);
+        tmem_ld32(taddr, r);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = c * 32 + i;
+          const uint4 q = tg[col >> 3];
+          const int w2 = (col & 7) >> 1;
+          const uint32_t w = w2 == 0 ? q.x : w2 == 1 ? q.y : w2 == 2 ? q.z : q.w;
+          const uint32_t en = (col & 1) ? (w >> 16) : (w & 0xFFFFu);
+          // fs = f 2^S = hi 2^20 + lo with hi, lo rounded to integers by adding
+          // 1.5 2^23 (exact for |x| < 2^22): no conversion instructions, which
+          // would run on the narrow FP64/conversion pipe.  The reductions are
+          // skipped (not predicated) for invalid entries: issued reduction
+          // instructions, even predicated off, are what limits this loop.
+          if (en != 0xFFFFu) {
+            const float fsv = __uint_as_float(r[i]) * fscale;
+            const float fs = (en & 0x4000u) ? -fsv : fsv;
+            const float th = fmaf(fs, 0x1p-20f, 12582912.0f);
+            const float hf = th - 12582912.0f;
+            const float tl = fmaf(-hf, 0x1p20f, fs) + 12582912.0f;
+            atomicAdd(&acc_hi[en & 0x3FFFu], __float_as_int(th) - 0x4B400000);
+            atomicAdd(&acc_lo[en & 0x3FFFu], __float_as_int(tl) - 0x4B400000);
           }
         }
       }
       tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
     }
   }
   __syncthreads();
   if (*sAbort) {
     // wait (bounded) for this CTA's MMAs still in flight before TMEM is released
-    if (tid == 0) {
-      for (int tt = (issued >= 2 ? issued - 2 : 0); tt < issued; ++tt) mbar_wait(&mbar[tt & 1], (uint32_t)((tt >> 1) & 1));
+    if (warp == 4 && lane == 0) {
+      for (int tt = (issued >= WS_ACC ? issued - WS_ACC : 0); tt < issued; ++tt)
+        mbar_wait(&tfull[tt % WS_ACC], (uint32_t)((tt / WS_ACC) & 1));
     }
   } else {
     const float *ss = Sss + v * v64 + Ia * NB;
@@ -472,13 +537,14 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, MX_TMEM_COLS);
+  if (warp == 4) tmem_dealloc(tmem, WS_ACC * MX_TILE_N);
 }
 
 // ------------------------------------------------------------ host side
 
 static size_t mx_smem_bytes(long long NB) {
-  return 1024 + MX_OFF_ROW + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 + 16 + 16 + 64;
+  return 1024 + WS_OFF_ACC + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 +
+         8 * (2 * WS_STAGES + 2 * WS_ACC) + 16 + 64;
 }
 
 int mixed_setup(forte_ctx *ctx) {
@@ -540,6 +606,7 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
   }
   if ((rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec))) return rc;
   if (nkA > 0 && nkB > 0) {
+    const int nN = ctx->npair <= 112 ? 112 : 128;
     const size_t smem = mx_smem_bytes(NB);
     if (smem > 232448) {
       set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
@@ -549,14 +616,14 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
     if (mode == FORTE_BF16X2) {
       FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
-      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabT, ctx->sd[1].Np, NA, NB, NBp,
+      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                              ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
                                                              ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
       FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       FORTE_PROF(ctx, "ab_mma_tf32");
-      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabT, ctx->sd[1].Np, NA, NB, NBp,
+      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                            ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
                                                            ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
