@@ -148,6 +148,24 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2);
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
 
+/* FP64 sigma = H C that allocates no device memory (the paper has no
+ * counterpart; this is a service for callers of the library).  It is meant for
+ * callers that cannot call cudaMalloc during the call: code whose device memory
+ * belongs to another allocator (a framework's caching allocator, a fixed memory
+ * budget) and latency-critical loops where cudaMalloc/cudaFree, which may
+ * synchronise the device, are not acceptable.  forte_sigma grows scratch
+ * buffers on demand; this entry point instead uses a fixed 16 MB array built
+ * into the library, which every GPU that loads the library holds until exit.
+ *   C, S, nvec  as for forte_sigma (device pointers, FP64, S overwritten,
+ *               S must not overlap C); always FP64 whatever forte_set_precision says
+ * Limit: nvec * N_alpha * N_beta <= 1,048,576 (e.g. one CAS(12,12) vector);
+ * larger requests return FORTE_ERR_ARG without touching the GPU.
+ * The first call on a device looks up the array's device address (with that
+ * device made current); make that first call before any stream capture.  All
+ * calls share the array, so calls that overlap on the GPU (for instance on two
+ * streams at once) race.  Asynchronous on the context stream. */
+int forte_sigma_fp64_noalloc(forte_ctx *ctx, const double *C, double *S, int nvec);
+
 /* Kernel tracing.  While enabled, every kernel this library launches for the
  * context is bracketed by CUDA events on the context stream (on = 1 also
  * clears earlier records; on = 0 stops recording and keeps them). */

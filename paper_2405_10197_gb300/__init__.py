@@ -74,6 +74,7 @@ def library():
         "forte_set_guess": [vp, vp, i],
         "forte_rdms": [vp, vp, vp, vp],
         "forte_tdm1": [vp, vp, vp, vp],
+        "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -173,6 +174,14 @@ def forte_get_hdiag(ctx, out):
 def forte_sigma(ctx, C, S, nvec):
     na, nb = forte_get_sizes(ctx)
     return _check(library().forte_sigma(ctx, _ptr(C, nvec * na * nb), _ptr(S, nvec * na * nb), int(nvec)))
+
+
+def forte_sigma_fp64_noalloc(ctx, C, S, nvec):
+    """FP64 sigma through the entry point that allocates no device memory
+    (scratch is a fixed array inside the library; nvec * N_det <= 2^20)."""
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_sigma_fp64_noalloc(ctx, _ptr(C, nvec * na * nb), _ptr(S, nvec * na * nb),
+                                                     int(nvec)))
 
 
 def forte_davidson(ctx, nroots, tol, allow_not_converged=False):

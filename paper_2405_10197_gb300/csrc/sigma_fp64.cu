@@ -219,6 +219,57 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
   return FORTE_OK;
 }
 
+// The FP64 sigma with caller-provided scratch T1, T2 (each >= nvec * Ndet
+// doubles): the same kernels as sigma_fp64, no allocation and no tracing.
+int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, double *T1, double *T2) {
+  cudaStream_t st = ctx->stream;
+  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
+  {
+    int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NA * nchunk), nvec);
+    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
+                                                   ctx->sd[0].csr_val, C, S, NA, NB, nchunk, ND, 0);
+    FORTE_LAUNCH_CHECK();
+  }
+  {
+    dim3 tb(32, 8);
+    dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
+    k_transpose<double><<<g1, tb, 0, st>>>(C, T1, NA, NB, ND, 0);
+    FORTE_LAUNCH_CHECK();
+    int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NB * nchunk), nvec);
+    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
+                                                   ctx->sd[1].csr_val, T1, T2, NB, NA, nchunk, ND, 0);
+    FORTE_LAUNCH_CHECK();
+    dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
+    k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
+    FORTE_LAUNCH_CHECK();
+  }
+  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
+  if (nkA > 0 && nkB > 0) {
+    if (nkA > 80) {
+      set_error("alpha replacement list too long (%d)", nkA);
+      return FORTE_ERR_ARG;
+    }
+    int TJ = 64;
+    size_t smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
+    while (smem > 220 * 1024 && TJ > 8) {
+      TJ /= 2;
+      smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
+    }
+    if (smem > 220 * 1024) {
+      set_error("alpha-beta FP64 kernel needs %zu bytes of shared memory", smem);
+      return FORTE_ERR_ARG;
+    }
+    FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((unsigned)NA, nvec);
+    k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB, ctx->d_gpair,
+                                              ctx->npair, C, S, ND, TJ);
+    FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
 // FP32 same-spin term for the reduced-precision path:
 //   S32 = H_aa C32  then  S32 += (H_bb C32^T)^T,  via the scratch buffers T1/T2.
 int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec) {
