@@ -1,16 +1,19 @@
-"""Benchmark of the CASCI hot path on CAS(14,14) (7 alpha + 7 beta electrons in
-14 orbitals, 11,778,624 determinants; seeded synthetic integrals, 28 factors,
-seed 2).
+"""Benchmark of the CASCI hot path on CAS(14,14): 7 alpha + 7 beta electrons in
+14 orbitals, 11,778,624 determinants, seeded synthetic integrals (28 factors,
+seed 2), inputs resident in HBM (vectors of 94 MB, subspace > 2 GB: larger than
+the 129 MB L2, so no flush is needed between steps).
 
-One step = one Davidson-Liu solve of the lowest root from the unit-vector
-guess to an FP64 residual that puts the energy within 1e-8 Eh (tol 1e-5,
-energy error ~ |r|^2 / gap), followed by the spin-free 1- and 2-RDMs of the
-root.  ``value`` is the sigma throughput of the whole step: determinants x
-sigma vectors built during the step / step time (det/s).
+One step = a Davidson-Liu solve of the lowest root from the standard guess to an
+FP64 residual of `--tol` (default 1e-5, energy error <= |r|^2/gap ~ 1e-9 Eh), in
+the chosen sigma precision (default split BF16 with FP64 Jacobi-Davidson
+refinement), followed by the spin-free 1- and 2-RDMs of the root.
+``value`` = determinants x sigma vectors built in the timed steps / time (det/s).
+The same run also times one FP64 solve of the same problem, which gives the
+reference energy and the "mixed vs FP64 time-to-1e-8 Eh" comparison.
 
-Contract: prints one JSON line (rank 0).  --impl reference times the CPU
-oracle (the plain Slater-Condon program under oracle/) on a bounded sample of
-output determinants of the same workload.
+--impl reference times the CPU oracle (the plain Slater-Condon program under
+oracle/) on a bounded random sample of output determinants of the same workload.
+Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
@@ -30,16 +33,17 @@ sys.path.insert(0, ROOT)
 import synth_inputs as si  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FALLBACK_HBM_GBS = 6800.0
-FALLBACK_BF16_TFLOPS = 1900.0
-# FP64 FMA pipe: nominal GB300 FP64 rate (1.25 TFLOP/s = 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+# FP64 pipe: nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz); a DFMA
+# probe measured 1.197 TF/s.  FP32 pipe: 152 x 128 FFMA/clk x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 80.5
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio
 
-WORKLOADS = {
-    "cas1414": si.CAS1414,
-    "cas1212": si.CAS1212,
-    "cas88": si.CAS88,
-}
+WORKLOADS = {"cas1414": si.CAS1414, "cas1212": si.CAS1212, "cas88": si.CAS88}
+WORKLOAD_NAMES = {"cas1414": "CAS(14,14) 7a+7b in 14 orbitals, 11,778,624 determinants, seed 2, 28 factors",
+                  "cas1212": "CAS(12,12) 6a+6b in 12 orbitals, 853,776 determinants, seed 1, 24 factors",
+                  "cas88": "CAS(8,8) 4a+4b in 8 orbitals, 4,900 determinants, seed 0, 16 factors"}
 METRIC = "CASCI H*C det/s and Davidson time-to-1e-8 Eh, CAS(14,14), mixed vs FP64, 1 GB300"
 
 
@@ -47,10 +51,18 @@ def peaks():
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)
-        return p.get("hbm_gbs", FALLBACK_HBM_GBS), p.get("bf16_tflops", FALLBACK_BF16_TFLOPS), \
-            p.get("bf16_tflops_sustained", FALLBACK_BF16_TFLOPS), "measured"
+        return (p.get("hbm_gbs", 6800.0), p.get("bf16_tflops", 1900.0), p.get("bf16_tflops_sustained", 1700.0),
+                "measured")
     except Exception:
-        return FALLBACK_HBM_GBS, FALLBACK_BF16_TFLOPS, 1700.0, "fallback"
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def traffic_table():
+    try:
+        with open(TRAFFIC_FILE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
 
 
 # ------------------------------------------------------------------ clocks
@@ -91,33 +103,38 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        smax = [v for v in (num(r[2]) for r in rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
-        return {"sm_mhz": float(np.median(sm)) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
 
 
-# ------------------------------------------------------------------ oracle arm
+# ------------------------------------------------------------------ oracle (CPU baseline / reference arm)
 def oracle_sigma_rate(cfg, seconds=10.0, seed=21):
-    """Oracle direct sigma on a bounded random sample of output determinants;
-    returns (det/s, rows, wall s, threads)."""
+    """Oracle direct sigma on a bounded random sample of output determinants.
+    Returns (det/s, rows, wall seconds, threads)."""
     import oracle
     n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
     Na, Nb = si.n_strings(n, na), si.n_strings(n, nb)
     C = si.random_vectors(1, Na, Nb, seed=7).reshape(1, -1)
     rng = np.random.default_rng(seed)
-    # calibrate: per-call set-up cost + per-row cost from two probe sizes
     t = []
-    for m in (256, 4096):
+    for m in (256, 4096):  # per-call set-up cost and per-row cost
         probe = rng.integers(0, Na * Nb, size=m)
         t0 = time.perf_counter()
         oracle.sigma(n, na, nb, h, eri, C, rows=probe)
         t.append(time.perf_counter() - t0)
-    per_row = max((t[1] - t[0]) / 3840.0, t[1] / 4096.0 * 0.5, 1e-7)
+    per_row = max((t[1] - t[0]) / 3840.0, 1e-7)
     nrows = int(max(4096, min(5_000_000, max(seconds - t[0], 0.5) / per_row)))
     rows = rng.integers(0, Na * Nb, size=nrows)
     t0 = time.perf_counter()
@@ -127,45 +144,58 @@ def oracle_sigma_rate(cfg, seconds=10.0, seed=21):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
     cfg = WORKLOADS[args.workload]
     for _ in range(args.warmup):
-        oracle_sigma_rate(cfg, seconds=2.0)
-    rates = []
-    t_all = 0.0
-    nthreads = 1
-    rows_tot = 0
+        oracle_sigma_rate(cfg, seconds=1.0)
+    t_all, rows_tot, nthreads = 0.0, 0, 1
     for _ in range(args.steps):
-        r, rows, dt, nthreads = oracle_sigma_rate(cfg, seconds=args.ref_seconds)
-        rates.append(r)
+        _, rows, dt, nthreads = oracle_sigma_rate(cfg, seconds=args.ref_seconds)
         t_all += dt
         rows_tot += rows
     value = rows_tot / t_all
-    sample = (f"oracle direct sigma on {rows_tot} random output determinants of {args.workload} "
-              f"over {args.steps} steps")
-    out = {
+    sample = (f"oracle direct sigma (Slater-Condon, FP64) on {rows_tot} random output determinants of "
+              f"{args.workload}, {args.steps} steps")
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "det/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_all / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": "det/s", "cores": nthreads, "kind": "oracle",
-                         "sample": sample},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t_all / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "det/s", "cores": nthreads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "det/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(out))
+    }))
     return 0
 
 
-# ------------------------------------------------------------------ GPU arm
-def kernel_flops(ctx_info, name, nvec):
-    """Algorithmic FLOPs of one sigma vector through kernel `name`."""
-    nd, nka, nkb, nnz_a, nnz_b = ctx_info
+# ------------------------------------------------------------------ roofline bookkeeping
+def kernel_work(name, prob, n_sig64, n_sigm, n_rdm, tables):
+    """(algorithmic work, unit, bound, peak, peak note) of all launches of `name`."""
+    hbm, bf16, bf16s, src = peaks()
+    n = prob.norb
+    nd = prob.ndet
+    nk = lambda ne: ne * (n - ne) + ne  # noqa: E731
+    nka, nkb = nk(prob.nalpha), nk(prob.nbeta)
+    npair = n * (n + 1) // 2
+    nnz_a, nnz_b = tables
     if name == "ab_fp64":
-        return 2.0 * nd * nka * nkb * nvec
+        return 2.0 * nd * nka * nkb * n_sig64, "TFLOP/s", "alu", FP64_PEAK_TFLOPS, "FP64 pipe, nominal"
     if name == "ss_spmm":
-        return 2.0 * nd * (nnz_a + nnz_b) / 2.0 * nvec
+        return (2.0 * (nnz_a * prob.nb + nnz_b * prob.na) * n_sig64, "TFLOP/s", "alu", FP64_PEAK_TFLOPS,
+                "FP64 pipe, nominal")
+    if name == "ss_spmm_f32":
+        return (2.0 * (nnz_a * prob.nb + nnz_b * prob.na) * n_sigm, "TFLOP/s", "alu", FP32_PEAK_TFLOPS,
+                "FP32 pipe, nominal")
+    if name == "ab_mma_bf16x2":
+        return (3 * 2.0 * nd * npair * nka * n_sigm, "TFLOP/s", "tensor", bf16s,
+                f"bf16 dense sustained ({src})")
+    if name == "ab_mma_tf32":
+        return (2.0 * nd * npair * nka * n_sigm, "TFLOP/s", "tensor", bf16s * TF32_OVER_BF16,
+                f"bf16 dense sustained ({src}) x nominal tf32/bf16 ratio")
+    if name == "gram":
+        nt = (n * n + 63) // 64  # symmetric Gram: tiles ta <= tb of 64 x 64
+        return (2.0 * 64 * 64 * nt * (nt + 1) // 2 * nd * n_rdm, "TFLOP/s", "alu", FP64_PEAK_TFLOPS,
+                "FP64 pipe, nominal")
     return None
 
 
@@ -187,7 +217,8 @@ def run_ours(args):
     cfg = WORKLOADS[args.workload]
     n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
-    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}[args.precision]
+    modes = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}
+    mode = modes[args.precision]
     stream = torch.cuda.current_stream()
 
     t0 = time.perf_counter()
@@ -195,28 +226,34 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t0
     nd = prob.ndet
-    nroots = 1
-    tol = args.tol
-
+    nroots, tol = 1, args.tol
     g1 = torch.empty(n, n, dtype=torch.float64, device="cuda")
     g2 = torch.empty((n,) * 4, dtype=torch.float64, device="cuda")
     root = torch.empty(nroots, prob.na, prob.nb, dtype=torch.float64, device="cuda")
 
-    def step():
+    def solve(m):
+        fg.forte_set_precision(prob.ctx, m)
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
         fg.forte_davidson(prob.ctx, nroots, tol, allow_not_converged=True)
-        fg.forte_get_roots(prob.ctx, nroots, root)
-        fg.forte_rdms(prob.ctx, root[0], g1, g2, n)
+        d1.record(stream)
+        E, rn, it = fg.forte_get_roots(prob.ctx, nroots, root)
+        return float(E[0]), float(rn[0]), it, (d0, d1)
 
-    # reference energy (FP64, tight), outside every timed region
-    E_ref = None
-    if args.ref_energy:
-        fg.forte_set_precision(prob.ctx, fg.FORTE_FP64)
-        fg.forte_davidson(prob.ctx, 1, 1e-8, allow_not_converged=True)
-        E_ref = float(fg.forte_get_roots(prob.ctx, 1)[0][0])
-        fg.forte_set_precision(prob.ctx, mode)
+    # FP64 comparison solve (also the reference energy), outside the timed region
+    fp64_cmp = None
+    if args.fp64_compare:
+        c0 = fg.forte_get_counters(prob.ctx)
+        E64, rn64, it64, ev = solve(fg.FORTE_FP64)
+        torch.cuda.synchronize()
+        c1 = fg.forte_get_counters(prob.ctx)
+        fp64_cmp = {"ms": ev[0].elapsed_time(ev[1]), "energy": E64, "residual": rn64, "iterations": it64,
+                    "sigma_vectors_fp64": c1[0] - c0[0]}
+    E_ref = fp64_cmp["energy"] if fp64_cmp else None
 
     for _ in range(args.warmup):
-        step()
+        solve(mode)
+        fg.forte_rdms(prob.ctx, root[0], g1, g2, n)
     torch.cuda.synchronize()
 
     s0 = fg.forte_get_counters(prob.ctx)
@@ -227,18 +264,12 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    dav_ms = []
-    energies = []
+    per_step = []
     ev0.record(stream)
     for _ in range(args.steps):
-        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        fg.forte_davidson(prob.ctx, nroots, tol, allow_not_converged=True)
-        d1.record(stream)
-        E, rn, it = fg.forte_get_roots(prob.ctx, nroots, root)
+        E, rn, it, dev_ev = solve(mode)
         fg.forte_rdms(prob.ctx, root[0], g1, g2, n)
-        energies.append(float(E[0]))
-        dav_ms.append((d0, d1, it, float(rn[0])))
+        per_step.append((E, rn, it, dev_ev))
     ev1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -247,102 +278,161 @@ def run_ours(args):
     fg.forte_profile_enable(prob.ctx, 0)
     t_ms = ev0.elapsed_time(ev1)
     s1 = fg.forte_get_counters(prob.ctx)
-    nsig64, nsigm = s1[0] - s0[0], s1[1] - s0[1]
+    n_sig64, n_sigm = s1[0] - s0[0], s1[1] - s0[1]
     prof = fg.profile_table(prob.ctx)
     launches = sum(v[0] for v in prof.values())
-
     if dist:
         tt = torch.tensor([t_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_ms = float(tt.item())
-    units = nd * (nsig64 + nsigm) * world
-    value = units / (t_ms / 1000.0)
+    value = nd * (n_sig64 + n_sigm) * world / (t_ms / 1000.0)
 
-    # roofline of the dominant kernel
-    hbm, bf16, bf16s, peak_src = peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_n, dom_ms) = dom
-    nka = prob.norb * 0  # placeholder replaced below
-    nk = lambda ne: ne * (n - ne) + ne  # noqa: E731
-    info = (nd, nk(na), nk(nb), None, None)
-    roof = None
-    if dom_name == "ab_fp64":
-        flops = 2.0 * nd * nk(na) * nk(nb) * nsig64
-        ach = flops / (dom_ms / 1000.0) / 1e12
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 pipe rate (152 SMs x 2 DFMA/clk x 2 x ~2.06 GHz)",
-                "launches": dom_n, "avg_ms": dom_ms / max(dom_n, 1)}
-    else:
-        roof = {"kernel": dom_name, "bound": None, "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "launches": dom_n, "avg_ms": dom_ms / max(dom_n, 1)}
+    # rooflines
+    traffic = traffic_table()
+    nnz = fg_nnz(prob)
+    rows = {}
+    for name, (cnt, ms) in prof.items():
+        w = kernel_work(name, prob, n_sig64, n_sigm, args.steps, nnz)
+        if w is None or ms <= 0:
+            continue
+        work, unit, bound, peak, note = w
+        ach = work / (ms / 1000.0) / 1e12
+        tr = traffic.get(args.workload, {}).get(name)
+        rows[name] = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                      "frac": ach / peak, "traffic": tr["bytes_per_launch"] if tr else None,
+                      "peak_note": note, "launches": cnt, "total_ms": ms, "avg_ms": ms / cnt}
+    dom_name = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = rows.get(dom_name) or {"kernel": dom_name, "bound": None, "achieved": None, "peak": None,
+                                  "unit": None, "frac": None, "traffic": None}
 
-    dav_times = [a.elapsed_time(b) for (a, b, _, _) in dav_ms]
-    dav_iters = [x[2] for x in dav_ms]
+    dav = []
+    for (E, rn, it, (d0, d1)) in per_step:
+        dav.append({"ms": d0.elapsed_time(d1), "energy": E, "residual": rn, "iterations": it,
+                    "energy_err_vs_fp64": abs(E - E_ref) if E_ref is not None else None})
     out = {
         "metric": METRIC, "value": value, "unit": "det/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if mode == fg.FORTE_FP64 else args.precision,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32+f64", "bf16x2": "bf16x2+f64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"CAS(14,14) 7a7b 11,778,624 dets seed 2 (n_L 28)"
-                   if args.workload == "cas1414" else args.workload,
-                   "precision": args.precision, "nroots": nroots, "tol": tol,
-                   "step": "Davidson to tol + 1-/2-RDM", "l2": "inputs larger than L2 (94 MB vectors, >2 GB subspace)",
-                   "parallelism": f"replicas{world}"},
-        "davidson": {"ms": dav_times, "iterations": dav_iters, "energy": energies,
-                     "E_ref_fp64": E_ref,
-                     "energy_err": [abs(e - E_ref) for e in energies] if E_ref is not None else None,
-                     "sigma_vectors_fp64": nsig64, "sigma_vectors_mixed": nsigm},
+        "config": {"workload": WORKLOAD_NAMES[args.workload], "precision": args.precision, "nroots": nroots,
+                   "tol": tol, "step": "Davidson-Liu to FP64 residual tol, then 1-/2-RDM of the root",
+                   "l2": "inputs larger than L2 (94 MB vectors, >2 GB subspace); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "time_to_1e-8": {
+            "precision": args.precision,
+            "ms": [d["ms"] for d in dav],
+            "energy_err_vs_fp64": [d["energy_err_vs_fp64"] for d in dav],
+            "fp64_ms": fp64_cmp["ms"] if fp64_cmp else None,
+            "speedup_vs_fp64": (fp64_cmp["ms"] / min(d["ms"] for d in dav)) if fp64_cmp else None,
+        },
+        "davidson": dav, "fp64_solve": fp64_cmp,
+        "sigma_vectors": {"fp64": n_sig64, "reduced": n_sigm},
         "setup_s": t_setup,
         "roofline": roof,
+        "rooflines": rows,
         "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "gpu_launches": launches,
         "clocks": clk,
     }
 
-    # end to end through the C ABI with host buffers
+    # sigma-only throughput per precision (det/s), outside the timed region
+    if args.sigma_rates:
+        C = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=12), device="cuda")
+        S = torch.empty_like(C)
+        rates = {}
+        for name, m in modes.items():
+            fg.forte_set_precision(prob.ctx, m)
+            fg.forte_sigma(prob.ctx, C, S, 1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3 if m == fg.FORTE_FP64 else 10
+            a.record(stream)
+            for _ in range(reps):
+                fg.forte_sigma(prob.ctx, C, S, 1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            rates[name] = {"ms": a.elapsed_time(b) / reps, "det_per_s": nd / (a.elapsed_time(b) / reps / 1000.0)}
+        out["sigma_rates"] = rates
+        fg.forte_set_precision(prob.ctx, mode)
+
+    # end to end through the C ABI: host integrals in, host energies + RDMs out
     if args.e2e_steps > 0:
-        import paper_2405_10197_gb300 as fg2
         h_pin = torch.tensor(h).pin_memory()
         eri_pin = torch.tensor(eri).pin_memory()
-        E_host = np.zeros(1)
         g1_host = torch.empty(n, n, dtype=torch.float64).pin_memory()
         g2_host = torch.empty((n,) * 4, dtype=torch.float64).pin_memory()
-        e2e_t = []
-        e2e_units = 0
+        e2e_t, e2e_units = [], 0
         for _ in range(args.e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx = fg2.forte_cas_create(n, na, nb, h_pin.numpy(), eri_pin.numpy())
-            fg2.forte_set_stream(ctx, stream)
-            fg2.forte_set_precision(ctx, mode)
-            fg2.forte_davidson(ctx, nroots, tol, allow_not_converged=True)
-            E_host[:], _, _ = fg2.forte_get_roots(ctx, nroots, root)
-            fg2.forte_rdms(ctx, root[0], g1, g2, n)
+            ctx = fg.forte_cas_create(n, na, nb, h_pin.numpy(), eri_pin.numpy())
+            fg.forte_set_stream(ctx, stream)
+            fg.forte_set_precision(ctx, mode)
+            fg.forte_davidson(ctx, nroots, tol, allow_not_converged=True)
+            fg.forte_get_roots(ctx, nroots, root)
+            fg.forte_rdms(ctx, root[0], g1, g2, n)
             g1_host.copy_(g1, non_blocking=True)
             g2_host.copy_(g2, non_blocking=True)
             torch.cuda.synchronize()
-            c = fg2.forte_get_counters(ctx)
-            fg2.forte_destroy(ctx)
+            c = fg.forte_get_counters(ctx)
+            fg.forte_destroy(ctx)
             e2e_t.append(time.perf_counter() - t0)
             e2e_units += nd * (c[0] + c[1])
         out["e2e"] = {"value": e2e_units * world / sum(e2e_t), "unit": "det/s",
                       "h2d_bytes_per_step": 8 * (n * n + n ** 4),
                       "d2h_bytes_per_step": 8 * (nroots + n * n + n ** 4),
                       "steps": args.e2e_steps, "s_per_step": sum(e2e_t) / len(e2e_t),
-                      "includes": "forte_cas_create (string tables, CSR, H_II) + Davidson + RDMs + D2H"}
+                      "includes": "forte_cas_create from host integrals (strings, tables, CSR, H_II) + "
+                                  "Davidson + RDMs + copies of energies and RDMs to host"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r, rows, dt, thr = oracle_sigma_rate(cfg, seconds=args.ref_seconds)
+        r, nrows, dt, thr = oracle_sigma_rate(cfg, seconds=args.ref_seconds)
         out["cpu_baseline"] = {"value": r, "unit": "det/s", "cores": thr, "kind": "oracle",
-                               "sample": f"oracle direct sigma on {rows} random output determinants "
-                                         f"({dt:.1f} s)"}
+                               "sample": f"oracle direct sigma (Slater-Condon, FP64) on {nrows} random output "
+                                         f"determinants of the same workload, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(out))
     prob.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_kernel_case(args):
+    """Small fixed invocation for profilers: build the workload, then run one
+    operation twice (the second call is the one to capture)."""
+    import torch
+    import paper_2405_10197_gb300 as fg
+    torch.cuda.set_device(0)
+    cfg = WORKLOADS[args.workload]
+    n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
+    h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
+    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}[args.precision]
+    prob = fg.CASProblem(n, na, nb, h, eri, precision=mode)
+    C = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=12), device="cuda")
+    out = {"case": args.kernel_case, "workload": args.workload, "precision": args.precision}
+    for _ in range(2):
+        if args.kernel_case == "sigma":
+            S = prob.sigma(C)
+            out["max_abs"] = float(S.abs().max())
+        else:
+            g1, _ = prob.rdms(C[0])
+            out["trace_g1"] = float(g1.trace())
+    torch.cuda.synchronize()
+    prob.close()
+    print(json.dumps(out))
+    return 0
+
+
+def fg_nnz(prob):
+    """Stored entries of the alpha and beta same-spin string Hamiltonians: every
+    string within two replacements of a row string (itself, singles, doubles)."""
+    from math import comb
+    n = prob.norb
+
+    def per_row(ne):
+        return 1 + ne * (n - ne) + comb(ne, 2) * comb(n - ne, 2)
+    return prob.na * per_row(prob.nalpha), prob.nb * per_row(prob.nbeta)
 
 
 def main():
@@ -352,13 +442,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cas1414")
-    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16x2"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16x2"], default="bf16x2")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
-    ap.add_argument("--ref-energy", action="store_true")
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--no-sigma-rates", dest="sigma_rates", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
+                    help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
     args = ap.parse_args()
+    if args.steps < 1:
+        ap.error("--steps must be >= 1")
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -105,13 +105,23 @@ constexpr int GT = 64;   // Gram tile
 constexpr int GK = 32;   // K slab
 
 // part[split][a][b] = sum_{k in split's range} X[a][k] Y[b][k]; m x m output in GT tiles.
+// With sym (X == Y) only the tiles ta <= tb are formed (grid.x = ntile(ntile+1)/2).
 __global__ void __launch_bounds__(256) k_gram(const double *__restrict__ X, const double *__restrict__ Y,
-                                              int m, long long K, long long kper,
+                                              int m, long long K, long long kper, int sym,
                                               double *__restrict__ part) {
   __shared__ double As[GK][GT + 1];
   __shared__ double Bs[GK][GT + 1];
   const int ntile = (m + GT - 1) / GT;
-  const int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
+  int ta = blockIdx.x / ntile, tb = blockIdx.x % ntile;
+  if (sym) {
+    int rem = blockIdx.x;
+    ta = 0;
+    while (rem >= ntile - ta) {
+      rem -= ntile - ta;
+      ++ta;
+    }
+    tb = ta + rem;
+  }
   const int a0 = ta * GT, b0 = tb * GT;
   const long long k0 = (long long)blockIdx.y * kper, k1 = min(K, k0 + kper);
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -153,13 +163,19 @@ __global__ void __launch_bounds__(256) k_gram(const double *__restrict__ X, cons
 }
 
 // g2[p][q][r][s] = sum_split part[split][(q,p)][(r,s)] - d_qr g1[p][s]
-__global__ void k_finish_g2(const double *__restrict__ part, int nsplit, int n,
+__global__ void k_finish_g2(const double *__restrict__ part, int nsplit, int n, int sym,
                             const double *__restrict__ g1, double *__restrict__ g2) {
   const int m = n * n;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m * m) return;
   int p = i / (n * n * n), q = (i / (n * n)) % n, r = (i / n) % n, s = i % n;
-  long long idx = (long long)(q * n + p) * m + (r * n + s);
+  int a = q * n + p, b = r * n + s;
+  if (sym && a / GT > b / GT) {  // only tiles ta <= tb were formed; the Gram is symmetric
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  long long idx = (long long)a * m + b;
   double v = 0.0;
   for (int t = 0; t < nsplit; ++t) v += part[(long long)t * m * m + idx];
   if (q == r) v -= g1[p * n + s];
@@ -244,16 +260,17 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
   double *G = (double *)(w + off_G);
   const int ntile = (n2 + GT - 1) / GT;
   long long kper = (ND + nsplit - 1) / nsplit;
-  dim3 gg(ntile * ntile, nsplit);
+  const int sym = same ? 1 : 0;
+  dim3 gg(sym ? ntile * (ntile + 1) / 2 : ntile * ntile, nsplit);
   // M[a][b] = <D_bra^a, D_ket^b>, where D_bra^{qp} = E_qp bra
   {
     FORTE_PROF(ctx, "gram");
-    k_gram<<<gg, 256, 0, st>>>(Db, Dk, n2, ND, kper, G);
+    k_gram<<<gg, 256, 0, st>>>(Db, Dk, n2, ND, kper, sym, G);
   FORTE_LAUNCH_CHECK();
   }
   {
     FORTE_PROF(ctx, "finish_g2");
-    k_finish_g2<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(G, nsplit, n, g1w, g2);
+    k_finish_g2<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(G, nsplit, n, sym, g1w, g2);
   FORTE_LAUNCH_CHECK();
   }
   return FORTE_OK;
