@@ -144,6 +144,20 @@ int forte_set_guess(forte_ctx *ctx, const double *C, int nvec);
  * (gamma_2), summed over spin.  FP64. */
 int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2);
 
+/* Adjoint of the state-averaged energy E_SA = sum_k w_k E_k (the CI part of the
+ * Lagrangian of Sec. II.B, weights w_k of the states) with respect to the
+ * integrals.  The E_k are variational, so by Hellmann-Feynman
+ *   dE_SA/dh_pq        = sum_k w_k gamma^k_pq
+ *   dE_SA/d(pq|rs)     = 1/2 sum_k w_k Gamma^k_pqrs   (each of the n^4 entries of eri
+ *                        treated as independent; E = sum h gamma + 1/2 sum (pq|rs) Gamma)
+ * and this call ACCUMULATES scale times those into dh (device [n][n]) and
+ * deri (device [n]^4).
+ *   weights  host [nstates]
+ *   C        device [nstates][N_alpha][N_beta], normalised eigenvectors of H
+ * FP64.  Asynchronous on the context stream. */
+int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale,
+                      double *dh, double *deri);
+
 /* One-body transition density matrix between two states (Sec. II.A.1):
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);

@@ -75,6 +75,7 @@ def library():
         "forte_rdms": [vp, vp, vp, vp],
         "forte_tdm1": [vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
+        "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -223,6 +224,16 @@ def forte_tdm1(ctx, bra, ket, t1, norb):
                                        _ptr(t1, norb * norb)))
 
 
+def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
+    """Accumulate scale * d(sum_k w_k E_k)/d(h, eri) into the device tensors dh, deri."""
+    na, nb = forte_get_sizes(ctx)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if w.size != nstates:
+        raise ValueError("need one weight per state")
+    return _check(library().forte_sa_gradient(ctx, int(nstates), w.ctypes.data, _ptr(C, nstates * na * nb),
+                                              float(scale), _ptr(dh, norb * norb), _ptr(deri, norb ** 4)))
+
+
 def forte_profile_enable(ctx, on):
     return _check(library().forte_profile_enable(ctx, int(on)))
 
@@ -325,3 +336,52 @@ class CASProblem:
 
     def string_tables(self, spin):
         return forte_get_string_tables(self.ctx, spin, self.norb)
+
+
+# --------------------------------------------------------------- differentiable SA energy
+
+def _make_sa_energy():
+    import torch
+
+    class SAEnergy(torch.autograd.Function):
+        """E_SA(h, eri) = sum_k w_k E_k over the lowest len(weights) roots.
+
+        forward: forte_cas_create + forte_davidson; backward: forte_sa_gradient,
+        the library's adjoint kernel (dE/dh = sum w gamma, dE/d(pq|rs) = 1/2 sum w Gamma).
+        """
+
+        @staticmethod
+        def forward(fctx, h, eri, norb, nalpha, nbeta, weights, precision=FORTE_FP64, tol=1e-10):
+            hn = h.detach().to("cpu", torch.float64).numpy()
+            en = eri.detach().to("cpu", torch.float64).numpy()
+            prob = CASProblem(norb, nalpha, nbeta, hn, en, precision=precision)
+            w = np.asarray(weights, dtype=np.float64)
+            E, C, rn, it = prob.davidson(len(w), tol)
+            fctx.prob, fctx.C, fctx.w = prob, C, w
+            fctx.meta = (h.device, h.dtype, eri.device, eri.dtype)
+            fctx.energies, fctx.residuals = E, rn
+            return torch.tensor(float(w @ E), dtype=h.dtype, device=h.device)
+
+        @staticmethod
+        def backward(fctx, grad):
+            import torch as T
+            prob = fctx.prob
+            n = prob.norb
+            dh = T.zeros(n, n, dtype=T.float64, device=prob.device)
+            deri = T.zeros((n,) * 4, dtype=T.float64, device=prob.device)
+            forte_sa_gradient(prob.ctx, len(fctx.w), fctx.w, fctx.C, float(grad), dh, deri, n)
+            hdev, hdt, edev, edt = fctx.meta
+            return dh.to(hdev, hdt), deri.to(edev, edt), None, None, None, None, None, None
+
+    return SAEnergy
+
+
+_SAEnergy = None
+
+
+def sa_energy(h, eri, norb, nalpha, nbeta, weights, precision=FORTE_FP64, tol=1e-10):
+    """Differentiable state-averaged CASCI energy (torch scalar)."""
+    global _SAEnergy
+    if _SAEnergy is None:
+        _SAEnergy = _make_sa_energy()
+    return _SAEnergy.apply(h, eri, norb, nalpha, nbeta, tuple(weights), precision, tol)

@@ -612,7 +612,7 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_gpair); cudaFree(ctx->d_gpair32); cudaFree(ctx->d_hdiag);
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
-  ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release();
+  ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
@@ -779,6 +779,15 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2) {
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1) {
   if (!ctx || !bra || !ket || !t1) { set_error("NULL argument"); return FORTE_ERR_ARG; }
   return rdm12_fp64(ctx, bra, ket, t1, nullptr);
+}
+
+int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale,
+                      double *dh, double *deri) {
+  if (!ctx || nstates < 1 || !weights || !C || !dh || !deri) { set_error("bad arguments"); return FORTE_ERR_ARG; }
+  for (int k = 0; k < nstates; ++k)
+    if (!isfinite(weights[k])) { set_error("non-finite weight"); return FORTE_ERR_ARG; }
+  if (!isfinite(scale)) { set_error("non-finite scale"); return FORTE_ERR_ARG; }
+  return sa_gradient(ctx, nstates, weights, C, scale, dh, deri);
 }
 
 int forte_get_counters(const forte_ctx *ctx, long long *fp64, long long *mixed) {

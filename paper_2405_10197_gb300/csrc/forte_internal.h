@@ -131,6 +131,7 @@ struct forte_ctx {
   forte::Scratch sc_small;         // small device arrays (dots, norms)
   forte::Scratch sc_rdm;           // RDM intermediates
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
+  forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -189,6 +190,8 @@ int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_hos
 
 // rdm.cu
 int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2);
+int sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale, double *dh,
+                double *deri);
 
 // Host Jacobi eigensolver for the small symmetric subspace matrix (ascending).
 void sym_eig(int k, const double *A, double *w, double *U);

@@ -182,6 +182,37 @@ __global__ void k_finish_g2(const double *__restrict__ part, int nsplit, int n, 
   g2[i] = v;
 }
 
+// Adjoint of the state-averaged energy E_SA = sum_k w_k E_k (Sec. II.B):
+// dh += c1 gamma^k, deri += c2 Gamma^k for one state (c1 = scale w_k, c2 = scale w_k / 2).
+__global__ void k_sa_accum(const double *__restrict__ g1, const double *__restrict__ g2, int n, double c1,
+                           double c2, double *__restrict__ dh, double *__restrict__ deri) {
+  const int n2 = n * n, n4 = n2 * n2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    deri[i] += c2 * g2[i];
+    if (i < n2) dh[i] += c1 * g1[i];
+  }
+}
+
+int sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale, double *dh,
+                double *deri) {
+  const int n = ctx->n, n2 = n * n;
+  int rc = ctx->sc_grad.ensure(sizeof(double) * ((size_t)n2 + (size_t)n2 * n2) + 256);
+  if (rc) return rc;
+  double *g1 = (double *)ctx->sc_grad.ptr, *g2 = g1 + n2;
+  for (int k = 0; k < nstates; ++k) {
+    const double *ck = C + (size_t)k * ctx->Ndet;
+    if ((rc = rdm12_fp64(ctx, ck, ck, g1, g2))) return rc;
+    const double c1 = scale * weights[k], c2 = 0.5 * scale * weights[k];
+    {
+      FORTE_PROF(ctx, "sa_accum");
+      k_sa_accum<<<(unsigned)std::min(1024, (n2 * n2 + 255) / 256), 256, 0, ctx->stream>>>(g1, g2, n, c1, c2, dh,
+                                                                                          deri);
+      FORTE_LAUNCH_CHECK();
+    }
+  }
+  return FORTE_OK;
+}
+
 int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2) {
   cudaStream_t st = ctx->stream;
   const int n = ctx->n, n2 = n * n;

@@ -1,0 +1,118 @@
+"""Differentiation of the state-averaged energy E_SA = sum_k w_k E_k (Sec. II.B
+Lagrangian, CI part): the backward of `sa_energy` is the library's adjoint
+kernel (forte_sa_gradient), dE/dh = sum w gamma and dE/d(pq|rs) = 1/2 sum w Gamma.
+
+Checked against (i) the oracle's RDMs of its own dense eigenvectors and (ii)
+central finite differences (step 1e-5) along symmetry orbits of the integrals
+(h_pq with h_qp; the 8 equivalents of (pq|rs)), so that the convention for the
+split of the derivative among equivalent entries cancels.  Tolerance 1e-6
+absolute for the finite differences (energy noise ~1e-12 / step + O(step^2))."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+import synth_inputs as si
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2405_10197_gb300 as fg  # noqa: E402
+
+
+def _orbit_h(n, p, q):
+    m = np.zeros((n, n))
+    m[p, q] = m[q, p] = 1.0
+    return m
+
+
+def _orbit_eri(n, p, q, r, s):
+    m = np.zeros((n,) * 4)
+    for a, b, c, d in {(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+                       (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)}:
+        m[a, b, c, d] = 1.0
+    return m
+
+
+def _energy(h, eri, n, na, nb, w, precision=fg.FORTE_FP64):
+    with torch.no_grad():
+        e = fg.sa_energy(torch.tensor(h), torch.tensor(eri), n, na, nb, w, precision=precision, tol=1e-10)
+    return float(e)
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(6, 3, 3, 3), (6, 2, 3, 4)])
+def test_sa_gradient_equals_weighted_oracle_rdms(n, na, nb, seed):
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w = [1 / 3, 1 / 3, 1 / 3]
+    ev, V = oracle.solve_dense(n, na, nb, h, eri, nroots=4)
+    assert ev[3] - ev[2] > 1e-4 and min(np.diff(ev[:3])) > 1e-6
+    ht = torch.tensor(h, requires_grad=True)
+    et = torch.tensor(eri, requires_grad=True)
+    E = fg.sa_energy(ht, et, n, na, nb, w)
+    E.backward()
+    assert abs(float(E.detach()) - sum(wi * e for wi, e in zip(w, ev[:3]))) < 1e-10
+    g1 = sum(wi * oracle.rdm12(n, na, nb, V[k], two=False)[0] for k, wi in enumerate(w))
+    g2 = sum(wi * oracle.rdm12(n, na, nb, V[k], one=False)[1] for k, wi in enumerate(w))
+    assert np.abs(ht.grad.numpy() - g1).max() < 1e-9
+    assert np.abs(et.grad.numpy() - 0.5 * g2).max() < 1e-9
+
+
+def test_sa_gradient_central_differences_small():
+    n, na, nb, seed = 6, 3, 3, 3
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w = [1 / 3, 1 / 3, 1 / 3]
+    ht = torch.tensor(h, requires_grad=True)
+    et = torch.tensor(eri, requires_grad=True)
+    fg.sa_energy(ht, et, n, na, nb, w).backward()
+    gh, ge = ht.grad.numpy(), et.grad.numpy()
+    rng = np.random.default_rng(17)
+    step = 1e-5
+    for _ in range(8):
+        p, q = rng.integers(0, n, size=2)
+        d = _orbit_h(n, p, q)
+        fd = (_energy(h + step * d, eri, n, na, nb, w) - _energy(h - step * d, eri, n, na, nb, w)) / (2 * step)
+        assert abs(fd - (gh * d).sum()) < 1e-6, ("h", p, q)
+    for _ in range(8):
+        p, q, r, s = rng.integers(0, n, size=4)
+        d = _orbit_eri(n, p, q, r, s)
+        fd = (_energy(h, eri + step * d, n, na, nb, w) - _energy(h, eri - step * d, n, na, nb, w)) / (2 * step)
+        assert abs(fd - (ge * d).sum()) < 1e-6, ("eri", p, q, r, s)
+
+
+def test_sa_gradient_cas1212_three_roots():
+    # The differentiation workload: CAS(12,12), seed 3, equal weights over 3 roots.
+    cfg = si.CAS1212_SA
+    n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
+    h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
+    w = [1 / 3, 1 / 3, 1 / 3]
+    ht = torch.tensor(h, requires_grad=True)
+    et = torch.tensor(eri, requires_grad=True)
+    E = fg.sa_energy(ht, et, n, na, nb, w, tol=1e-10)
+    E.backward()
+    gh, ge = ht.grad.numpy(), et.grad.numpy()
+    # invariants of the averaged RDMs: tr gamma = N, sum_pr Gamma_pprr = N(N-1), and
+    # E_SA = sum h gamma + 1/2 sum (pq|rs) Gamma
+    N = na + nb
+    assert abs(np.trace(gh) - N) < 1e-8
+    assert abs(2 * np.einsum("pprr->", ge) - N * (N - 1)) < 1e-7
+    assert abs((h * gh).sum() + (eri * ge).sum() - float(E.detach())) < 1e-8
+    rng = np.random.default_rng(5)
+    step = 1e-5
+    for kind in ("h", "eri"):
+        if kind == "h":
+            p, q = rng.integers(0, n, size=2)
+            d = _orbit_h(n, p, q)
+            args_p, args_m = (h + step * d, eri), (h - step * d, eri)
+            an = (gh * d).sum()
+        else:
+            p, q, r, s = rng.integers(0, n, size=4)
+            d = _orbit_eri(n, p, q, r, s)
+            args_p, args_m = (h, eri + step * d), (h, eri - step * d)
+            an = (ge * d).sum()
+        ep = _energy(*args_p, n, na, nb, w, precision=fg.FORTE_BF16X2)
+        em = _energy(*args_m, n, na, nb, w, precision=fg.FORTE_BF16X2)
+        assert abs((ep - em) / (2 * step) - an) < 1e-6, kind
