@@ -162,6 +162,20 @@ int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const 
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
 
+/* Batched solve of nprob independent problems (many ActiveSpaceMethod instances
+ * of the ActiveSpaceSolver, Sec. III): for problem i, the nroots[i] lowest
+ * eigenvalues of its Hamiltonian, written to E_out[offset_i .. offset_i +
+ * nroots[i]) with offset_i = sum_{j<i} nroots[j] (host).  Inputs per problem as
+ * for forte_cas_create (host arrays h[i], eri[i]).  precision, tol as for
+ * forte_set_precision / forte_davidson.  nworkers host threads (<= 0: 8), each
+ * with its own CUDA stream, take problems largest first; every context is freed
+ * after its solve.  status_out (host [nprob], may be NULL) gets each problem's
+ * status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED keeps energies).
+ * Synchronous. */
+int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *nbeta, const int *nroots,
+                      const double *const *h, const double *const *eri, int precision, double tol,
+                      int nworkers, double *E_out, int *status_out);
+
 /* FP64 sigma = H C that allocates no device memory (the paper has no
  * counterpart; this is a service for callers of the library).  It is meant for
  * callers that cannot call cudaMalloc during the call: code whose device memory

@@ -76,6 +76,7 @@ def library():
         "forte_tdm1": [vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
+        "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -232,6 +233,35 @@ def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
         raise ValueError("need one weight per state")
     return _check(library().forte_sa_gradient(ctx, int(nstates), w.ctypes.data, _ptr(C, nstates * na * nb),
                                               float(scale), _ptr(dh, norb * norb), _ptr(deri, norb ** 4)))
+
+
+def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, nworkers=8, allow_not_converged=False):
+    """Solve a list of independent problems.
+
+    problems: sequence of dicts with norb, nalpha, nbeta, nroots, h, eri (host arrays).
+    Returns (list of energy arrays, per-problem status array)."""
+    P = len(problems)
+    if P == 0:
+        return [], np.zeros(0, dtype=np.int32)
+    norb = np.array([p["norb"] for p in problems], dtype=np.int32)
+    na = np.array([p["nalpha"] for p in problems], dtype=np.int32)
+    nb = np.array([p["nbeta"] for p in problems], dtype=np.int32)
+    nr = np.array([p["nroots"] for p in problems], dtype=np.int32)
+    hs = [_host_f64(p["h"], (int(n), int(n))) for p, n in zip(problems, norb)]
+    es = [_host_f64(p["eri"], (int(n),) * 4) for p, n in zip(problems, norb)]
+    hp = (ctypes.c_void_p * P)(*[a.ctypes.data for a in hs])
+    ep = (ctypes.c_void_p * P)(*[a.ctypes.data for a in es])
+    E = np.zeros(int(nr.sum()))
+    st = np.zeros(P, dtype=np.int32)
+    code = library().forte_batch_solve(P, norb.ctypes.data, na.ctypes.data, nb.ctypes.data, nr.ctypes.data,
+                                       ctypes.cast(hp, ctypes.c_void_p), ctypes.cast(ep, ctypes.c_void_p),
+                                       int(precision), float(tol), int(nworkers), E.ctypes.data, st.ctypes.data)
+    _check(code, (FORTE_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    out, o = [], 0
+    for k in nr:
+        out.append(E[o:o + k].copy())
+        o += k
+    return out, st
 
 
 def forte_profile_enable(ctx, on):

@@ -336,7 +336,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     }
     int nnew_want = 0;
     for (int r = 0; r < nroots; ++r) nnew_want += (res.rn[r] < tol) ? 0 : 1;
-    if (k + nnew_want > maxsub) {
+    if (k + nnew_want > maxsub && k > keep) {
       // collapse onto the lowest `keep` Ritz vectors
       coef.assign((size_t)k * keep, 0.0);
       for (int i = 0; i < k; ++i)

@@ -156,6 +156,10 @@ struct ProfScope {
 namespace forte {
 
 // setup.cu
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum.
+// Always the same value, so concurrent callers (batched solves) cannot undercut
+// one another's launches.
+cudaError_t set_smem_optin_max(const void *func);
 int build_spin_tables(forte_ctx *ctx);
 int upload_tables(forte_ctx *ctx);
 

@@ -161,6 +161,19 @@ static int build_one_spin(forte_ctx *ctx, SpinHost &S, int nel) {
   return FORTE_OK;
 }
 
+cudaError_t set_smem_optin_max(const void *func) {
+  int dev = 0, mx = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  // the limit covers static + dynamic shared memory
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, mx - (int)fa.sharedSizeBytes);
+}
+
 int build_spin_tables(forte_ctx *ctx) {
   const int n = ctx->n;
   ctx->kmat.assign((size_t)n * n, 0.0);

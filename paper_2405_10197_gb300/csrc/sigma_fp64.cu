@@ -207,7 +207,7 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
       set_error("alpha-beta FP64 kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;
     }
-    FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_fp64));
     dim3 grid((unsigned)NA, nvec);
     {
       FORTE_PROF(ctx, "ab_fp64");
@@ -261,7 +261,7 @@ int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, dou
       set_error("alpha-beta FP64 kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;
     }
-    FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_fp64));
     dim3 grid((unsigned)NA, nvec);
     k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB, ctx->d_gpair,
                                               ctx->npair, C, S, ND, TJ);

@@ -614,14 +614,14 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
     }
     dim3 grid((unsigned)NA, (unsigned)nvec);
     if (mode == FORTE_BF16X2) {
-      FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_BF16X2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2>));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
       k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                              ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
                                                              ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
-      FORTE_CUDA_TRY(cudaFuncSetAttribute(k_ab_mma<FORTE_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32>));
       FORTE_PROF(ctx, "ab_mma_tf32");
       k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                            ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,

@@ -218,6 +218,18 @@ def test_davidson_finds_roots_of_both_spin_flip_sectors(n, na, nb, seed, nroots)
     prob.close()
 
 
+@pytest.mark.parametrize("n,na,nb,nroots", [(5, 1, 0, 3), (3, 1, 1, 4), (4, 2, 1, 3), (2, 1, 1, 4)])
+def test_davidson_tiny_spaces_with_many_roots(n, na, nb, nroots):
+    # subspace limit capped by the dimension: the collapse must never shrink below
+    # what the space already holds
+    h, eri = si.integrals(n, 2 * n, seed=31 + n)
+    w, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=nroots)
+    prob = fg.CASProblem(n, na, nb, h, eri)
+    E, C, rn, it = prob.davidson(nroots=nroots, tol=1e-10)
+    assert np.abs(E - w).max() < 1e-10
+    prob.close()
+
+
 def test_profile_counts_launches():
     h, eri = si.integrals(6, 12, seed=0)
     prob = fg.CASProblem(6, 3, 3, h, eri)
