@@ -424,6 +424,32 @@ def run_kernel_case(args):
     return 0
 
 
+def run_batch(args):
+    """Solves/s of forte_batch_solve on the first `args.batch` instances of the
+    batched workload (orbital counts {6,8,10,12}, 1-3 roots, seeds 1000+i)."""
+    import torch
+    import paper_2405_10197_gb300 as fg
+    torch.cuda.set_device(0)
+    inst = si.batch_instances()[:args.batch]
+    probs = []
+    for q in inst:
+        h, eri = si.integrals(q["norb"], q["n_l"], q["seed"])
+        probs.append(dict(norb=q["norb"], nalpha=q["nalpha"], nbeta=q["nbeta"], nroots=q["nroots"], h=h, eri=eri))
+    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}[args.precision]
+    fg.forte_batch_solve(probs[:8], precision=mode, tol=args.tol)  # warm-up (module load, code paths)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, st = fg.forte_batch_solve(probs, precision=mode, tol=args.tol, allow_not_converged=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    counts = {n: sum(1 for q in inst if q["norb"] == n) for n in (6, 8, 10, 12)}
+    print(json.dumps({"metric": "batched CASCI solves/s", "value": len(probs) / dt, "unit": "solves/s",
+                      "instances": len(probs), "seconds": dt, "precision": args.precision, "tol": args.tol,
+                      "orbital_counts": counts, "roots": int(sum(q["nroots"] for q in inst)),
+                      "status_nonzero": int((st != 0).sum())}))
+    return 0
+
+
 def fg_nnz(prob):
     """Stored entries of the alpha and beta same-spin string Hamiltonians: every
     string within two replacements of a row string (itself, singles, doubles)."""
@@ -449,6 +475,8 @@ def main():
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-sigma-rates", dest="sigma_rates", action="store_false")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time forte_batch_solve on the first N instances of the batched workload instead")
     ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
                     help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
     args = ap.parse_args()
@@ -456,6 +484,8 @@ def main():
         ap.error("--steps must be >= 1")
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.batch > 0:
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -611,6 +611,8 @@ void forte_destroy(forte_ctx *ctx) {
   }
   cudaFree(ctx->d_gpair); cudaFree(ctx->d_gpair32); cudaFree(ctx->d_hdiag);
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
+  cudaFree(ctx->d_gT_hi); cudaFree(ctx->d_gT_lo); cudaFree(ctx->d_gT_t32); cudaFree(ctx->d_err);
+  cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp);
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

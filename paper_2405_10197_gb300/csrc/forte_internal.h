@@ -113,6 +113,8 @@ struct forte_ctx {
   uint16_t *d_gT_hi = nullptr, *d_gT_lo = nullptr;
   float *d_gT_t32 = nullptr;
   int *d_err = nullptr;         // device status word of bounded waits (0 = ok)
+  uint16_t *d_ozT = nullptr;    // [n*n][Nb padded to 64]: E_sr |Ib> of the beta strings (RDM Gram)
+  double *d_g1tmp = nullptr;    // 1-RDM workspace of the tensor-core 2-RDM when the caller passes none
   float gmax = 0.f;             // max |(pq|rs)| (bounds the alpha-beta fixed-point scale)
 
   // Davidson controls and results
@@ -194,6 +196,10 @@ int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_hos
 
 // rdm.cu
 int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2);
+// rdm_oz.cu: 2-RDM from the 1-RDM g1 and the tensor-core Gram of the
+// symmetric / antisymmetric one-body images (reduced-precision modes, bra == ket)
+bool rdm2_oz_supported(const forte_ctx *ctx);
+int rdm2_oz(forte_ctx *ctx, const double *C, const double *g1, double *g2);
 int sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale, double *dh,
                 double *deri);
 

@@ -225,19 +225,25 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
   size_t off_g1 = off_P + sz_P;
   size_t sz_g1 = sizeof(double) * n2;
   size_t base_bytes = off_g1 + sz_g1 + 256;
-  // 2-RDM: D for ket (and bra when different), Gram partials
+  // 2-RDM: D for ket (and bra when different), Gram partials; the reduced-precision
+  // modes take the tensor-core Gram (rdm_oz.cu) for bra == ket
   const bool same = (bra == ket);
+  const bool oz = g2 && same && ctx->precision != FORTE_FP64 && rdm2_oz_supported(ctx);
   const int nsplit = 64;
   size_t off_D = (base_bytes + 255) & ~(size_t)255;
-  size_t sz_D = g2 ? sizeof(double) * (size_t)n2 * ND * (same ? 1 : 2) : 0;
+  size_t sz_D = (g2 && !oz) ? sizeof(double) * (size_t)n2 * ND * (same ? 1 : 2) : 0;
   size_t off_G = off_D + sz_D;
-  size_t sz_G = g2 ? sizeof(double) * (size_t)nsplit * n2 * n2 : 0;
+  size_t sz_G = (g2 && !oz) ? sizeof(double) * (size_t)nsplit * n2 * n2 : 0;
   int rc = ctx->sc_rdm.ensure(off_G + sz_G + 256);
   if (rc) return rc;
   char *w = (char *)ctx->sc_rdm.ptr;
   double *Tb = (double *)(w + off_T), *Tk = Tb + ND;
   double *P = (double *)(w + off_P);
   double *g1w = g1 ? g1 : (double *)(w + off_g1);
+  if (oz && !g1) {  // the Gram step reallocates sc_rdm: keep the 1-RDM elsewhere
+    if (!ctx->d_g1tmp) FORTE_CUDA_TRY(cudaMalloc(&ctx->d_g1tmp, sizeof(double) * n2));
+    g1w = ctx->d_g1tmp;
+  }
 
   // gamma: alpha rows, then beta rows on the transposed vectors
   {
@@ -272,6 +278,10 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
   FORTE_LAUNCH_CHECK();
   }
   if (!g2) return FORTE_OK;
+  if (oz) {
+    if ((rc = rdm2_oz(ctx, ket, g1w, g2))) return rc;
+    return mixed_status(ctx);  // bounded waits of the tensor-core kernel (synchronises the stream)
+  }
 
   double *Dk = (double *)(w + off_D);
   double *Db = same ? Dk : Dk + (size_t)n2 * ND;
