@@ -39,6 +39,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 80.5
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio
+OZ_PAIRS = 26  # digit pairs (i, j), 1 <= i, j <= 6, i + j <= 8, of the tensor-core RDM Gram
 
 WORKLOADS = {"cas1414": si.CAS1414, "cas1212": si.CAS1212, "cas88": si.CAS88}
 WORKLOAD_NAMES = {"cas1414": "CAS(14,14) 7a+7b in 14 orbitals, 11,778,624 determinants, seed 2, 28 factors",
@@ -196,6 +197,12 @@ def kernel_work(name, prob, n_sig64, n_sigm, n_rdm, tables):
         nt = (n * n + 63) // 64  # symmetric Gram: tiles ta <= tb of 64 x 64
         return (2.0 * 64 * 64 * nt * (nt + 1) // 2 * nd * n_rdm, "TFLOP/s", "alu", FP64_PEAK_TFLOPS,
                 "FP64 pipe, nominal")
+    if name in ("gram_oz_u", "gram_oz_v"):
+        # 26 BF16 digit-pair products (i + j <= 8 of six digits) of the Gram of the
+        # symmetric (n(n+1)/2 rows) or antisymmetric (n(n-1)/2 rows) one-body images
+        rows = n * (n + 1) // 2 if name == "gram_oz_u" else n * (n - 1) // 2
+        return (OZ_PAIRS * 2.0 * rows * rows * nd * n_rdm, "TFLOP/s", "tensor", bf16s,
+                f"bf16 dense sustained ({src})")
     return None
 
 

@@ -613,6 +613,9 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
   cudaFree(ctx->d_gT_hi); cudaFree(ctx->d_gT_lo); cudaFree(ctx->d_gT_t32); cudaFree(ctx->d_err);
   cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp);
+  for (int s = 0; s < (ctx->same_strings ? 1 : 2); ++s) {
+    cudaFree(ctx->d_hd_hi[s]); cudaFree(ctx->d_hd_lo[s]); cudaFree(ctx->d_hd_t32[s]);
+  }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

@@ -113,6 +113,10 @@ struct forte_ctx {
   uint16_t *d_gT_hi = nullptr, *d_gT_lo = nullptr;
   float *d_gT_t32 = nullptr;
   int *d_err = nullptr;         // device status word of bounded waits (0 = ok)
+  // dense same-spin string Hamiltonians for the tensor-core same-spin sigma,
+  // [N][N padded to 16] per spin (aliases when alpha and beta strings coincide)
+  uint16_t *d_hd_hi[2] = {nullptr, nullptr}, *d_hd_lo[2] = {nullptr, nullptr};
+  float *d_hd_t32[2] = {nullptr, nullptr};
   uint16_t *d_ozT = nullptr;    // [n*n][Nb padded to 64]: E_sr |Ib> of the beta strings (RDM Gram)
   double *d_g1tmp = nullptr;    // 1-RDM workspace of the tensor-core 2-RDM when the caller passes none
   float gmax = 0.f;             // max |(pq|rs)| (bounds the alpha-beta fixed-point scale)
@@ -170,6 +174,12 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
 int hdiag_build(forte_ctx *ctx);
 
 int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec);
+
+// sigma_ss_mma.cu: same-spin sigma of the reduced-precision modes as one dense
+// tensor-core GEMM per vector (S32 = same-spin part, FP32)
+bool ss_mma_supported(const forte_ctx *ctx);
+int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
+                  void *tw, float *S32, int nvec, int mode);
 
 // sigma_mixed.cu
 int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode);

@@ -41,19 +41,6 @@ constexpr int MX_TILE_N = 128;
 constexpr int MX_OFF_B = 32768;               // A: 32 KB
 constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
 
-// Round-to-nearest-even of an FP64 value to `drop` fewer mantissa bits
-// (IEEE-754 binary64 layout; drop = 45 gives a BF16 value, 42 a TF32 value).
-__device__ __forceinline__ double rne_drop(double x, int drop) {
-  unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned long long lsb = (b >> drop) & 1ull;
-  b += ((1ull << (drop - 1)) - 1ull) + lsb;
-  b &= ~((1ull << drop) - 1ull);
-  return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ uint16_t bf16_bits(double exact_bf16) {
-  return __bfloat16_as_ushort(__double2bfloat16(exact_bf16));
-}
-
 // ------------------------------------------------------------ conversion kernels
 
 // C (FP64 [v][NA][NB]) -> C32 (FP32, same layout) and the tensor-core copy in a
@@ -477,14 +464,18 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
   const size_t nf = (size_t)nvec * ND, np = (size_t)nvec * NA * NBp;
   // scratch: C32, T1, T2, S32 (FP32, ND each) + tensor-core copy (2 x u16 or 1 x f32 per
   // padded element) + per-vector max |C|
-  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + 1024 + 256 + sizeof(unsigned) * nvec;
+  // + the transposed copies of the tensor-core same-spin GEMM (4 bytes per element)
+  const bool ssm = ss_mma_supported(ctx);
+  const size_t ntw = ssm ? (size_t)nvec * NB * ((NA + 15) & ~15LL) * 4 : 0;
+  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + ntw + 1024 + 512 + sizeof(unsigned) * nvec;
   if ((rc = ctx->sc_mixed.ensure(bytes))) return rc;
   float *C32 = (float *)ctx->sc_mixed.ptr;
   float *T1 = C32 + nf, *T2 = T1 + nf, *S32 = T2 + nf;
   uint8_t *tc = (uint8_t *)(((uintptr_t)(S32 + nf) + 255) & ~(uintptr_t)255);
   uint16_t *Chi = (uint16_t *)tc, *Clo = Chi + np;
   float *Ct32 = (float *)tc;
-  unsigned *cmax = (unsigned *)(((uintptr_t)(tc + np * 4) + 255) & ~(uintptr_t)255);
+  uint8_t *tw = (uint8_t *)(((uintptr_t)(tc + np * 4) + 255) & ~(uintptr_t)255);
+  unsigned *cmax = (unsigned *)(((uintptr_t)(tw + ntw) + 255) & ~(uintptr_t)255);
   FORTE_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned) * nvec, st));
   {
     const long long per = NA * NBp;
@@ -496,7 +487,11 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
       k_split<FORTE_TF32><<<grid, 256, 0, st>>>(C, C32, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
     FORTE_LAUNCH_CHECK();
   }
-  if ((rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec))) return rc;
+  if (ssm)
+    rc = same_spin_mma(ctx, C, Chi, Clo, Ct32, tw, S32, nvec, mode);
+  else
+    rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec);
+  if (rc) return rc;
   if (nkA > 0 && nkB > 0) {
     const int nN = ctx->npair <= 112 ? 112 : 128;
     const size_t smem = mx_smem_bytes(NB);

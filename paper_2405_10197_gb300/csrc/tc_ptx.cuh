@@ -4,6 +4,7 @@
 // the 128-byte swizzle.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include "forte_internal.h"
@@ -120,5 +121,33 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, vol
   return true;
 }
 
+
+// Round-to-nearest-even of an FP64 value to `drop` fewer mantissa bits
+// (IEEE-754 binary64 layout; drop = 45 gives a BF16 value, 42 a TF32 value).
+__device__ __forceinline__ double rne_drop(double x, int drop) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long lsb = (b >> drop) & 1ull;
+  b += ((1ull << (drop - 1)) - 1ull) + lsb;
+  b &= ~((1ull << drop) - 1ull);
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ uint16_t bf16_bits(double exact_bf16) {
+  return __bfloat16_as_ushort(__double2bfloat16(exact_bf16));
+}
+
+// TMA: one tiled copy of a 3-D box (x = innermost element index, y = row, z = matrix)
+// into shared memory, completing `bytes` on the mbarrier; arrive with the byte count.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *tmap, int x, int y, int z, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_map(const void *tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
+}
 
 }  // namespace forte

@@ -1,5 +1,5 @@
-"""GPU parity of the reduced-precision sigma (tcgen05 alpha-beta GEMM in TF32 or
-split BF16, FP32 same-spin terms) and of the mixed-precision Davidson with FP64
+"""GPU parity of the reduced-precision sigma (tcgen05 alpha-beta GEMM and dense
+tcgen05 same-spin GEMM, in TF32 or split BF16) and of the mixed-precision Davidson with FP64
 refinement, against the CPU oracle.
 
 Tolerances (max|S - S_ref| / max|S_ref|), from the arithmetic:
@@ -27,7 +27,8 @@ import paper_2405_10197_gb300 as fg  # noqa: E402
 
 TOL = {fg.FORTE_BF16X2: 5e-5, fg.FORTE_TF32: 5e-3}
 MODES = [fg.FORTE_BF16X2, fg.FORTE_TF32]
-CASES = [(2, 1, 1), (4, 2, 2), (5, 2, 3), (6, 3, 3), (7, 3, 2), (8, 4, 4), (9, 2, 5), (10, 5, 5)]
+CASES = [(2, 1, 1), (4, 2, 2), (5, 2, 3), (6, 3, 3), (7, 3, 2), (8, 4, 4), (9, 2, 5), (10, 5, 5), (6, 3, 0),
+         (5, 0, 2), (11, 5, 4)]
 
 
 def _rel(a, b):
