@@ -106,6 +106,16 @@ static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, 
   return sigma_mixed(ctx, C, S, nvec, mode);
 }
 
+static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
+  if (nvec <= 0) return FORTE_OK;
+  if (mode == FORTE_FP64) {
+    set_error("FP32 vectors need a reduced-precision sigma");
+    return FORTE_ERR_ARG;
+  }
+  ctx->n_sigma_mixed += nvec;
+  return sigma_mixed(ctx, C, S, nvec, mode);
+}
+
 // ----------------------------------------------------------------- Davidson
 
 struct DvResult {
@@ -154,14 +164,15 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
 // ~amp, entries amp*sqrt(12/n)*(u-1/2) with u = splitmix64(i + (k+1)*gamma)
 // in [0,1).  The perturbation couples the spin-flip symmetry sectors so that
 // roots of every total spin are reachable from closed-shell guesses.
-__global__ void k_guess(double *__restrict__ x, long long n, long long idx, int k, double amp) {
+template <typename T>
+__global__ void k_guess(T *__restrict__ x, long long n, long long idx, int k, double amp) {
   const double scale = amp * sqrt(12.0 / (double)n);
   const unsigned long long key = (unsigned long long)(k + 1) * 0x9E3779B97F4A7C15ull;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     unsigned long long z = splitmix64((unsigned long long)i + key);
     double u = (double)(z >> 11) * 0x1.0p-53;
-    x[i] = scale * (u - 0.5) + (i == idx ? 1.0 : 0.0);
+    x[i] = (T)(scale * (u - 0.5) + (i == idx ? 1.0 : 0.0));
   }
 }
 
@@ -192,9 +203,25 @@ static int fix_sign(forte_ctx *ctx, double *x, long long n) {
   return FORTE_OK;
 }
 
-// Davidson-Liu with the sigma of `mode`; all vector arithmetic FP64.
-// guess: ng device vectors (may be 0 -> unit vectors at the lowest H_II).
-// On return the Ritz vectors are in out_roots [nroots][N].
+// Ritz vectors X = B U (first nroots columns of the coefficients) into the FP64
+// output; FP32 bases combine into the workspace W first.
+static int ritz_out(forte_ctx *ctx, const double *B, int k, long long N, const double *coef, int nroots, double *,
+                    double *out) {
+  return vk_combine(ctx, B, k, N, coef, nroots, out, N, N);
+}
+static int ritz_out(forte_ctx *ctx, const float *B, int k, long long N, const double *coef, int nroots, float *W,
+                    double *out) {
+  int rc = vk_combine(ctx, B, k, N, coef, nroots, W, N, N);
+  if (rc) return rc;
+  return vk_convert(ctx, W, out, (long long)nroots * N);
+}
+
+// Davidson-Liu with the sigma of `mode` on vectors of type T: FP64, or FP32 for
+// the reduced-precision phase that precedes the FP64 refinement (the subspace
+// matrix and its eigenproblem are FP64 in both).
+// guess: ng FP64 device vectors (may be 0 -> unit vectors at the lowest H_II).
+// On return the Ritz vectors are in out_roots [nroots][N] (FP64).
+template <typename T>
 static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const double *guess, int ng,
                         int max_iter, double *out_roots, DvResult &res) {
   cudaStream_t st = ctx->stream;
@@ -207,14 +234,14 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
   keep = std::min(keep, maxsub);
   // device layout: B[maxsub], S[maxsub], T[nroots], W[keep] vectors; then small arrays
   size_t nvecs = (size_t)maxsub * 2 + nroots + keep;
-  size_t small_off = sizeof(double) * nvecs * N;
+  size_t small_off = ((sizeof(T) * nvecs * N + 255) / 256) * 256;
   size_t small_bytes = sizeof(double) * (64 * 64 + 4 * 64 + 64);
   int rc = ctx->sc_dv.ensure(small_off + small_bytes + 256);
   if (rc) return rc;
-  double *B = (double *)ctx->sc_dv.ptr;
-  double *S = B + (size_t)maxsub * N;
-  double *T = S + (size_t)maxsub * N;
-  double *W = T + (size_t)nroots * N;
+  T *B = (T *)ctx->sc_dv.ptr;
+  T *S = B + (size_t)maxsub * N;
+  T *Tv = S + (size_t)maxsub * N;
+  T *W = Tv + (size_t)nroots * N;
   double *d_coef = (double *)((char *)ctx->sc_dv.ptr + small_off);  // [64*64]
   double *d_u = d_coef + 64 * 64;                                    // [64]
   double *d_d0 = d_u + 64;                                           // [65]
@@ -226,7 +253,13 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     // orthonormalise the supplied vectors into B
     std::vector<double> h_d(65);
     for (int i = 0; i < ng && k < maxsub; ++i) {
-      const double *t = guess + (size_t)i * N;
+      const T *t;
+      if (sizeof(T) == sizeof(double)) {
+        t = (const T *)(const void *)(guess + (size_t)i * N);
+      } else {  // the FP32 copy of the guess goes into the next basis slot first
+        if ((rc = vk_convert(ctx, guess + (size_t)i * N, (float *)(void *)(B + (size_t)k * N), N))) return rc;
+        t = B + (size_t)k * N;
+      }
       FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, B + (size_t)k * N, d_d0, N))) return rc;
       FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
@@ -249,12 +282,12 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     if ((rc = vk_argmin_k(ctx, ctx->d_hdiag, N, std::min<long long>(N, need + k), idx.data()))) return rc;
     int used = 0;
     for (size_t c = 0; c < idx.size() && used < need && c < (size_t)std::min<long long>(N, need + k); ++c) {
-      double *b = B + (size_t)k * N;
+      T *b = B + (size_t)k * N;
       {
         unsigned nbk = (unsigned)std::min<long long>((N + 255) / 256, 152LL * 16);
         {
           FORTE_PROF(ctx, "guess");
-          k_guess<<<nbk, 256, 0, st>>>(b, N, idx[c], k, 0.02);
+          k_guess<T><<<nbk, 256, 0, st>>>(b, N, idx[c], k, 0.02);
         FORTE_LAUNCH_CHECK();
         }
       }
@@ -309,7 +342,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       std::vector<double> u(k);
       for (int i = 0; i < k; ++i) u[i] = U[(size_t)i * k + r];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_u, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-      if ((rc = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, T + (size_t)r * N,
+      if ((rc = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, Tv + (size_t)r * N,
                                     d_d0 + r, N)))
         return rc;
     }
@@ -330,7 +363,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       for (int i = 0; i < k; ++i)
         for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
-      if ((rc = vk_combine(ctx, B, k, N, d_coef, nroots, out_roots, N, N))) return rc;
+      if ((rc = ritz_out(ctx, B, k, N, d_coef, nroots, W, out_roots))) return rc;
       res.converged = all || (k >= N);
       return FORTE_OK;
     }
@@ -343,9 +376,9 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
         for (int c = 0; c < keep; ++c) coef[(size_t)i * keep + c] = U[(size_t)i * k + c];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
       if ((rc = vk_combine(ctx, B, k, N, d_coef, keep, W, N, N))) return rc;
-      FORTE_CUDA_TRY(cudaMemcpyAsync(B, W, sizeof(double) * keep * N, cudaMemcpyDeviceToDevice, st));
+      FORTE_CUDA_TRY(cudaMemcpyAsync(B, W, sizeof(T) * keep * N, cudaMemcpyDeviceToDevice, st));
       if ((rc = vk_combine(ctx, S, k, N, d_coef, keep, W, N, N))) return rc;
-      FORTE_CUDA_TRY(cudaMemcpyAsync(S, W, sizeof(double) * keep * N, cudaMemcpyDeviceToDevice, st));
+      FORTE_CUDA_TRY(cudaMemcpyAsync(S, W, sizeof(T) * keep * N, cudaMemcpyDeviceToDevice, st));
       std::fill(G.begin(), G.end(), 0.0);
       for (int c = 0; c < keep; ++c) Gat(c, c) = w[c];
       k = keep;
@@ -354,8 +387,8 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     for (int r = 0; r < nroots; ++r) {
       if (res.rn[r] < tol) continue;
       if (k >= maxsub) break;
-      double *t = T + (size_t)r * N;
-      double *b = B + (size_t)k * N;
+      T *t = Tv + (size_t)r * N;
+      T *b = B + (size_t)k * N;
       std::vector<double> h_d(65);
       FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, b, d_d0, N))) return rc;     // copy + B^T t + |t|^2
@@ -376,7 +409,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       for (int i = 0; i < k; ++i)
         for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
-      if ((rc = vk_combine(ctx, B, k, N, d_coef, nroots, out_roots, N, N))) return rc;
+      if ((rc = ritz_out(ctx, B, k, N, d_coef, nroots, W, out_roots))) return rc;
       return FORTE_OK;
     }
     if ((rc = sigma_dispatch(ctx, B + (size_t)k_old * N, S + (size_t)k_old * N, k - k_old, mode))) return rc;
@@ -425,7 +458,21 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
     return vk_orth_update(ctx, V, nk, N, d_b, v, v, d_a, N);
   };
   FORTE_CUDA_TRY(cudaMemcpyAsync(V, X0, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
+  // the start vectors come from a reduced-precision (FP32) phase: orthonormalise
+  // them in FP64, since the Rayleigh-Ritz step below takes V as orthonormal
+  {
+    std::vector<double> hn(2);
+    for (int r = 0; r < nroots; ++r) {
+      double *v = V + (size_t)r * N;
+      if (r > 0 && (rc = project(v, r))) return rc;
+      if ((rc = vk_multidot(ctx, v, 1, N, v, N, d_s))) return rc;
+      if ((rc = fetch(d_s, 1, hn.data()))) return rc;
+      if (!(hn[0] > 0.0) || !isfinite(hn[0])) { set_error("degenerate start vector in refinement"); return FORTE_ERR_NUMERIC; }
+      if ((rc = vk_scale(ctx, v, v, 1.0 / sqrt(hn[0]), N))) return rc;
+    }
+  }
   if ((rc = sigma_dispatch(ctx, V, HV, nroots, FORTE_FP64))) return rc;
+  double prev_rn = INFINITY;
   int k = nroots;
   std::vector<double> G, Gk, w, U, coef, h(66);
   res.E.assign(nroots, 0.0);
@@ -468,6 +515,11 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
       if (!(res.rn[r] < tol)) all = false;
     }
     res.iters = outer;
+    // an outer step that does not halve the residual means the reduced-precision
+    // inner operator no longer resolves the correction: continue with FP64 ones
+    const double max_rn = *std::max_element(res.rn.begin(), res.rn.end());
+    if (outer > 0 && max_rn > 0.5 * prev_rn) inner_mode = FORTE_FP64;
+    prev_rn = max_rn;
     if (all || outer >= max_outer) {
       FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
       res.converged = all;
@@ -731,7 +783,8 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
   DvResult res;
   ctx->nroots_done = 0;
   if (ctx->precision == FORTE_FP64) {
-    rc = davidson_run(ctx, nroots, tol, FORTE_FP64, ctx->d_guess, ctx->nguess, ctx->dv_max_iter, ctx->d_roots, res);
+    rc = davidson_run<double>(ctx, nroots, tol, FORTE_FP64, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
+                              ctx->d_roots, res);
     if (rc) return rc;
     ctx->dv_iters = res.iters;
   } else {
@@ -739,8 +792,8 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     // operator can still resolve, then FP64 Jacobi-Davidson refinement whose
     // inner solves use the mixed sigma
     double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 1e-2 : 1e-3);
-    rc = davidson_run(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
-                      ctx->d_roots, res);
+    rc = davidson_run<float>(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
+                             ctx->d_roots, res);
     if (rc) return rc;
     if ((rc = mixed_status(ctx))) return rc;
     int it_in = res.iters;

@@ -180,24 +180,36 @@ int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float
 bool ss_mma_supported(const forte_ctx *ctx);
 int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
                   void *tw, float *S32, int nvec, int mode);
+int same_spin_mma(forte_ctx *ctx, const float *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
+                  void *tw, float *S32, int nvec, int mode);
 
 // sigma_mixed.cu
 int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode);
+int sigma_mixed(forte_ctx *ctx, const float *C, float *S, int nvec, int mode);  // FP32 vectors
 int mixed_setup(forte_ctx *ctx);
 int mixed_status(forte_ctx *ctx);
 
-// vec_kernels.cu: Davidson building blocks (all FP64, HBM-bound).  Reductions
-// use the context's sc_small buffer for block partials.
-int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n,
-                double *out);
-int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb,
-               double *out, long long ldo, long long n);
-int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld,
-                        const double *u, double theta, double guard, double *t, double *rnorm2,
-                        long long n);
-int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c,
-                   const double *t_in, double *t_out, double *dots_out, long long n);
+// vec_kernels.cu: Davidson building blocks on FP64 vectors and on the FP32 vectors
+// of the reduced-precision phase (HBM-bound; FP32 ones accumulate per warp in
+// FP32, beyond that in FP64).  Reductions use the context's sc_small buffer.
+int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n, double *out);
+int vk_multidot(forte_ctx *ctx, const float *V, int nv, long long ld, const float *x, long long n, double *out);
+int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb, double *out,
+               long long ldo, long long n);
+int vk_combine(forte_ctx *ctx, const float *V, int nv, long long ld, const double *coef, int ncomb, float *out,
+               long long ldo, long long n);
+int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld, const double *u,
+                        double theta, double guard, double *t, double *rnorm2, long long n);
+int vk_residual_precond(forte_ctx *ctx, const float *B, const float *S, int k, long long ld, const double *u,
+                        double theta, double guard, float *t, double *rnorm2, long long n);
+int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c, const double *t_in,
+                   double *t_out, double *dots_out, long long n);
+int vk_orth_update(forte_ctx *ctx, const float *B, int k, long long ld, const double *c, const float *t_in,
+                   float *t_out, double *dots_out, long long n);
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n);
+int vk_scale(forte_ctx *ctx, float *x, const float *src, double alpha, long long n);
+int vk_convert(forte_ctx *ctx, const double *x, float *y, long long n);
+int vk_convert(forte_ctx *ctx, const float *x, double *y, long long n);
 int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n);
 int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, double *z, double *dot_out,
                    long long n);

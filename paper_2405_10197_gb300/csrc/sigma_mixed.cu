@@ -47,23 +47,23 @@ constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
 // row-padded layout [v][NA][NBp] (NBp multiple of 16, zero padding); also the
 // per-vector bound cmax_bits[v] = bits of max |C| (non-negative floats order as
 // their bit patterns).  grid.y = vector.
-template <int MODE>
-__global__ void k_split(const double *__restrict__ C, float *__restrict__ C32, uint16_t *__restrict__ hi,
+template <int MODE, typename TI>
+__global__ void k_split(const TI *__restrict__ C, float *__restrict__ C32, uint16_t *__restrict__ hi,
                         uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA, long long NB,
                         long long NBp, unsigned *__restrict__ cmax_bits) {
   __shared__ unsigned red[32];
   const long long v = blockIdx.y;
   const long long per = NA * NBp;
-  const double *Cv = C + v * NA * NB;
-  float *C32v = C32 + v * NA * NB;
+  const TI *Cv = C + v * NA * NB;
+  float *C32v = C32 ? C32 + v * NA * NB : nullptr;
   unsigned mx = 0u;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per;
        i += (long long)gridDim.x * blockDim.x) {
     const long long b = i % NBp, row = i / NBp;
     double x = 0.0;
     if (b < NB) {
-      x = Cv[row * NB + b];
-      C32v[row * NB + b] = (float)x;
+      x = (double)Cv[row * NB + b];
+      if (C32v) C32v[row * NB + b] = (float)x;
     }
     mx = max(mx, __float_as_uint(fabsf((float)x)));
     if (MODE == FORTE_BF16X2) {
@@ -123,13 +123,13 @@ constexpr int WS_ACC = 4;                                 // TMEM accumulators o
 constexpr int WS_OFF_ACC = MX_OFF_B + WS_STAGES * MX_STAGE;
 // warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 8-15 epilogue
 
-template <int MODE>
+template <int MODE, typename TO>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabJ, int nN, long long NA,
              long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
-             const float *__restrict__ Sss, double *__restrict__ S, int *__restrict__ err) {
+             const float *__restrict__ Sss, TO *__restrict__ S, int *__restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   // the swizzle pattern is a function of the shared-space address: align there
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -407,10 +407,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     }
   } else {
     const float *ss = Sss + v * v64 + Ia * NB;
-    double *out = S + v * v64 + Ia * NB;
+    TO *out = S + v * v64 + Ia * NB;
     for (long long i = tid; i < NB; i += MX_THREADS) {
       const long long tot = (long long)acc_hi[i] * 1048576LL + (long long)acc_lo[i];
-      out[i] = (double)ss[i] + ldexp((double)tot, -Sx);
+      out[i] = (TO)((double)ss[i] + ldexp((double)tot, -Sx));
     }
   }
   tc_fence_before();
@@ -446,7 +446,9 @@ int mixed_setup(forte_ctx *ctx) {
   return FORTE_OK;
 }
 
-int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
+// C, S: FP64 vectors, or the FP32 vectors of the reduced-precision Davidson phase.
+template <typename T>
+static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   if (mode != FORTE_BF16X2 && mode != FORTE_TF32) {
     set_error("unknown precision mode %d", mode);
     return FORTE_ERR_ARG;
@@ -470,6 +472,9 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
   const size_t bytes = 4 * nf * sizeof(float) + np * 4 + ntw + 1024 + 512 + sizeof(unsigned) * nvec;
   if ((rc = ctx->sc_mixed.ensure(bytes))) return rc;
   float *C32 = (float *)ctx->sc_mixed.ptr;
+  // the FP32 copy of C feeds only the CSR fallback of the same-spin term
+  float *C32w = (!ssm && sizeof(T) == 8) ? C32 : nullptr;
+  const float *C32r = sizeof(T) == 8 ? C32 : (const float *)(const void *)C;
   float *T1 = C32 + nf, *T2 = T1 + nf, *S32 = T2 + nf;
   uint8_t *tc = (uint8_t *)(((uintptr_t)(S32 + nf) + 255) & ~(uintptr_t)255);
   uint16_t *Chi = (uint16_t *)tc, *Clo = Chi + np;
@@ -482,15 +487,15 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
     dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
     if (mode == FORTE_BF16X2)
-      k_split<FORTE_BF16X2><<<grid, 256, 0, st>>>(C, C32, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+      k_split<FORTE_BF16X2, T><<<grid, 256, 0, st>>>(C, C32w, Chi, Clo, nullptr, NA, NB, NBp, cmax);
     else
-      k_split<FORTE_TF32><<<grid, 256, 0, st>>>(C, C32, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+      k_split<FORTE_TF32, T><<<grid, 256, 0, st>>>(C, C32w, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
     FORTE_LAUNCH_CHECK();
   }
   if (ssm)
     rc = same_spin_mma(ctx, C, Chi, Clo, Ct32, tw, S32, nvec, mode);
   else
-    rc = same_spin_f32(ctx, C32, S32, T1, T2, nvec);
+    rc = same_spin_f32(ctx, C32r, S32, T1, T2, nvec);
   if (rc) return rc;
   if (nkA > 0 && nkB > 0) {
     const int nN = ctx->npair <= 112 ? 112 : 128;
@@ -501,26 +506,36 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) 
     }
     dim3 grid((unsigned)NA, (unsigned)nvec);
     if (mode == FORTE_BF16X2) {
-      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2>));
+      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2, T>));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
-      k_ab_mma<FORTE_BF16X2><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
+      k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                              ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
                                                              ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
-      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32>));
+      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32, T>));
       FORTE_PROF(ctx, "ab_mma_tf32");
-      k_ab_mma<FORTE_TF32><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
+      k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                            ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
                                                            ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     }
-  } else {
+  } else if (sizeof(T) == 8) {
     FORTE_PROF(ctx, "f32_to_f64");
-    k_f32_to_f64<<<(unsigned)std::min<size_t>((nf + 255) / 256, 152 * 32), 256, 0, st>>>(S32, S, (long long)nf);
+    k_f32_to_f64<<<(unsigned)std::min<size_t>((nf + 255) / 256, 152 * 32), 256, 0, st>>>(S32, (double *)(void *)S,
+                                                                                     (long long)nf);
     FORTE_LAUNCH_CHECK();
+  } else {
+    FORTE_CUDA_TRY(cudaMemcpyAsync((void *)S, S32, sizeof(float) * nf, cudaMemcpyDeviceToDevice, st));
   }
   return FORTE_OK;
+}
+
+int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
+  return sigma_mixed_t(ctx, C, S, nvec, mode);
+}
+int sigma_mixed(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
+  return sigma_mixed_t(ctx, C, S, nvec, mode);
 }
 
 // Device status of bounded waits: FORTE_OK, or FORTE_ERR_TIMEOUT (and reset).

@@ -260,16 +260,16 @@ __global__ void k_dense_h(const int *__restrict__ ptr, const int *__restrict__ c
 }
 
 // Transposed split: Ct[v][Ib][Ia] (pitch NAp, zero for Ia >= NA) from C[v][Ia][Ib].
-template <int MODE>
-__global__ void k_split_t(const double *__restrict__ C, long long NA, long long NB, long long NAp,
+template <int MODE, typename TI>
+__global__ void k_split_t(const TI *__restrict__ C, long long NA, long long NB, long long NAp,
                           uint16_t *__restrict__ hi, uint16_t *__restrict__ lo, float *__restrict__ t32) {
   __shared__ double tile[32][33];
   const long long v = blockIdx.z;
   const long long a0 = (long long)blockIdx.x * 32, b0 = (long long)blockIdx.y * 32;
-  const double *Cv = C + v * NA * NB;
+  const TI *Cv = C + v * NA * NB;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const long long a = a0 + i, b = b0 + threadIdx.x;
-    tile[i][threadIdx.x] = (a < NA && b < NB) ? Cv[a * NB + b] : 0.0;
+    tile[i][threadIdx.x] = (a < NA && b < NB) ? (double)Cv[a * NB + b] : 0.0;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -364,8 +364,9 @@ static int ss_dense_setup(forte_ctx *ctx) {
 // S32[v] = same-spin sigma of C[v] (FP64 input; Chi/Clo or Ct32 are the row-split
 // copies [nvec][NA][NBp] made by the caller).  `tw` is workspace for the
 // transposed copies: nvec * NB * NAp * 4 bytes.
-int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
-                  void *tw, float *S32, int nvec, int mode) {
+template <typename TI>
+static int same_spin_mma_t(forte_ctx *ctx, const TI *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
+                           void *tw, float *S32, int nvec, int mode) {
   int rc = ss_dense_setup(ctx);
   if (rc) return rc;
   cudaStream_t st = ctx->stream;
@@ -377,9 +378,9 @@ int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const ui
     dim3 tb(32, 8), g((unsigned)((NAp + 31) / 32), (unsigned)((NB + 31) / 32), (unsigned)nvec);
     FORTE_PROF(ctx, "split_t");
     if (bf)
-      k_split_t<FORTE_BF16X2><<<g, tb, 0, st>>>(C, NA, NB, NAp, Thi, Tlo, nullptr);
+      k_split_t<FORTE_BF16X2, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, Thi, Tlo, nullptr);
     else
-      k_split_t<FORTE_TF32><<<g, tb, 0, st>>>(C, NA, NB, NAp, nullptr, nullptr, Tt);
+      k_split_t<FORTE_TF32, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, nullptr, nullptr, Tt);
     FORTE_LAUNCH_CHECK();
   }
   SsmMaps maps;
@@ -422,6 +423,15 @@ int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const ui
     FORTE_LAUNCH_CHECK();
   }
   return FORTE_OK;
+}
+
+int same_spin_mma(forte_ctx *ctx, const double *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
+                  void *tw, float *S32, int nvec, int mode) {
+  return same_spin_mma_t(ctx, C, Chi, Clo, Ct32, tw, S32, nvec, mode);
+}
+int same_spin_mma(forte_ctx *ctx, const float *C, const uint16_t *Chi, const uint16_t *Clo, const float *Ct32,
+                  void *tw, float *S32, int nvec, int mode) {
+  return same_spin_mma_t(ctx, C, Chi, Clo, Ct32, tw, S32, nvec, mode);
 }
 
 }  // namespace forte

@@ -1,6 +1,8 @@
-// Davidson-Liu building blocks on long FP64 vectors (step a7).  Each kernel
-// streams its operands once; reductions go through per-block partial sums
-// and a second pass, so results do not depend on atomic ordering.
+// Davidson-Liu building blocks on long vectors (step a7), for FP64 vectors and
+// for the FP32 vectors of the reduced-precision phase.  Each kernel streams its
+// operands once; reductions go through per-block partial sums (FP64) and a second
+// pass, so results do not depend on atomic ordering.  FP32 kernels accumulate in
+// FP32 within a warp and in FP64 across warps and blocks.
 #include "forte_internal.h"
 
 namespace forte {
@@ -32,6 +34,23 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return red[0];
 }
 
+// Block-wide sum of per-thread values of type T: warp sums in T, the sum over
+// warps in FP64 (one warp); every thread returns the total.  red holds 32 doubles.
+template <typename T>
+__device__ __forceinline__ double block_sum_t(T v, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = (double)v;
+  __syncthreads();
+  double t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  return red[0];
+}
+
 // part[b][m] -> out[m] (sum over b).  grid.x = m.
 __global__ void k_sum_partials(const double *__restrict__ part, int nblk, int m, double *__restrict__ out) {
   __shared__ double red[32];
@@ -42,110 +61,116 @@ __global__ void k_sum_partials(const double *__restrict__ part, int nblk, int m,
 }
 
 // part[block][i] = sum over the block's chunk of V_i . x   (i < nv)
-__global__ void __launch_bounds__(VK_THREADS) k_multidot(const double *__restrict__ V, int nv, long long ld,
-                                                         const double *__restrict__ x, long long n,
+template <typename T>
+__global__ void __launch_bounds__(VK_THREADS) k_multidot(const T *__restrict__ V, int nv, long long ld,
+                                                         const T *__restrict__ x, long long n,
                                                          double *__restrict__ part) {
   __shared__ double red[32];
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
-  double xr[VK_EPT];
+  T xr[VK_EPT];
 #pragma unroll
   for (int k = 0; k < VK_EPT; ++k) {
     long long j = base + (long long)k * VK_THREADS;
-    xr[k] = (j < n) ? x[j] : 0.0;
+    xr[k] = (j < n) ? x[j] : T(0);
   }
   for (int i = 0; i < nv; ++i) {
-    const double *v = V + (long long)i * ld;
-    double a = 0.0;
+    const T *v = V + (long long)i * ld;
+    T a = 0;
 #pragma unroll
     for (int k = 0; k < VK_EPT; ++k) {
       long long j = base + (long long)k * VK_THREADS;
       if (j < n) a += v[j] * xr[k];
     }
-    a = block_sum(a, red);
-    if (threadIdx.x == 0) part[(long long)blockIdx.x * nv + i] = a;
+    const double at = block_sum_t<T>(a, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * nv + i] = at;
   }
 }
 
-// out_j = sum_i coef[i*ncomb + j] V_i  (j < ncomb <= 32)
-__global__ void __launch_bounds__(VK_THREADS) k_combine(const double *__restrict__ V, int nv, long long ld,
-                                                        const double *__restrict__ coef, int ncomb,
-                                                        double *__restrict__ out, long long ldo, long long n) {
-  __shared__ double sc[VK_MAXV * 32];
-  for (int i = threadIdx.x; i < nv * ncomb; i += blockDim.x) sc[i] = coef[i];
+// out_{c0+c} = sum_i coef[i*ncomb + c0 + c] V_i  for c < NC.  NC is a template
+// parameter: the FP64 pipe of this GPU is narrow enough that issuing
+// predicated-off multiply-adds for unused outputs would dominate the kernel.
+template <int NC, typename T>
+__global__ void __launch_bounds__(VK_THREADS) k_combine(const T *__restrict__ V, int nv, long long ld,
+                                                        const double *__restrict__ coef, int ncomb, int c0,
+                                                        T *__restrict__ out, long long ldo, long long n) {
+  __shared__ T sc[VK_MAXV * NC];
+  for (int i = threadIdx.x; i < nv * NC; i += blockDim.x) sc[i] = (T)coef[(i / NC) * ncomb + c0 + i % NC];
   __syncthreads();
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x) {
-    double acc[32];
+    T acc[NC];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[c] = 0;
+#pragma unroll 4
     for (int i = 0; i < nv; ++i) {
-      double v = V[(long long)i * ld + j];
+      const T v = V[(long long)i * ld + j];
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
-        if (c < ncomb) acc[c] += sc[i * ncomb + c] * v;
+      for (int c = 0; c < NC; ++c) acc[c] += sc[i * NC + c] * v;
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < ncomb) out[(long long)c * ldo + j] = acc[c];
+    for (int c = 0; c < NC; ++c) out[(long long)(c0 + c) * ldo + j] = acc[c];
   }
 }
 
 // r = sum_i u_i S_i - theta sum_i u_i B_i ;  t = r / (theta - hdiag) (guarded);
 // part[block] = sum r^2 over the block's chunk.
+template <typename T>
 __global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
-    const double *__restrict__ B, const double *__restrict__ S, int k, long long ld,
+    const T *__restrict__ B, const T *__restrict__ S, int k, long long ld,
     const double *__restrict__ u, double theta, const double *__restrict__ hd, double guard,
-    double *__restrict__ t, long long n, double *__restrict__ part) {
+    T *__restrict__ t, long long n, double *__restrict__ part) {
   __shared__ double red[32];
-  __shared__ double su[VK_MAXV];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) su[i] = u[i];
+  __shared__ T su[VK_MAXV];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) su[i] = (T)u[i];
   __syncthreads();
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
-  double rr = 0.0;
+  const T th = (T)theta;
+  T rr = 0;
 #pragma unroll 4
   for (int e = 0; e < VK_EPT; ++e) {
     long long j = base + (long long)e * VK_THREADS;
     if (j >= n) break;
-    double hx = 0.0, x = 0.0;
+    T hx = 0, x = 0;
     for (int i = 0; i < k; ++i) {
       hx += su[i] * S[(long long)i * ld + j];
       x += su[i] * B[(long long)i * ld + j];
     }
-    double r = hx - theta * x;
+    const T r = hx - th * x;
     rr += r * r;
     double den = theta - hd[j];
     if (fabs(den) < guard) den = (den >= 0.0) ? guard : -guard;
-    t[j] = r / den;
+    t[j] = r / (T)den;
   }
-  rr = block_sum(rr, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = rr;
+  const double rt = block_sum_t<T>(rr, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = rt;
 }
 
 // t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2
-__global__ void __launch_bounds__(VK_THREADS) k_orth_update(const double *__restrict__ Bm, int k,
+template <typename T>
+__global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict__ Bm, int k,
                                                             long long ld, const double *__restrict__ c,
-                                                            const double *t_in, double *t_out, long long n,
+                                                            const T *t_in, T *t_out, long long n,
                                                             double *__restrict__ part) {
   __shared__ double red[32];
-  __shared__ double sc[VK_MAXV];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = c[i];
+  __shared__ T sc[VK_MAXV];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = (T)c[i];
   __syncthreads();
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
-  double tr[VK_EPT];
+  T tr[VK_EPT];
 #pragma unroll
   for (int e = 0; e < VK_EPT; ++e) {
     long long j = base + (long long)e * VK_THREADS;
-    tr[e] = (j < n) ? t_in[j] : 0.0;
+    tr[e] = (j < n) ? t_in[j] : T(0);
   }
   for (int i = 0; i < k; ++i) {
-    const double *b = Bm + (long long)i * ld;
+    const T *b = Bm + (long long)i * ld;
 #pragma unroll
     for (int e = 0; e < VK_EPT; ++e) {
       long long j = base + (long long)e * VK_THREADS;
       if (j < n) tr[e] -= sc[i] * b[j];
     }
   }
-  double nn = 0.0;
+  T nn = 0;
 #pragma unroll
   for (int e = 0; e < VK_EPT; ++e) {
     long long j = base + (long long)e * VK_THREADS;
@@ -155,18 +180,18 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const double *__rest
     }
   }
   for (int i = 0; i < k; ++i) {
-    const double *b = Bm + (long long)i * ld;
-    double a = 0.0;
+    const T *b = Bm + (long long)i * ld;
+    T a = 0;
 #pragma unroll
     for (int e = 0; e < VK_EPT; ++e) {
       long long j = base + (long long)e * VK_THREADS;
       if (j < n) a += b[j] * tr[e];
     }
-    a = block_sum(a, red);
-    if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + i] = a;
+    const double at = block_sum_t<T>(a, red);
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + i] = at;
   }
-  nn = block_sum(nn, red);
-  if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nn;
+  const double nt = block_sum_t<T>(nn, red);
+  if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nt;
 }
 
 // y = a x + b y
@@ -199,10 +224,19 @@ __global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__rest
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void k_scale(double *__restrict__ x, const double *__restrict__ src, double alpha, long long n) {
+template <typename T>
+__global__ void k_scale(T *__restrict__ x, const T *__restrict__ src, double alpha, long long n) {
+  const T al = (T)alpha;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += (long long)gridDim.x * blockDim.x)
-    x[j] = alpha * src[j];
+    x[j] = al * src[j];
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI *__restrict__ x, TO *__restrict__ y, long long n) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (long long)gridDim.x * blockDim.x)
+    y[j] = (TO)x[j];
 }
 
 // Block minimum of (value, index) over entries not in excl[0..nex); lexicographic.
@@ -252,8 +286,8 @@ static int part_buffer(forte_ctx *ctx, size_t doubles, double **p) {
   return FORTE_OK;
 }
 
-int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n,
-                double *out) {
+template <typename T>
+static int vk_multidot_t(forte_ctx *ctx, const T *V, int nv, long long ld, const T *x, long long n, double *out) {
   if (nv <= 0) return FORTE_OK;
   if (nv > VK_MAXV) { set_error("multidot: too many vectors (%d)", nv); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
@@ -262,7 +296,7 @@ int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const dou
   if (rc) return rc;
   {
     FORTE_PROF(ctx, "multidot");
-    k_multidot<<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
+    k_multidot<T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
   FORTE_LAUNCH_CHECK();
   }
   {
@@ -273,21 +307,32 @@ int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const dou
   return FORTE_OK;
 }
 
-int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb,
-               double *out, long long ldo, long long n) {
-  if (nv > VK_MAXV || ncomb > 32) { set_error("combine: too many vectors"); return FORTE_ERR_ARG; }
+template <typename T>
+static int vk_combine_t(forte_ctx *ctx, const T *V, int nv, long long ld, const double *coef, int ncomb, T *out,
+                        long long ldo, long long n) {
+  if (nv > VK_MAXV || ncomb > 64) { set_error("combine: too many vectors"); return FORTE_ERR_ARG; }
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
-  {
+  // outputs in groups of 8, 4, 2, 1 (each group streams V once)
+  for (int c0 = 0; c0 < ncomb;) {
+    const int left = ncomb - c0, g = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
     FORTE_PROF(ctx, "combine");
-    k_combine<<<nb, 256, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, out, ldo, n);
-  FORTE_LAUNCH_CHECK();
+    if (g == 8)
+      k_combine<8, T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, c0, out, ldo, n);
+    else if (g == 4)
+      k_combine<4, T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, c0, out, ldo, n);
+    else if (g == 2)
+      k_combine<2, T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, c0, out, ldo, n);
+    else
+      k_combine<1, T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, coef, ncomb, c0, out, ldo, n);
+    FORTE_LAUNCH_CHECK();
+    c0 += g;
   }
   return FORTE_OK;
 }
 
-int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld,
-                        const double *u, double theta, double guard, double *t, double *rnorm2,
-                        long long n) {
+template <typename T>
+static int vk_residual_precond_t(forte_ctx *ctx, const T *B, const T *S, int k, long long ld, const double *u,
+                                 double theta, double guard, T *t, double *rnorm2, long long n) {
   if (k > VK_MAXV) { set_error("residual: subspace too large (%d)", k); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
@@ -295,7 +340,7 @@ int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k,
   if (rc) return rc;
   {
     FORTE_PROF(ctx, "residual_precond");
-    k_residual_precond<<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
+    k_residual_precond<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
                                                           n, part);
   FORTE_LAUNCH_CHECK();
   }
@@ -307,8 +352,9 @@ int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k,
   return FORTE_OK;
 }
 
-int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c,
-                   const double *t_in, double *t_out, double *dots_out, long long n) {
+template <typename T>
+static int vk_orth_update_t(forte_ctx *ctx, const T *B, int k, long long ld, const double *c, const T *t_in,
+                            T *t_out, double *dots_out, long long n) {
   if (k + 1 > VK_MAXV) { set_error("orth: subspace too large (%d)", k); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
@@ -316,7 +362,7 @@ int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const d
   if (rc) return rc;
   {
     FORTE_PROF(ctx, "orth_update");
-    k_orth_update<<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+    k_orth_update<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
   FORTE_LAUNCH_CHECK();
   }
   {
@@ -327,15 +373,63 @@ int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const d
   return FORTE_OK;
 }
 
-int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n) {
+template <typename T>
+static int vk_scale_t(forte_ctx *ctx, T *x, const T *src, double alpha, long long n) {
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
   {
     FORTE_PROF(ctx, "scale");
-    k_scale<<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
+    k_scale<T><<<nb, 256, 0, ctx->stream>>>(x, src, alpha, n);
   FORTE_LAUNCH_CHECK();
   }
   return FORTE_OK;
 }
+
+int vk_multidot(forte_ctx *ctx, const double *V, int nv, long long ld, const double *x, long long n, double *out) {
+  return vk_multidot_t(ctx, V, nv, ld, x, n, out);
+}
+int vk_multidot(forte_ctx *ctx, const float *V, int nv, long long ld, const float *x, long long n, double *out) {
+  return vk_multidot_t(ctx, V, nv, ld, x, n, out);
+}
+int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const double *coef, int ncomb, double *out,
+               long long ldo, long long n) {
+  return vk_combine_t(ctx, V, nv, ld, coef, ncomb, out, ldo, n);
+}
+int vk_combine(forte_ctx *ctx, const float *V, int nv, long long ld, const double *coef, int ncomb, float *out,
+               long long ldo, long long n) {
+  return vk_combine_t(ctx, V, nv, ld, coef, ncomb, out, ldo, n);
+}
+int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld, const double *u,
+                        double theta, double guard, double *t, double *rnorm2, long long n) {
+  return vk_residual_precond_t(ctx, B, S, k, ld, u, theta, guard, t, rnorm2, n);
+}
+int vk_residual_precond(forte_ctx *ctx, const float *B, const float *S, int k, long long ld, const double *u,
+                        double theta, double guard, float *t, double *rnorm2, long long n) {
+  return vk_residual_precond_t(ctx, B, S, k, ld, u, theta, guard, t, rnorm2, n);
+}
+int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c, const double *t_in,
+                   double *t_out, double *dots_out, long long n) {
+  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n);
+}
+int vk_orth_update(forte_ctx *ctx, const float *B, int k, long long ld, const double *c, const float *t_in,
+                   float *t_out, double *dots_out, long long n) {
+  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n);
+}
+int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n) {
+  return vk_scale_t(ctx, x, src, alpha, n);
+}
+int vk_scale(forte_ctx *ctx, float *x, const float *src, double alpha, long long n) {
+  return vk_scale_t(ctx, x, src, alpha, n);
+}
+template <typename TI, typename TO>
+static int vk_convert_t(forte_ctx *ctx, const TI *x, TO *y, long long n) {
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
+  FORTE_PROF(ctx, "convert");
+  k_convert<TI, TO><<<nb, 256, 0, ctx->stream>>>(x, y, n);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+int vk_convert(forte_ctx *ctx, const double *x, float *y, long long n) { return vk_convert_t(ctx, x, y, n); }
+int vk_convert(forte_ctx *ctx, const float *x, double *y, long long n) { return vk_convert_t(ctx, x, y, n); }
 
 int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n) {
   unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 16);
