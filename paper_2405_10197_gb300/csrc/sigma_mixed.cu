@@ -109,14 +109,14 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 // ------------------------------------------------------------ the alpha-beta MMA kernel
 //
 // Scatter accumulation.  Every contribution f is turned into the fixed-point
-// value V = f 2^S with |V| < 2^41 (S per vector from the bound
-// |f| <= n_kl * max|g| * max|C|, with 2% slack for the operand splits), split
-// as V = hi 2^20 + lo with hi = rint(V 2^-20) and lo = rint(V - hi 2^20) in
-// [-2^19, 2^19], and added with two 32-bit integer reductions into shared
-// memory.  At most n_kl <= 64 contributions reach one output, so neither word
-// can overflow.  Integer
-// shared-memory reductions are native on the SM, FP32 ones are not; the sum is
-// exact and independent of the order of the atomics.
+// value V = rint(f 2^S) with |V| <= 2^22 (S per vector from the bound
+// |f| <= n_kl * max|g| * max|C|, with 2% slack for the operand splits) and added
+// with one 32-bit integer reduction into shared memory.  At most n_kl <= 64
+// contributions reach one output, so the word cannot overflow, and the rounding
+// adds at most 64 * 2^-23 = 7.6e-6 of the bound to an output: below the 2^-16
+// relative error the BF16 hi/lo operands already carry.  Integer shared-memory
+// reductions are native on the SM, FP32 ones are not; the sum is exact and
+// independent of the order of the atomics.
 
 constexpr int WS_STAGES = 3;                              // B operand ring
 constexpr int WS_ACC = 4;                                 // TMEM accumulators of 128 columns
@@ -136,9 +136,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   uint8_t *sA = sm;
   uint8_t *sB = sm + MX_OFF_B;
   const long long NB4 = (NB + 3) & ~3LL;
-  int *acc_hi = (int *)(sm + WS_OFF_ACC);
-  int *acc_lo = acc_hi + NB4;
-  int *sJ = (int *)(acc_lo + NB4);
+  int *acc = (int *)(sm + WS_OFF_ACC);
+  int *sJ = (int *)(acc + NB4);
   uint8_t *sPair = (uint8_t *)(sJ + 64);
   int8_t *sSgn = (int8_t *)(sPair + 64);
   uint64_t *bar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
   int eb = 0;
   if (bound > 0.f) frexpf(bound, &eb);
-  const int Sx = (bound > 0.f) ? min(100, 41 - eb) : 0;
+  const int Sx = (bound > 0.f) ? min(100, 22 - eb) : 0;
   const float fscale = ldexpf(1.f, Sx);
 
   if (warp == 4) tmem_alloc(sTmem, WS_ACC * MX_TILE_N);
@@ -184,8 +183,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     }
   }
   for (long long i = tid; i < NB; i += MX_THREADS) {
-    acc_hi[i] = 0;
-    acc_lo[i] = 0;
+    acc[i] = 0;
   }
   __syncthreads();
 
@@ -377,19 +375,15 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           const int w2 = (col & 7) >> 1;
           const uint32_t w = w2 == 0 ? q.x : w2 == 1 ? q.y : w2 == 2 ? q.z : q.w;
           const uint32_t en = (col & 1) ? (w >> 16) : (w & 0xFFFFu);
-          // fs = f 2^S = hi 2^20 + lo with hi, lo rounded to integers by adding
-          // 1.5 2^23 (exact for |x| < 2^22): no conversion instructions, which
-          // would run on the narrow FP64/conversion pipe.  The reductions are
-          // skipped (not predicated) for invalid entries: issued reduction
-          // instructions, even predicated off, are what limits this loop.
+          // V = rint(f 2^S) by adding 1.5 2^23 (exact for |x| <= 2^22): no
+          // conversion instruction, which would run on the narrow FP64 /
+          // conversion pipe.  The reduction is skipped (not predicated) for
+          // invalid entries: issued reductions, even predicated off, are what
+          // limits this loop.
           if (en != 0xFFFFu) {
             const float fsv = __uint_as_float(r[i]) * fscale;
-            const float fs = (en & 0x4000u) ? -fsv : fsv;
-            const float th = fmaf(fs, 0x1p-20f, 12582912.0f);
-            const float hf = th - 12582912.0f;
-            const float tl = fmaf(-hf, 0x1p20f, fs) + 12582912.0f;
-            atomicAdd(&acc_hi[en & 0x3FFFu], __float_as_int(th) - 0x4B400000);
-            atomicAdd(&acc_lo[en & 0x3FFFu], __float_as_int(tl) - 0x4B400000);
+            const float t = ((en & 0x4000u) ? -fsv : fsv) + 12582912.0f;
+            atomicAdd(&acc[en & 0x3FFFu], __float_as_int(t) - 0x4B400000);
           }
         }
       }
@@ -409,8 +403,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     const float *ss = Sss + v * v64 + Ia * NB;
     TO *out = S + v * v64 + Ia * NB;
     for (long long i = tid; i < NB; i += MX_THREADS) {
-      const long long tot = (long long)acc_hi[i] * 1048576LL + (long long)acc_lo[i];
-      out[i] = (TO)((double)ss[i] + ldexp((double)tot, -Sx));
+      out[i] = (TO)((double)ss[i] + ldexp((double)acc[i], -Sx));
     }
   }
   tc_fence_before();
@@ -422,7 +415,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // ------------------------------------------------------------ host side
 
 static size_t mx_smem_bytes(long long NB) {
-  return 1024 + WS_OFF_ACC + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 +
+  return 1024 + WS_OFF_ACC + sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 +
          8 * (2 * WS_STAGES + 2 * WS_ACC) + 16 + 64;
 }
 
