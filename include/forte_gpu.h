@@ -46,13 +46,23 @@ enum {
   FORTE_ERR_TIMEOUT = 6        /* a bounded device wait gave up */
 };
 
-/* Arithmetic of the sigma build (forte_set_precision). */
+/* Arithmetic of the sigma build (forte_set_precision).  The paper's CASCI
+ * (Sec. II.A.1) is FP64 throughout; the reduced-precision modes are an
+ * extension: reduced-precision sigma vectors for the bulk of the Davidson
+ * iterations, then a refinement with an FP64-class sigma to the requested tolerance. */
 enum {
   FORTE_FP64 = 0,   /* every term in FP64 */
-  FORTE_TF32 = 1,   /* alpha-beta GEMM in TF32 on the tensor cores, FP32 accumulate;
-                       same-spin terms in FP32; Davidson vectors FP64 */
-  FORTE_BF16X2 = 2  /* alpha-beta GEMM with split hi+lo BF16 operands
-                       (hi*hi + hi*lo + lo*hi), FP32 accumulate; same-spin FP32 */
+  FORTE_TF32 = 1,   /* tensor-core GEMMs (same-spin and alpha-beta) on TF32-rounded
+                       operands, FP32 accumulate; Davidson phase on FP32 vectors,
+                       then refinement with the FORTE_DF32 sigma */
+  FORTE_BF16X2 = 2, /* as FORTE_TF32 with split hi+lo BF16 operands
+                       (hi*hi + hi*lo + lo*hi) */
+  FORTE_DF32 = 3    /* FP64-class sigma in double-FP32 arithmetic: every FP64
+                       operand as an unevaluated sum of two FP32 values, exact
+                       FP32 products via FMA, compensated sums; relative error
+                       ~2^-46 per term.  Davidson as for FORTE_FP64 (FP64 vectors).
+                       Not part of the paper's schemes: an FP64 substitute for
+                       GPUs whose FP64 pipe is narrow. */
 };
 
 /* Build a CAS problem: string lists (a1), signed single-replacement tables
@@ -79,8 +89,9 @@ const char *forte_last_error(void);
  * default stream). */
 int forte_set_stream(forte_ctx *ctx, void *cuda_stream);
 
-/* Select FORTE_FP64, FORTE_TF32 or FORTE_BF16X2 for forte_sigma and for the
- * inner iterations of forte_davidson.  Default FORTE_FP64. */
+/* Select FORTE_FP64, FORTE_TF32, FORTE_BF16X2 or FORTE_DF32 for forte_sigma,
+ * forte_davidson and forte_rdms (every mode but FORTE_FP64 forms the 2-RDM with
+ * the tensor-core Gram).  Default FORTE_FP64.  FORTE_ERR_ARG for other values. */
 int forte_set_precision(forte_ctx *ctx, int mode);
 
 /* N_alpha = C(n, nalpha), N_beta = C(n, nbeta) (host outputs, either may be NULL). */

@@ -102,13 +102,17 @@ static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, 
     ctx->n_sigma_fp64 += nvec;
     return sigma_fp64(ctx, C, S, nvec);
   }
+  if (mode == FORTE_DF32) {  // FP64-class: counted with the FP64 ones
+    ctx->n_sigma_fp64 += nvec;
+    return sigma_df(ctx, C, S, nvec);
+  }
   ctx->n_sigma_mixed += nvec;
   return sigma_mixed(ctx, C, S, nvec, mode);
 }
 
 static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
-  if (mode == FORTE_FP64) {
+  if (mode == FORTE_FP64 || mode == FORTE_DF32) {
     set_error("FP32 vectors need a reduced-precision sigma");
     return FORTE_ERR_ARG;
   }
@@ -471,7 +475,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
       if ((rc = vk_scale(ctx, v, v, 1.0 / sqrt(hn[0]), N))) return rc;
     }
   }
-  if ((rc = sigma_dispatch(ctx, V, HV, nroots, FORTE_FP64))) return rc;
+  if ((rc = sigma_dispatch(ctx, V, HV, nroots, FORTE_DF32))) return rc;
   double prev_rn = INFINITY;
   int k = nroots;
   std::vector<double> G, Gk, w, U, coef, h(66);
@@ -518,7 +522,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
     // an outer step that does not halve the residual means the reduced-precision
     // inner operator no longer resolves the correction: continue with FP64 ones
     const double max_rn = *std::max_element(res.rn.begin(), res.rn.end());
-    if (outer > 0 && max_rn > 0.5 * prev_rn) inner_mode = FORTE_FP64;
+    if (outer > 0 && max_rn > 0.5 * prev_rn) inner_mode = FORTE_DF32;
     prev_rn = max_rn;
     if (all || outer >= max_outer) {
       FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
@@ -579,7 +583,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
       FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
       return FORTE_OK;
     }
-    if ((rc = sigma_dispatch(ctx, V + (size_t)k0 * N, HV + (size_t)k0 * N, k - k0, FORTE_FP64))) return rc;
+    if ((rc = sigma_dispatch(ctx, V + (size_t)k0 * N, HV + (size_t)k0 * N, k - k0, FORTE_DF32))) return rc;
   }
 }
 
@@ -664,12 +668,14 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_gpair); cudaFree(ctx->d_gpair32); cudaFree(ctx->d_hdiag);
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
   cudaFree(ctx->d_gT_hi); cudaFree(ctx->d_gT_lo); cudaFree(ctx->d_gT_t32); cudaFree(ctx->d_err);
-  cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp);
+  cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp); cudaFree(ctx->d_gpair2);
+  cudaFree(ctx->d_csr_val2[0]);
+  if (!ctx->same_strings) cudaFree(ctx->d_csr_val2[1]);
   for (int s = 0; s < (ctx->same_strings ? 1 : 2); ++s) {
     cudaFree(ctx->d_hd_hi[s]); cudaFree(ctx->d_hd_lo[s]); cudaFree(ctx->d_hd_t32[s]);
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
-  ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release();
+  ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
@@ -683,7 +689,7 @@ int forte_set_stream(forte_ctx *ctx, void *s) {
 
 int forte_set_precision(forte_ctx *ctx, int mode) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
-  if (mode != FORTE_FP64 && mode != FORTE_TF32 && mode != FORTE_BF16X2) {
+  if (mode != FORTE_FP64 && mode != FORTE_TF32 && mode != FORTE_BF16X2 && mode != FORTE_DF32) {
     set_error("unknown precision mode %d", mode);
     return FORTE_ERR_ARG;
   }
@@ -782,8 +788,8 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
   if (rc) return rc;
   DvResult res;
   ctx->nroots_done = 0;
-  if (ctx->precision == FORTE_FP64) {
-    rc = davidson_run<double>(ctx, nroots, tol, FORTE_FP64, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
+  if (ctx->precision == FORTE_FP64 || ctx->precision == FORTE_DF32) {
+    rc = davidson_run<double>(ctx, nroots, tol, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                               ctx->d_roots, res);
     if (rc) return rc;
     ctx->dv_iters = res.iters;

@@ -117,6 +117,8 @@ struct forte_ctx {
   // [N][N padded to 16] per spin (aliases when alpha and beta strings coincide)
   uint16_t *d_hd_hi[2] = {nullptr, nullptr}, *d_hd_lo[2] = {nullptr, nullptr};
   float *d_hd_t32[2] = {nullptr, nullptr};
+  void *d_gpair2 = nullptr;                      // (hi, lo) FP32 pairs of d_gpair
+  void *d_csr_val2[2] = {nullptr, nullptr};      // (hi, lo) pairs of the CSR values
   uint16_t *d_ozT = nullptr;    // [n*n][Nb padded to 64]: E_sr |Ib> of the beta strings (RDM Gram)
   double *d_g1tmp = nullptr;    // 1-RDM workspace of the tensor-core 2-RDM when the caller passes none
   float gmax = 0.f;             // max |(pq|rs)| (bounds the alpha-beta fixed-point scale)
@@ -138,6 +140,7 @@ struct forte_ctx {
   forte::Scratch sc_rdm;           // RDM intermediates
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
+  forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -172,6 +175,8 @@ int upload_tables(forte_ctx *ctx);
 // sigma_fp64.cu
 int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
 int hdiag_build(forte_ctx *ctx);
+// FP64-class sigma in double-FP32 arithmetic (relative error ~2^-46 per term)
+int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec);
 
 int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec);
 

@@ -362,4 +362,282 @@ int hdiag_build(forte_ctx *ctx) {
   return FORTE_OK;
 }
 
+// ============================================================================
+// FP64-class sigma in double-FP32 arithmetic (precision FORTE_DF32, and the
+// refinement operator of the reduced-precision modes).
+//
+// Every FP64 operand x is held as an unevaluated pair x = hi + lo of FP32 values
+// (hi = fl32(x), lo = fl32(x - hi); |x - hi - lo| <= 2^-48 |x|).  A product term
+// a b adds hi_a hi_b exactly (the FMA residual of the FP32 product), the cross
+// terms hi_a lo_b + lo_a hi_b in FP32, and drops lo_a lo_b (2^-48 relative); the
+// running sum is a compensated pair (TwoSum of Knuth, TAOCP vol. 2, Sec. 4.2.2).
+// Relative error per product about 2^-46.  The FP32 pipe of this GPU issues 64
+// times the FP64 pipe's operations, so ~12 FP32 operations per term beat one DFMA.
+// ============================================================================
+
+__device__ __forceinline__ void df_fma(float &ah, float &al, float2 a, float2 b) {
+  const float p = a.x * b.x;
+  const float pe = fmaf(a.x, b.x, -p);
+  const float c = fmaf(a.x, b.y, a.y * b.x);
+  const float s = ah + p;
+  const float bb = s - ah;
+  const float e = (ah - (s - bb)) + (p - bb);
+  ah = s;
+  al += e + (pe + c);
+}
+
+// Y[c][r] = X[r][c] for an R x Cc matrix of (hi, lo) pairs per vector.
+__global__ void k_transpose_df(const float2 *__restrict__ X, float2 *__restrict__ Y, long long R, long long Cc,
+                               long long vstride) {
+  __shared__ float2 tile[32][33];
+  const float2 *Xv = X + (long long)blockIdx.z * vstride;
+  float2 *Yv = Y + (long long)blockIdx.z * vstride;
+  const long long r0 = (long long)blockIdx.y * 32, c0 = (long long)blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long long r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < Cc) tile[i][threadIdx.x] = Xv[r * Cc + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const long long c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < Cc) Yv[c * R + r] = tile[threadIdx.x][i];
+  }
+}
+
+// (ah, al) += (bh, bl): compensated sum of two pairs.
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
+  const float s = ah + bh;
+  const float bb = s - ah;
+  const float e = (ah - (s - bb)) + (bh - bb);
+  ah = s;
+  al += e + bl;
+}
+
+// x -> (hi, lo)
+__global__ void k_df_split(const double *__restrict__ x, float2 *__restrict__ y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    y[i] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+// Same-spin CSR product in double-FP32: Y[row, c] (+)= sum_nz val * X[col, c],
+// X and val as (hi, lo) pairs, Y FP64.  grid.x = nrow * nchunk, grid.y = vector.
+__global__ void __launch_bounds__(SS_THREADS) k_ss_spmm_df(const int *__restrict__ ptr, const int *__restrict__ col,
+                                                           const float2 *__restrict__ val, const float2 *__restrict__ X,
+                                                           double *__restrict__ Y, long long nrow, long long ncol,
+                                                           int nchunk, long long vstride, int accumulate) {
+  __shared__ int s_col[SS_SEG];
+  __shared__ float2 s_val[SS_SEG];
+  const long long row = blockIdx.x / nchunk;
+  const int chunk = blockIdx.x % nchunk;
+  const float2 *Xv = X + (long long)blockIdx.y * vstride;
+  double *Yv = Y + (long long)blockIdx.y * vstride;
+  const long long c0 = (long long)chunk * SS_THREADS * SS_CPT + threadIdx.x;
+  float ah[SS_CPT], al[SS_CPT], bh[SS_CPT], bl[SS_CPT];  // two chains per column
+#pragma unroll
+  for (int k = 0; k < SS_CPT; ++k) ah[k] = al[k] = bh[k] = bl[k] = 0.f;
+  const int b = ptr[row], e = ptr[row + 1];
+  for (int s0 = b; s0 < e; s0 += SS_SEG) {
+    const int cnt = min(SS_SEG, e - s0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += SS_THREADS) {
+      s_col[i] = col[s0 + i];
+      s_val[i] = val[s0 + i];
+    }
+    __syncthreads();
+    int i = 0;
+#pragma unroll 2
+    for (; i + 1 < cnt; i += 2) {
+      const float2 v0 = s_val[i], v1 = s_val[i + 1];
+      const float2 *x0 = Xv + (long long)s_col[i] * ncol, *x1 = Xv + (long long)s_col[i + 1] * ncol;
+#pragma unroll
+      for (int k = 0; k < SS_CPT; ++k) {
+        const long long c = c0 + (long long)k * SS_THREADS;
+        if (c < ncol) {
+          df_fma(ah[k], al[k], v0, x0[c]);
+          df_fma(bh[k], bl[k], v1, x1[c]);
+        }
+      }
+    }
+    if (i < cnt) {
+      const float2 v = s_val[i];
+      const float2 *xr = Xv + (long long)s_col[i] * ncol;
+#pragma unroll
+      for (int k = 0; k < SS_CPT; ++k) {
+        const long long c = c0 + (long long)k * SS_THREADS;
+        if (c < ncol) df_fma(ah[k], al[k], v, xr[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < SS_CPT; ++k) {
+    const long long c = c0 + (long long)k * SS_THREADS;
+    if (c < ncol) {
+      double *y = Yv + row * ncol + c;
+      df_add(ah[k], al[k], bh[k], bl[k]);
+      const double r = (double)ah[k] + (double)al[k];
+      *y = accumulate ? *y + r : r;
+    }
+  }
+}
+
+// sigma_ab in double-FP32 for one alpha string Ia (blockIdx.x) and one vector
+// (blockIdx.y): k_ab_fp64 with (hi, lo) operands; the output row stays FP64.
+__global__ void __launch_bounds__(AB_THREADS) k_ab_df(const Repl *__restrict__ listA, int nkA,
+                                                      const Repl *__restrict__ listB, int nkB, long long NB,
+                                                      const float2 *__restrict__ gpair2, int npair,
+                                                      const float2 *__restrict__ C2, double *__restrict__ S,
+                                                      long long vstride, int TJ) {
+  extern __shared__ double smem[];
+  float2 *Gs = reinterpret_cast<float2 *>(smem);                 // nkA * npair
+  double *srow = smem + (size_t)nkA * npair;                     // NB
+  float2 *D = reinterpret_cast<float2 *>(srow + NB);              // nkA * TJ
+  Repl *Lb = reinterpret_cast<Repl *>(D + (size_t)nkA * TJ);      // TJ * nkB
+  const long long Ia = blockIdx.x;
+  const float2 *Cv = C2 + (long long)blockIdx.y * vstride;
+  double *Sv = S + (long long)blockIdx.y * vstride;
+  const Repl *la = listA + Ia * nkA;
+  __shared__ int s_J[80];
+  for (int e = threadIdx.x; e < nkA; e += AB_THREADS) s_J[e] = la[e].J;
+  for (int i = threadIdx.x; i < nkA * npair; i += AB_THREADS) {
+    const int e = i / npair, rs = i % npair;
+    const Repl r = la[e];
+    float2 g = gpair2[(size_t)r.pair * npair + rs];
+    if (r.sgn < 0) g = make_float2(-g.x, -g.y);
+    Gs[i] = g;
+  }
+  for (long long i = threadIdx.x; i < NB; i += AB_THREADS) srow[i] = 0.0;
+  __syncthreads();
+  for (long long j0 = 0; j0 < NB; j0 += TJ) {
+    const int tj = (int)min((long long)TJ, NB - j0);
+    for (int i = threadIdx.x; i < nkA * tj; i += AB_THREADS) {
+      const int e = i / tj, j = i % tj;
+      D[e * TJ + j] = Cv[(long long)s_J[e] * NB + j0 + j];
+    }
+    for (int i = threadIdx.x; i < tj * nkB; i += AB_THREADS) Lb[i] = listB[j0 * nkB + i];
+    __syncthreads();
+    const int npairs_tile = tj * nkB;
+    for (int w = threadIdx.x; w < npairs_tile; w += AB_THREADS) {
+      const int j = w / nkB;
+      const Repl rf = Lb[w];
+      const float2 *g = Gs + rf.pair;
+      const float2 *d = D + j;
+      // four independent compensated sums (the dependent FP32 adds of one
+      // chain would leave the pipe idle), merged at the end
+      float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f, ah2 = 0.f, al2 = 0.f, ah3 = 0.f, al3 = 0.f;
+      int e = 0;
+#pragma unroll 2
+      for (; e + 3 < nkA; e += 4) {
+        df_fma(ah0, al0, g[e * npair], d[e * TJ]);
+        df_fma(ah1, al1, g[(e + 1) * npair], d[(e + 1) * TJ]);
+        df_fma(ah2, al2, g[(e + 2) * npair], d[(e + 2) * TJ]);
+        df_fma(ah3, al3, g[(e + 3) * npair], d[(e + 3) * TJ]);
+      }
+      for (; e < nkA; ++e) df_fma(ah0, al0, g[e * npair], d[e * TJ]);
+      df_add(ah0, al0, ah1, al1);
+      df_add(ah2, al2, ah3, al3);
+      df_add(ah0, al0, ah2, al2);
+      atomicAdd(&srow[rf.J], rf.sgn * ((double)ah0 + (double)al0));
+    }
+    __syncthreads();
+  }
+  for (long long i = threadIdx.x; i < NB; i += AB_THREADS) Sv[Ia * NB + i] += srow[i];
+}
+
+static int df_setup(forte_ctx *ctx) {
+  if (ctx->d_gpair2) return FORTE_OK;
+  const int np = ctx->npair;
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gpair2, sizeof(float2) * (size_t)np * np));
+  k_df_split<<<(unsigned)std::min<long long>(((long long)np * np + 255) / 256, 1024), 256, 0, ctx->stream>>>(
+      ctx->d_gpair, (float2 *)ctx->d_gpair2, (long long)np * np);
+  FORTE_LAUNCH_CHECK();
+  const int nsp = ctx->same_strings ? 1 : 2;
+  for (int s = 0; s < nsp; ++s) {
+    const long long nnz = (long long)ctx->sh[s].csr_col.size();
+    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_csr_val2[s], sizeof(float2) * (size_t)std::max(1LL, nnz)));
+    if (nnz > 0) {
+      k_df_split<<<(unsigned)std::min<long long>((nnz + 255) / 256, 152LL * 16), 256, 0, ctx->stream>>>(
+          ctx->sd[s].csr_val, (float2 *)ctx->d_csr_val2[s], nnz);
+      FORTE_LAUNCH_CHECK();
+    }
+  }
+  if (ctx->same_strings) ctx->d_csr_val2[1] = ctx->d_csr_val2[0];
+  return FORTE_OK;
+}
+
+int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec) {
+  int rc = df_setup(ctx);
+  if (rc) return rc;
+  cudaStream_t st = ctx->stream;
+  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
+  const size_t nf = (size_t)nvec * ND;
+  if ((rc = ctx->sc_df.ensure(sizeof(float2) * nf + 256))) return rc;
+  if ((rc = ctx->sc_t1.ensure(sizeof(float2) * nf + 256))) return rc;
+  if ((rc = ctx->sc_t2.ensure(sizeof(double) * nf + 256))) return rc;
+  float2 *C2 = (float2 *)ctx->sc_df.ptr, *T1 = (float2 *)ctx->sc_t1.ptr;
+  double *T2 = (double *)ctx->sc_t2.ptr;
+  const float2 *v2a = (const float2 *)ctx->d_csr_val2[0], *v2b = (const float2 *)ctx->d_csr_val2[1];
+  {
+    FORTE_PROF(ctx, "df_split");
+    k_df_split<<<(unsigned)std::min<size_t>((nf + 255) / 256, 152 * 16), 256, 0, st>>>(C, C2, (long long)nf);
+    FORTE_LAUNCH_CHECK();
+  }
+  {
+    const int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NA * nchunk), nvec);
+    FORTE_PROF(ctx, "ss_spmm_df");
+    k_ss_spmm_df<<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col, v2a, C2, S, NA, NB, nchunk, ND, 0);
+    FORTE_LAUNCH_CHECK();
+  }
+  {
+    dim3 tb(32, 8);
+    dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
+    {
+      FORTE_PROF(ctx, "transpose");
+      k_transpose_df<<<g1, tb, 0, st>>>(C2, T1, NA, NB, ND);
+      FORTE_LAUNCH_CHECK();
+    }
+    const int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
+    dim3 grid((unsigned)(NB * nchunk), nvec);
+    {
+      FORTE_PROF(ctx, "ss_spmm_df");
+      k_ss_spmm_df<<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col, v2b, T1, T2, NB, NA, nchunk, ND,
+                                                0);
+      FORTE_LAUNCH_CHECK();
+    }
+    dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
+    {
+      FORTE_PROF(ctx, "transpose");
+      k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
+      FORTE_LAUNCH_CHECK();
+    }
+  }
+  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
+  if (nkA > 0 && nkB > 0) {
+    if (nkA > 80) {
+      set_error("alpha replacement list too long (%d)", nkA);
+      return FORTE_ERR_ARG;
+    }
+    int TJ = 64;
+    size_t smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
+    while (smem > 220 * 1024 && TJ > 8) {
+      TJ /= 2;
+      smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
+    }
+    if (smem > 220 * 1024) {
+      set_error("alpha-beta double-FP32 kernel needs %zu bytes of shared memory", smem);
+      return FORTE_ERR_ARG;
+    }
+    FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_df));
+    dim3 grid((unsigned)NA, nvec);
+    FORTE_PROF(ctx, "ab_df");
+    k_ab_df<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
+                                            (const float2 *)ctx->d_gpair2, ctx->npair, C2, S, ND, TJ);
+    FORTE_LAUNCH_CHECK();
+  }
+  return FORTE_OK;
+}
+
 }  // namespace forte
