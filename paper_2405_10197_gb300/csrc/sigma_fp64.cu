@@ -404,15 +404,6 @@ __global__ void k_transpose_df(const float2 *__restrict__ X, float2 *__restrict_
   }
 }
 
-// (ah, al) += (bh, bl): compensated sum of two pairs.
-__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl) {
-  const float s = ah + bh;
-  const float bb = s - ah;
-  const float e = (ah - (s - bb)) + (bh - bb);
-  ah = s;
-  al += e + bl;
-}
-
 // x -> (hi, lo)
 __global__ void k_df_split(const double *__restrict__ x, float2 *__restrict__ y, long long n) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -435,9 +426,9 @@ __global__ void __launch_bounds__(SS_THREADS) k_ss_spmm_df(const int *__restrict
   const float2 *Xv = X + (long long)blockIdx.y * vstride;
   double *Yv = Y + (long long)blockIdx.y * vstride;
   const long long c0 = (long long)chunk * SS_THREADS * SS_CPT + threadIdx.x;
-  float ah[SS_CPT], al[SS_CPT], bh[SS_CPT], bl[SS_CPT];  // two chains per column
+  float ah[SS_CPT], al[SS_CPT];
 #pragma unroll
-  for (int k = 0; k < SS_CPT; ++k) ah[k] = al[k] = bh[k] = bl[k] = 0.f;
+  for (int k = 0; k < SS_CPT; ++k) ah[k] = al[k] = 0.f;
   const int b = ptr[row], e = ptr[row + 1];
   for (int s0 = b; s0 < e; s0 += SS_SEG) {
     const int cnt = min(SS_SEG, e - s0);
@@ -447,21 +438,8 @@ __global__ void __launch_bounds__(SS_THREADS) k_ss_spmm_df(const int *__restrict
       s_val[i] = val[s0 + i];
     }
     __syncthreads();
-    int i = 0;
-#pragma unroll 2
-    for (; i + 1 < cnt; i += 2) {
-      const float2 v0 = s_val[i], v1 = s_val[i + 1];
-      const float2 *x0 = Xv + (long long)s_col[i] * ncol, *x1 = Xv + (long long)s_col[i + 1] * ncol;
-#pragma unroll
-      for (int k = 0; k < SS_CPT; ++k) {
-        const long long c = c0 + (long long)k * SS_THREADS;
-        if (c < ncol) {
-          df_fma(ah[k], al[k], v0, x0[c]);
-          df_fma(bh[k], bl[k], v1, x1[c]);
-        }
-      }
-    }
-    if (i < cnt) {
+#pragma unroll 4
+    for (int i = 0; i < cnt; ++i) {
       const float2 v = s_val[i];
       const float2 *xr = Xv + (long long)s_col[i] * ncol;
 #pragma unroll
@@ -476,7 +454,6 @@ __global__ void __launch_bounds__(SS_THREADS) k_ss_spmm_df(const int *__restrict
     const long long c = c0 + (long long)k * SS_THREADS;
     if (c < ncol) {
       double *y = Yv + row * ncol + c;
-      df_add(ah[k], al[k], bh[k], bl[k]);
       const double r = (double)ah[k] + (double)al[k];
       *y = accumulate ? *y + r : r;
     }
@@ -524,22 +501,10 @@ __global__ void __launch_bounds__(AB_THREADS) k_ab_df(const Repl *__restrict__ l
       const Repl rf = Lb[w];
       const float2 *g = Gs + rf.pair;
       const float2 *d = D + j;
-      // four independent compensated sums (the dependent FP32 adds of one
-      // chain would leave the pipe idle), merged at the end
-      float ah0 = 0.f, al0 = 0.f, ah1 = 0.f, al1 = 0.f, ah2 = 0.f, al2 = 0.f, ah3 = 0.f, al3 = 0.f;
-      int e = 0;
-#pragma unroll 2
-      for (; e + 3 < nkA; e += 4) {
-        df_fma(ah0, al0, g[e * npair], d[e * TJ]);
-        df_fma(ah1, al1, g[(e + 1) * npair], d[(e + 1) * TJ]);
-        df_fma(ah2, al2, g[(e + 2) * npair], d[(e + 2) * TJ]);
-        df_fma(ah3, al3, g[(e + 3) * npair], d[(e + 3) * TJ]);
-      }
-      for (; e < nkA; ++e) df_fma(ah0, al0, g[e * npair], d[e * TJ]);
-      df_add(ah0, al0, ah1, al1);
-      df_add(ah2, al2, ah3, al3);
-      df_add(ah0, al0, ah2, al2);
-      atomicAdd(&srow[rf.J], rf.sgn * ((double)ah0 + (double)al0));
+      float ah = 0.f, al = 0.f;
+#pragma unroll 8
+      for (int e = 0; e < nkA; ++e) df_fma(ah, al, g[e * npair], d[e * TJ]);
+      atomicAdd(&srow[rf.J], rf.sgn * ((double)ah + (double)al));
     }
     __syncthreads();
   }
