@@ -343,9 +343,11 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     __syncwarp();
   } else if (warp >= 8) {
     // ================= epilogue: thread = beta string j0 + j (accumulator lane),
-    //                   64 pairs rs per warp half (accumulator columns)
+    //                   nN/2 pairs rs per warp half (accumulator columns), read
+    //                   in blocks of 8 columns
     const int e = warp - 8, lg = e & 3, half = e >> 2;
     const int j = lg * 32 + lane;
+    const int hc = nN >> 1, nq = hc >> 3;
     for (int t = 0; t < ntiles; ++t) {
       const int b = t % WS_ACC, ub = t / WS_ACC;
       const long long Jb = (long long)t * MX_TILE_N + j;
@@ -353,9 +355,10 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 #pragma unroll
       for (int q = 0; q < 8; ++q) tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
       if (Jb < NB) {
-        const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * 64);
+        const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * hc);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) tg[q] = __ldg(row + q);
+        for (int q = 0; q < 8; ++q)
+          if (q < nq) tg[q] = __ldg(row + q);
       }
       if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
         *sAbort = 1;
@@ -363,26 +366,25 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         break;
       }
       tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * hc);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * 64 + c * 32);
-        tmem_ld32(taddr, r);
+      for (int q = 0; q < 8; ++q) {
+        if (q >= nq) break;
+        uint32_t r[8];
+        tmem_ld8(taddr + 8 * q, r);
+        tmem_wait_ld();
+        const uint4 tq = tg[q];
+        const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = c * 32 + i;
-          const uint4 q = tg[col >> 3];
-          const int w2 = (col & 7) >> 1;
-          const uint32_t w = w2 == 0 ? q.x : w2 == 1 ? q.y : w2 == 2 ? q.z : q.w;
-          const uint32_t en = (col & 1) ? (w >> 16) : (w & 0xFFFFu);
-          // V = rint(f 2^S) by adding 1.5 2^23 (exact for |x| <= 2^22): no
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t en = (i & 1) ? (wv[i >> 1] >> 16) : (wv[i >> 1] & 0xFFFFu);
+          // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
           // conversion instruction, which would run on the narrow FP64 /
           // conversion pipe.  The reduction is skipped (not predicated) for
           // invalid entries: issued reductions, even predicated off, are what
           // limits this loop.
           if (en != 0xFFFFu) {
-            const float fsv = __uint_as_float(r[i]) * fscale;
-            const float t = ((en & 0x4000u) ? -fsv : fsv) + 12582912.0f;
+            const float t = fmaf(__uint_as_float(r[i]), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
             atomicAdd(&acc[en & 0x3FFFu], __float_as_int(t) - 0x4B400000);
           }
         }
