@@ -4,9 +4,10 @@ seed 2), inputs resident in HBM (vectors of 94 MB, subspace > 2 GB: larger than
 the 129 MB L2, so no flush is needed between steps).
 
 One step = a Davidson-Liu solve of the lowest root from the standard guess to an
-FP64 residual of `--tol` (default 1e-5, energy error <= |r|^2/gap ~ 1e-9 Eh), in
-the chosen sigma precision (default split BF16 with FP64 Jacobi-Davidson
-refinement), followed by the spin-free 1- and 2-RDMs of the root.
+FP64-class residual of `--tol` (default 1e-5, energy error <= |r|^2/gap ~ 1e-10 Eh),
+in the chosen sigma precision (default: split-BF16 tensor-core sigma on FP32 vectors,
+then Jacobi-Davidson refinement with the double-FP32 sigma), followed by the
+spin-free 1- and 2-RDMs of the root (tensor-core Gram in the reduced-precision modes).
 ``value`` = determinants x sigma vectors built in the timed steps / time (det/s).
 The same run also times one FP64 solve of the same problem, which gives the
 reference energy and the "mixed vs FP64 time-to-1e-8 Eh" comparison.
@@ -39,6 +40,8 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 80.5
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor ratio
+# double-FP32 multiply-add: about 12 FP32 pipe operations for 2 FP64-equivalent flops
+DF32_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 6.0
 OZ_PAIRS = 26  # digit pairs (i, j), 1 <= i, j <= 6, i + j <= 8, of the tensor-core RDM Gram
 
 WORKLOADS = {"cas1414": si.CAS1414, "cas1212": si.CAS1212, "cas88": si.CAS88}
@@ -197,6 +200,19 @@ def kernel_work(name, prob, n_sig64, n_sigm, n_rdm, tables):
         nt = (n * n + 63) // 64  # symmetric Gram: tiles ta <= tb of 64 x 64
         return (2.0 * 64 * 64 * nt * (nt + 1) // 2 * nd * n_rdm, "TFLOP/s", "alu", FP64_PEAK_TFLOPS,
                 "FP64 pipe, nominal")
+    if name == "ss_mma_bf16x2":
+        # one GEMM [H_a | C] [C^T | H_b]^T per vector, 3 BF16 products
+        return (3 * 2.0 * prob.na * prob.nb * (prob.na + prob.nb) * n_sigm, "TFLOP/s", "tensor", bf16s,
+                f"bf16 dense sustained ({src})")
+    if name == "ss_mma_tf32":
+        return (2.0 * prob.na * prob.nb * (prob.na + prob.nb) * n_sigm, "TFLOP/s", "tensor",
+                bf16s * TF32_OVER_BF16, f"bf16 dense sustained ({src}) x nominal tf32/bf16 ratio")
+    if name == "ab_df":
+        return (2.0 * nd * nka * nkb * n_sig64, "TFLOP/s", "alu", DF32_PEAK_TFLOPS,
+                "FP32 pipe / 6 (12 FP32 operations per double-FP32 multiply-add)")
+    if name == "ss_spmm_df":
+        return (2.0 * (nnz_a * prob.nb + nnz_b * prob.na) * n_sig64, "TFLOP/s", "alu", DF32_PEAK_TFLOPS,
+                "FP32 pipe / 6 (12 FP32 operations per double-FP32 multiply-add)")
     if name in ("gram_oz_u", "gram_oz_v"):
         # 26 BF16 digit-pair products (i + j <= 8 of six digits) of the Gram of the
         # symmetric (n(n+1)/2 rows) or antisymmetric (n(n-1)/2 rows) one-body images
