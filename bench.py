@@ -473,6 +473,149 @@ def run_batch(args):
     return 0
 
 
+def run_configs(args):
+    """One JSON line per measurement config besides the headline CAS(14,14) step:
+    C0 CAS(8,8) FP64 (latency: us per sigma and per iteration), C1 CAS(12,12) 4 roots
+    (det/s per 4-vector sigma launch; Davidson to 1e-10 in every precision) and the
+    12-site Hubbard ring, C3 CAS(12,12) state-averaged energy gradient (forward +
+    backward, central differences along random integral directions), C4 batched
+    solves (solves/s, FP64 and BF16x2) and the oracle's own timings on the host."""
+    import torch
+    import paper_2405_10197_gb300 as fg
+    torch.cuda.set_device(0)
+    modes = {"fp64": fg.FORTE_FP64, "df32": fg.FORTE_DF32, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}
+
+    def ev_time(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def sigma_rates(prob, nvec, reps):
+        C = torch.tensor(si.random_vectors(nvec, prob.na, prob.nb, seed=7), device="cuda")
+        S = torch.empty_like(C)
+        out = {}
+        for name, m in modes.items():
+            fg.forte_set_precision(prob.ctx, m)
+            ms = ev_time(lambda: fg.forte_sigma(prob.ctx, C, S, nvec), reps if m != fg.FORTE_FP64 else max(2, reps // 4))
+            out[name] = {"ms_per_launch": ms, "det_per_s": prob.ndet * nvec / (ms / 1000.0)}
+        return out
+
+    def solves(prob, nroots, tol, names):
+        out = {}
+        for name in names:
+            fg.forte_set_precision(prob.ctx, modes[name])
+            prob.davidson(nroots=nroots, tol=tol)  # warm-up (tables, scratch)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            E, C, rn, it = prob.davidson(nroots=nroots, tol=tol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[name] = {"ms": 1000 * dt, "iterations": int(it), "max_residual": float(np.max(rn)),
+                         "energies": [float(e) for e in E]}
+        ref = out["fp64"]["energies"]
+        for name in names:
+            out[name]["max_energy_err_vs_fp64"] = float(np.max(np.abs(np.array(out[name]["energies"]) - ref)))
+        return out
+
+    lines = []
+    # C0
+    cfg = si.CAS88
+    h, eri = si.integrals(8, cfg["n_l"], cfg["seed"])
+    prob = fg.CASProblem(8, 4, 4, h, eri)
+    sr = sigma_rates(prob, 1, 50)
+    sv = solves(prob, 1, 1e-10, ["fp64", "df32", "bf16x2"])
+    c0 = {"config": "C0 CAS(8,8) seed 0, 4,900 determinants", "sigma": sr, "davidson_1e-10": sv,
+          "us_per_sigma_fp64": 1000 * sr["fp64"]["ms_per_launch"],
+          "us_per_iteration_fp64": 1000 * sv["fp64"]["ms"] / max(1, sv["fp64"]["iterations"])}
+    prob.close()
+    lines.append(c0)
+    # C1
+    cfg = si.CAS1212
+    h, eri = si.integrals(12, cfg["n_l"], cfg["seed"])
+    prob = fg.CASProblem(12, 6, 6, h, eri)
+    c1 = {"config": "C1 CAS(12,12) seed 1, 853,776 determinants, 4 roots",
+          "sigma_nvec4": sigma_rates(prob, 4, 10),
+          "davidson_4roots_1e-10": solves(prob, 4, 1e-10, ["fp64", "df32", "tf32", "bf16x2"])}
+    prob.close()
+    h, eri = si.hubbard_ring(12, 1.0, 4.0)
+    prob = fg.CASProblem(12, 6, 6, h, eri)
+    c1["hubbard12_U4_davidson_1e-10"] = solves(prob, 1, 1e-10, ["fp64", "df32", "bf16x2"])
+    prob.close()
+    lines.append(c1)
+    # C3: state-averaged gradient, forward + backward, central differences
+    cfg = si.CAS1212_SA
+    h, eri = si.integrals(12, cfg["n_l"], cfg["seed"])
+    w = [1.0 / 3] * 3
+    c3 = {"config": "C3 CAS(12,12) seed 3, state average of 3 roots (w = 1/3)"}
+    for name in ("fp64", "bf16x2"):
+        ht = torch.tensor(h, requires_grad=True)
+        et = torch.tensor(eri, requires_grad=True)
+        fg.sa_energy(ht, et, 12, 6, 6, w, precision=modes[name], tol=1e-9)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E = fg.sa_energy(ht, et, 12, 6, 6, w, precision=modes[name], tol=1e-9)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        E.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        rng = np.random.default_rng(11)
+        dev = []
+        for _ in range(args.fd_dirs):
+            dh = rng.normal(size=(12, 12)); dh = 0.5 * (dh + dh.T)
+            lin = float((ht.grad.numpy() * dh).sum())
+            eps = 1e-4
+            ep = fg.sa_energy(torch.tensor(h + eps * dh), et.detach(), 12, 6, 6, w, precision=modes[name], tol=1e-10)
+            em = fg.sa_energy(torch.tensor(h - eps * dh), et.detach(), 12, 6, 6, w, precision=modes[name], tol=1e-10)
+            dev.append(abs((float(ep) - float(em)) / (2 * eps) - lin))
+        c3[name] = {"forward_ms": 1000 * (t1 - t0), "backward_ms": 1000 * (t2 - t1), "E_SA": float(E),
+                    "fd_directions": args.fd_dirs, "max_fd_deviation_dh": float(max(dev)) if dev else None}
+    lines.append(c3)
+    # C4: batched solves
+    inst = si.batch_instances()[:args.configs_batch]
+    probs = []
+    for q in inst:
+        hq, eq = si.integrals(q["norb"], q["n_l"], q["seed"])
+        probs.append(dict(norb=q["norb"], nalpha=q["nalpha"], nbeta=q["nbeta"], nroots=q["nroots"], h=hq, eri=eq))
+    fg.forte_batch_solve(probs[:8], precision=fg.FORTE_BF16X2, tol=1e-6)
+    c4 = {"config": f"C4 batched: first {len(probs)} of the 512 seeded instances (orbitals "
+                    f"{sorted(set(q['norb'] for q in inst))}, 1-3 roots)", "roots": int(sum(q["nroots"] for q in inst))}
+    res = {}
+    for name in ("fp64", "bf16x2"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, st = fg.forte_batch_solve(probs, precision=modes[name], tol=1e-6, allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = E
+        c4[name] = {"seconds": dt, "solves_per_s": len(probs) / dt, "not_converged": int((st != 0).sum())}
+    c4["max_energy_diff_bf16x2_vs_fp64"] = float(max(np.max(np.abs(np.array(a) - np.array(b)))
+                                                    for a, b in zip(res["fp64"], res["bf16x2"])))
+    lines.append(c4)
+    # oracle timings on the host (bounded samples)
+    if not args.no_cpu_baseline:
+        import oracle
+        orc = {"config": "oracle (plain C Slater-Condon, FP64) on this host", "threads": oracle.num_threads()}
+        for key, c in (("C0", si.CAS88), ("C1", si.CAS1212)):
+            r, nrows, dt, thr = oracle_sigma_rate(c, seconds=5.0)
+            orc[key + "_sigma_det_per_s"] = r
+        cfg = si.CAS88
+        h, eri = si.integrals(8, cfg["n_l"], cfg["seed"])
+        t0 = time.perf_counter()
+        oracle.davidson(8, 4, 4, h, eri, nroots=1, tol=1e-10)
+        orc["C0_davidson_1e-10_s"] = time.perf_counter() - t0
+        lines.append(orc)
+    for ln in lines:
+        print(json.dumps(ln))
+    return 0
+
+
 def fg_nnz(prob):
     """Stored entries of the alpha and beta same-spin string Hamiltonians: every
     string within two replacements of a row string (itself, singles, doubles)."""
@@ -500,6 +643,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="time forte_batch_solve on the first N instances of the batched workload instead")
+    ap.add_argument("--configs", action="store_true",
+                    help="measure the other configurations (C0, C1, C3, C4, oracle) instead of the headline step")
+    ap.add_argument("--configs-batch", type=int, default=128, help="instances of the batched workload for --configs")
+    ap.add_argument("--fd-dirs", type=int, default=4, help="central-difference directions for the C3 gradient check")
     ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
                     help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
     args = ap.parse_args()
@@ -509,6 +656,8 @@ def main():
         return run_kernel_case(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.configs:
+        return run_configs(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
