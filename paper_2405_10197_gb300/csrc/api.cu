@@ -433,8 +433,8 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
 // preconditioned conjugate gradients whose operator H~ is the reduced-precision
 // sigma and whose preconditioner is |theta - H_II|^-1 (Jacobi-Davidson with an
 // inexact inner solve).  Each outer step costs one FP64 sigma per root.
-static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, const double *X0, double *out,
-                     int max_outer, DvResult &res) {
+static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int outer_mode, const double *X0,
+                     double *out, int max_outer, DvResult &res) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->Ndet;
   const int kmax = std::min(63, nroots * (max_outer + 1));
@@ -475,7 +475,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
       if ((rc = vk_scale(ctx, v, v, 1.0 / sqrt(hn[0]), N))) return rc;
     }
   }
-  if ((rc = sigma_dispatch(ctx, V, HV, nroots, FORTE_DF32))) return rc;
+  if ((rc = sigma_dispatch(ctx, V, HV, nroots, outer_mode))) return rc;
   double prev_rn = INFINITY;
   int k = nroots;
   std::vector<double> G, Gk, w, U, coef, h(66);
@@ -522,7 +522,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
     // an outer step that does not halve the residual means the reduced-precision
     // inner operator no longer resolves the correction: continue with FP64 ones
     const double max_rn = *std::max_element(res.rn.begin(), res.rn.end());
-    if (outer > 0 && max_rn > 0.5 * prev_rn) inner_mode = FORTE_DF32;
+    if (outer > 0 && max_rn > 0.5 * prev_rn) inner_mode = outer_mode;
     prev_rn = max_rn;
     if (all || outer >= max_outer) {
       FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
@@ -583,7 +583,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, con
       FORTE_CUDA_TRY(cudaMemcpyAsync(out, V, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
       return FORTE_OK;
     }
-    if ((rc = sigma_dispatch(ctx, V + (size_t)k0 * N, HV + (size_t)k0 * N, k - k0, FORTE_DF32))) return rc;
+    if ((rc = sigma_dispatch(ctx, V + (size_t)k0 * N, HV + (size_t)k0 * N, k - k0, outer_mode))) return rc;
   }
 }
 
@@ -797,13 +797,15 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     // Davidson with the reduced-precision sigma down to a residual the mixed
     // operator can still resolve, then FP64 Jacobi-Davidson refinement whose
     // inner solves use the mixed sigma
+    // (measured: handing over at 1e-2 .. 3e-1 to a reduced-precision Jacobi-Davidson
+    // stage first needs as many sigma applications and is no faster)
     double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 1e-2 : 1e-3);
     rc = davidson_run<float>(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                              ctx->d_roots, res);
     if (rc) return rc;
     if ((rc = mixed_status(ctx))) return rc;
     int it_in = res.iters;
-    rc = refine_jd(ctx, nroots, tol, ctx->precision, ctx->d_roots, ctx->d_roots, 30, res);
+    rc = refine_jd(ctx, nroots, tol, ctx->precision, FORTE_DF32, ctx->d_roots, ctx->d_roots, 30, res);
     if (rc) return rc;
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = it_in + res.iters;
