@@ -13,8 +13,11 @@
 // and forms hi*hi + hi*lo + lo*hi (kind::f16, FP32 accumulate); FORTE_TF32 rounds to
 // TF32 with round-to-nearest-even before the MMA (kind::tf32, FP32 accumulate).
 //
-// Kernel structure (one CTA per (Ia, vector), 16 warps, warp-specialised):
-//   * all warps build A once in shared memory (K-major, 128-byte swizzle);
+// Kernel structure (persistent: one CTA per SM loops over the items (vector, Ia);
+// 16 warps, warp-specialised):
+//   * warps 5-7 (set-up) build A for the next item in the other half of a double
+//     buffer (K-major, 128-byte swizzle) and write out the sigma row of the item
+//     before last from the other half of a double-buffered accumulator row;
 //   * warps 0-3 (producers) gather the n_kl C rows of each 128-column beta tile,
 //     transpose them into a K-major swizzled stage of a 3-deep ring and arrive on
 //     its `full` mbarrier;
@@ -24,9 +27,11 @@
 //   * warps 8-15 (epilogue) read the accumulator with tcgen05.ld, convert each
 //     valid element to fixed point and add it to the sigma row in shared memory
 //     with integer reductions, then arrive on the accumulator's `tempty` mbarrier.
+// The rings run across item boundaries, so one item's set-up and drain overlap
+// its neighbours' tiles.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel raises the
-// context's device status word, the other roles stop, the MMA thread waits
-// (bounded) for its own MMAs, TMEM is freed and the CTA exits.
+// context's device status word, the other roles stop, the MMA thread drains its
+// own MMAs (bounded), TMEM is freed and the CTA exits.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -38,7 +43,6 @@ namespace forte {
 
 constexpr int MX_THREADS = 512;
 constexpr int MX_TILE_N = 128;
-constexpr int MX_OFF_B = 32768;               // A: 32 KB
 constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
 
 // ------------------------------------------------------------ conversion kernels
@@ -120,42 +124,50 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 
 constexpr int WS_STAGES = 3;                              // B operand ring
 constexpr int WS_ACC = 4;                                 // TMEM accumulators of 128 columns
-constexpr int WS_OFF_ACC = MX_OFF_B + WS_STAGES * MX_STAGE;
-// warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 8-15 epilogue
+constexpr int MX_A_BYTES = 32768;                         // A operand: 2 x 16 KB
+constexpr int WS_OFF_B = 2 * MX_A_BYTES;                  // A double-buffered across items
+constexpr int WS_OFF_ACC = WS_OFF_B + WS_STAGES * MX_STAGE;
+// warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 5-7 item set-up and
+// write-out, 8-15 epilogue
 
+// One CTA per SM, persistent over the items w = (vector, Ia).  For item i the
+// set-up warps write out item i-2's sigma row from acc[i&1] and clear it
+// (`accReady`), then, once the MMAs of item i-2 are done with A[i&1] (`aEmpty`),
+// build A[i&1] and the gather rows of item i (`aFull`).  The producers, the MMA
+// thread and the epilogue run their tile rings across item boundaries, so the
+// set-up and the drain of one item overlap the tiles of its neighbours.
 template <int MODE, typename TO>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabJ, int nN, long long NA,
              long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
-             const float *__restrict__ Sss, TO *__restrict__ S, int *__restrict__ err) {
+             const float *__restrict__ Sss, TO *__restrict__ S, long long nitems, int *__restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
   // the swizzle pattern is a function of the shared-space address: align there
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *sA = sm;
-  uint8_t *sB = sm + MX_OFF_B;
+  uint8_t *sB = sm + WS_OFF_B;
   const long long NB4 = (NB + 3) & ~3LL;
-  int *acc = (int *)(sm + WS_OFF_ACC);
-  int *sJ = (int *)(acc + NB4);
-  uint8_t *sPair = (uint8_t *)(sJ + 64);
-  int8_t *sSgn = (int8_t *)(sPair + 64);
-  uint64_t *bar = (uint64_t *)(((uintptr_t)(sSgn + 64) + 15) & ~(uintptr_t)15);
+  int *accb = (int *)(sm + WS_OFF_ACC);          // acc[2][NB4]
+  int *sJb = accb + 2 * NB4;                     // gather rows [2][64]
+  uint64_t *bar = (uint64_t *)(((uintptr_t)(sJb + 128) + 15) & ~(uintptr_t)15);
   uint64_t *full = bar, *empty = bar + WS_STAGES, *tfull = bar + 2 * WS_STAGES, *tempty = tfull + WS_ACC;
-  uint32_t *sTmem = (uint32_t *)(tempty + WS_ACC);
+  uint64_t *aFull = tempty + WS_ACC, *aEmpty = aFull + 2, *accReady = aEmpty + 2, *accDone = accReady + 2;
+  uint64_t *drain = accDone + 2;
+  uint32_t *sTmem = (uint32_t *)(drain + 1);
   volatile int *sAbort = (volatile int *)(sTmem + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long Ia = blockIdx.x;
-  const long long v = blockIdx.y;
+  const long long nloc = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const long long vpad = NA * NBp, v64 = NA * NB;
-
-  // fixed-point exponent of this vector
-  const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
-  int eb = 0;
-  if (bound > 0.f) frexpf(bound, &eb);
-  const int Sx = (bound > 0.f) ? min(100, 22 - eb) : 0;
-  const float fscale = ldexpf(1.f, Sx);
+  const int ntiles = (int)((NB + MX_TILE_N - 1) / MX_TILE_N);
+  // fixed-point exponent of vector v (bound |f| <= 1.02 n_kl max|g| max|C|)
+  auto sx_of = [&](long long v) -> int {
+    const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
+    int eb = 0;
+    if (bound > 0.f) frexpf(bound, &eb);
+    return (bound > 0.f) ? min(100, 22 - eb) : 0;
+  };
 
   if (warp == 4) tmem_alloc(sTmem, WS_ACC * MX_TILE_N);
   if (tid == 0) {
@@ -167,140 +179,191 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       mbar_init(&tfull[i], 1);
       mbar_init(&tempty[i], 8);
     }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&aFull[i], 3);
+      mbar_init(&aEmpty[i], 1);
+      mbar_init(&accReady[i], 3);
+      mbar_init(&accDone[i], 8);
+    }
+    mbar_init(drain, 1);
     *sAbort = 0;
     fence_mbar_init();
   }
-  if (tid < 64) {
-    if (tid < nkA) {
-      const Repl r = listA[Ia * nkA + tid];
-      sJ[tid] = r.J;
-      sPair[tid] = r.pair;
-      sSgn[tid] = r.sgn;
-    } else {
-      sJ[tid] = 0;
-      sPair[tid] = 0;
-      sSgn[tid] = 0;
-    }
-  }
-  for (long long i = tid; i < NB; i += MX_THREADS) {
-    acc[i] = 0;
-  }
-  __syncthreads();
-
-  // ---- A operand: A[rs][k] = s_k (pq_k|rs), K-major swizzled
-  if (MODE == FORTE_BF16X2) {
-    const int kp = lane;  // k = 2kp, 2kp+1
-    const int k0 = 2 * kp, k1 = 2 * kp + 1;
-    for (int rs = warp; rs < 128; rs += MX_THREADS / 32) {
-      uint32_t wh = 0, wl = 0;
-      if (rs < npair) {
-        if (k0 < nkA) {
-          uint16_t h = gT_hi[rs * npair + sPair[k0]], l = gT_lo[rs * npair + sPair[k0]];
-          if (sSgn[k0] < 0) { h ^= 0x8000u; l ^= 0x8000u; }
-          wh |= h;
-          wl |= l;
-        }
-        if (k1 < nkA) {
-          uint16_t h = gT_hi[rs * npair + sPair[k1]], l = gT_lo[rs * npair + sPair[k1]];
-          if (sSgn[k1] < 0) { h ^= 0x8000u; l ^= 0x8000u; }
-          wh |= (uint32_t)h << 16;
-          wl |= (uint32_t)l << 16;
-        }
-      }
-      *(uint32_t *)(sA + swz(rs, 4 * kp)) = wh;
-      *(uint32_t *)(sA + 16384 + swz(rs, 4 * kp)) = wl;
-    }
-  } else {
-    for (int idx = tid; idx < 128 * 64; idx += MX_THREADS) {
-      const int k = idx & 63, rs = idx >> 6;
-      float val = 0.f;
-      if (rs < npair && k < nkA) {
-        val = gT_t32[rs * npair + sPair[k]];
-        if (sSgn[k] < 0) val = -val;
-      }
-      *(float *)(sA + (k >> 5) * 16384 + swz(rs, (k & 31) * 4)) = val;
-    }
-  }
-  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *sTmem;
-  const int ntiles = (int)((NB + MX_TILE_N - 1) / MX_TILE_N);
-  int issued = 0;  // tiles committed by the MMA thread
+  auto fail = [&]() {
+    *sAbort = 1;
+    atomicExch(err, 1);
+  };
 
-  if (warp < 4) {
-    // ================= producers: B[j][k] = C[J_k][j0 + j], warp p owns columns 32p..32p+31
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = t % WS_STAGES, u = t / WS_STAGES;
-      const long long col0 = (long long)t * MX_TILE_N + 32 * warp;
-      uint4 g[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) g[i] = make_uint4(0, 0, 0, 0);
-      if (MODE == FORTE_BF16X2) {
-#pragma unroll
-        for (int part = 0; part < 2; ++part)
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            const int k = 2 * lane + r;
-            if (k < nkA) {
-              const uint16_t *src = (part ? Clo : Chi) + v * vpad + (long long)sJ[k] * NBp;
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-                if (col0 + 8 * c < NBp) g[part * 8 + r * 4 + c] = __ldg((const uint4 *)(src + col0 + 8 * c));
-            }
-          }
-      } else {
-#pragma unroll
-        for (int atom = 0; atom < 2; ++atom) {
-          const int k = 32 * atom + lane;
-          if (k < nkA) {
-            const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBp;
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-              if (col0 + 4 * c < NBp) g[atom * 8 + c] = __ldg((const uint4 *)(src + col0 + 4 * c));
-          }
+  if (warp >= 5 && warp < 8) {
+    // ================= set-up / write-out (96 threads)
+    const int st = tid - 160;
+    for (long long i = 0; i < nloc + 2; ++i) {
+      const int buf = (int)(i & 1);
+      int *acc = accb + buf * NB4;
+      if (i >= 2) {
+        // write out item i-2 and clear its accumulator row
+        if (!__all_sync(0xffffffffu, mbar_wait_ab(&accDone[buf], (uint32_t)(((i - 2) >> 1) & 1), sAbort))) {
+          fail();
+          break;
         }
+        const long long w = blockIdx.x + (i - 2) * gridDim.x, v = w / NA, Ia = w % NA;
+        const int Sx = sx_of(v);
+        const float *ss = Sss + v * v64 + Ia * NB;
+        TO *out = S + v * v64 + Ia * NB;
+        for (long long x = st; x < NB; x += 96) {
+          out[x] = (TO)((double)ss[x] + ldexp((double)acc[x], -Sx));
+          acc[x] = 0;
+        }
+      } else {
+        for (long long x = st; x < NB4; x += 96) acc[x] = 0;
       }
-      if (t >= WS_STAGES && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
-        *sAbort = 1;
-        atomicExch(err, 1);
+      if (i >= nloc) continue;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accReady[buf]);
+      // A operand and gather rows of item i, once the MMAs of item i-2 are done
+      if (i >= 2 && !__all_sync(0xffffffffu, mbar_wait_ab(&aEmpty[buf], (uint32_t)(((i - 2) >> 1) & 1), sAbort))) {
+        fail();
         break;
       }
-      uint8_t *stg = sB + s * MX_STAGE;
+      const long long w = blockIdx.x + i * gridDim.x, Ia = w % NA;
+      const Repl *la = listA + Ia * nkA;
+      uint8_t *sA = sm + buf * MX_A_BYTES;
+      if (warp == 5) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = lane + 32 * h;
+          sJb[buf * 64 + k] = k < nkA ? la[k].J : 0;
+        }
+      }
+      // A[rs][k] = s_k (pq_k|rs), K-major swizzled
       if (MODE == FORTE_BF16X2) {
-#pragma unroll
-        for (int part = 0; part < 2; ++part) {
-          uint8_t *dst = stg + part * 16384;
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint4 qa = g[part * 8 + c], qb = g[part * 8 + 4 + c];
-            const uint32_t ea[4] = {qa.x, qa.y, qa.z, qa.w}, ebb[4] = {qb.x, qb.y, qb.z, qb.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              const uint32_t lo16 = (i & 1) ? (ea[i >> 1] >> 16) : (ea[i >> 1] & 0xFFFFu);
-              const uint32_t hi16 = (i & 1) ? (ebb[i >> 1] >> 16) : (ebb[i >> 1] & 0xFFFFu);
-              *(uint32_t *)(dst + swz(32 * warp + 8 * c + i, 4 * lane)) = lo16 | (hi16 << 16);
+        const int k0 = 2 * lane, k1 = 2 * lane + 1;  // k pair of this lane
+        Repl r0{}, r1{};
+        if (k0 < nkA) r0 = la[k0];
+        if (k1 < nkA) r1 = la[k1];
+        for (int rs = warp - 5; rs < 128; rs += 3) {
+          uint32_t wh = 0, wl = 0;
+          if (rs < npair) {
+            if (k0 < nkA) {
+              uint16_t h = gT_hi[rs * npair + r0.pair], l = gT_lo[rs * npair + r0.pair];
+              if (r0.sgn < 0) { h ^= 0x8000u; l ^= 0x8000u; }
+              wh |= h;
+              wl |= l;
+            }
+            if (k1 < nkA) {
+              uint16_t h = gT_hi[rs * npair + r1.pair], l = gT_lo[rs * npair + r1.pair];
+              if (r1.sgn < 0) { h ^= 0x8000u; l ^= 0x8000u; }
+              wh |= (uint32_t)h << 16;
+              wl |= (uint32_t)l << 16;
             }
           }
+          *(uint32_t *)(sA + swz(rs, 4 * lane)) = wh;
+          *(uint32_t *)(sA + 16384 + swz(rs, 4 * lane)) = wl;
         }
       } else {
-#pragma unroll
-        for (int atom = 0; atom < 2; ++atom) {
-          uint8_t *dst = stg + atom * 16384;
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint4 q = g[atom * 8 + c];
-            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 0, 4 * lane)) = q.x;
-            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 1, 4 * lane)) = q.y;
-            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 2, 4 * lane)) = q.z;
-            *(uint32_t *)(dst + swz(32 * warp + 4 * c + 3, 4 * lane)) = q.w;
+        for (int idx = st; idx < 128 * 64; idx += 96) {
+          const int k = idx & 63, rs = idx >> 6;
+          float val = 0.f;
+          if (rs < npair && k < nkA) {
+            const Repl r = la[k];
+            val = gT_t32[rs * npair + r.pair];
+            if (r.sgn < 0) val = -val;
           }
+          *(float *)(sA + (k >> 5) * 16384 + swz(rs, (k & 31) * 4)) = val;
         }
       }
       fence_proxy_async();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&full[s]);
+      if (lane == 0) mbar_arrive(&aFull[buf]);
+    }
+  } else if (warp < 4) {
+    // ================= producers: B[j][k] = C[J_k][j0 + j], warp p owns columns 32p..32p+31
+    bool ok = true;
+    for (long long i = 0; i < nloc && ok; ++i) {
+      const int buf = (int)(i & 1);
+      if (!mbar_wait_ab(&aFull[buf], (uint32_t)((i >> 1) & 1), sAbort)) {
+        fail();
+        break;
+      }
+      const long long v = (blockIdx.x + i * gridDim.x) / NA;
+      const int *sJ = sJb + buf * 64;
+      for (int t = 0; t < ntiles; ++t) {
+        const long long gt = i * ntiles + t;
+        const int s = (int)(gt % WS_STAGES);
+        const long long u = gt / WS_STAGES;
+        const long long col0 = (long long)t * MX_TILE_N + 32 * warp;
+        uint4 g[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) g[q] = make_uint4(0, 0, 0, 0);
+        if (MODE == FORTE_BF16X2) {
+#pragma unroll
+          for (int part = 0; part < 2; ++part)
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+              const int k = 2 * lane + r;
+              if (k < nkA) {
+                const uint16_t *src = (part ? Clo : Chi) + v * vpad + (long long)sJ[k] * NBp;
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                  if (col0 + 8 * c < NBp) g[part * 8 + r * 4 + c] = __ldg((const uint4 *)(src + col0 + 8 * c));
+              }
+            }
+        } else {
+#pragma unroll
+          for (int atom = 0; atom < 2; ++atom) {
+            const int k = 32 * atom + lane;
+            if (k < nkA) {
+              const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBp;
+#pragma unroll
+              for (int c = 0; c < 8; ++c)
+                if (col0 + 4 * c < NBp) g[atom * 8 + c] = __ldg((const uint4 *)(src + col0 + 4 * c));
+            }
+          }
+        }
+        if (gt >= WS_STAGES && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
+          fail();
+          ok = false;
+          break;
+        }
+        uint8_t *stg = sB + s * MX_STAGE;
+        if (MODE == FORTE_BF16X2) {
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            uint8_t *dst = stg + part * 16384;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const uint4 qa = g[part * 8 + c], qb = g[part * 8 + 4 + c];
+              const uint32_t ea[4] = {qa.x, qa.y, qa.z, qa.w}, ebb[4] = {qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const uint32_t lo16 = (q & 1) ? (ea[q >> 1] >> 16) : (ea[q >> 1] & 0xFFFFu);
+                const uint32_t hi16 = (q & 1) ? (ebb[q >> 1] >> 16) : (ebb[q >> 1] & 0xFFFFu);
+                *(uint32_t *)(dst + swz(32 * warp + 8 * c + q, 4 * lane)) = lo16 | (hi16 << 16);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int atom = 0; atom < 2; ++atom) {
+            uint8_t *dst = stg + atom * 16384;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const uint4 q = g[atom * 8 + c];
+              *(uint32_t *)(dst + swz(32 * warp + 4 * c + 0, 4 * lane)) = q.x;
+              *(uint32_t *)(dst + swz(32 * warp + 4 * c + 1, 4 * lane)) = q.y;
+              *(uint32_t *)(dst + swz(32 * warp + 4 * c + 2, 4 * lane)) = q.z;
+              *(uint32_t *)(dst + swz(32 * warp + 4 * c + 3, 4 * lane)) = q.w;
+            }
+          }
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);
+      }
     }
   } else if (warp == 4) {
     // ================= MMA issuer
@@ -310,103 +373,119 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       const uint32_t idesc = (MODE == FORTE_BF16X2)
                                  ? ((1u << 4) | (1u << 7) | (1u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24))
                                  : ((1u << 4) | (2u << 7) | (2u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24));
-      const uint32_t a0 = smem_u32(sA);
-      for (int t = 0; t < ntiles; ++t) {
-        const int s = t % WS_STAGES, u = t / WS_STAGES, b = t % WS_ACC, ub = t / WS_ACC;
-        if (!mbar_wait_ab(&full[s], (uint32_t)(u & 1), sAbort) ||
-            (t >= WS_ACC && !mbar_wait_ab(&tempty[b], (uint32_t)((ub - 1) & 1), sAbort))) {
-          *sAbort = 1;
-          atomicExch(err, 1);
+      bool ok = true;
+      for (long long i = 0; i < nloc && ok; ++i) {
+        const int buf = (int)(i & 1);
+        if (!mbar_wait_ab(&aFull[buf], (uint32_t)((i >> 1) & 1), sAbort)) {
+          ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(b * MX_TILE_N);
-        const uint32_t b0 = smem_u32(sB + s * MX_STAGE);
-        if (MODE == FORTE_BF16X2) {
-          // hi*hi + lo*hi + hi*lo  (C part first, integral part second)
-          const uint32_t coff[3] = {0u, 16384u, 0u}, goff[3] = {0u, 0u, 16384u};
-          for (int p = 0; p < 3; ++p)
-            for (int ks = 0; ks < 4; ++ks)
-              mma_issue<MODE>(d, desc_kmajor_sw128(b0 + coff[p] + 32u * ks),
-                              desc_kmajor_sw128(a0 + goff[p] + 32u * ks), idesc, (p | ks) != 0);
-        } else {
-          for (int ks = 0; ks < 8; ++ks) {
-            const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
-            mma_issue<MODE>(d, desc_kmajor_sw128(b0 + off), desc_kmajor_sw128(a0 + off), idesc, ks != 0);
+        const uint32_t a0 = smem_u32(sm + buf * MX_A_BYTES);
+        for (int t = 0; t < ntiles; ++t) {
+          const long long gt = i * ntiles + t;
+          const int s = (int)(gt % WS_STAGES), b = (int)(gt % WS_ACC);
+          const long long u = gt / WS_STAGES, ub = gt / WS_ACC;
+          if (!mbar_wait_ab(&full[s], (uint32_t)(u & 1), sAbort) ||
+              (gt >= WS_ACC && !mbar_wait_ab(&tempty[b], (uint32_t)((ub - 1) & 1), sAbort))) {
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(b * MX_TILE_N);
+          const uint32_t b0 = smem_u32(sB + s * MX_STAGE);
+          if (MODE == FORTE_BF16X2) {
+            // hi*hi + lo*hi + hi*lo  (C part first, integral part second)
+            const uint32_t coff[3] = {0u, 16384u, 0u}, goff[3] = {0u, 0u, 16384u};
+            for (int p = 0; p < 3; ++p)
+              for (int ks = 0; ks < 4; ++ks)
+                mma_issue<MODE>(d, desc_kmajor_sw128(b0 + coff[p] + 32u * ks),
+                                desc_kmajor_sw128(a0 + goff[p] + 32u * ks), idesc, (p | ks) != 0);
+          } else {
+            for (int ks = 0; ks < 8; ++ks) {
+              const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
+              mma_issue<MODE>(d, desc_kmajor_sw128(b0 + off), desc_kmajor_sw128(a0 + off), idesc, ks != 0);
+            }
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&tfull[b]);
         }
-        mma_commit(&empty[s]);
-        mma_commit(&tfull[b]);
-        issued = t + 1;
+        if (ok) mma_commit(&aEmpty[buf]);  // A[buf] free once this item's MMAs are done
       }
+      if (!ok) fail();
     }
     __syncwarp();
-  } else if (warp >= 8) {
+  } else {
     // ================= epilogue: thread = beta string j0 + j (accumulator lane),
     //                   nN/2 pairs rs per warp half (accumulator columns), read
     //                   in blocks of 8 columns
     const int e = warp - 8, lg = e & 3, half = e >> 2;
     const int j = lg * 32 + lane;
     const int hc = nN >> 1, nq = hc >> 3;
-    for (int t = 0; t < ntiles; ++t) {
-      const int b = t % WS_ACC, ub = t / WS_ACC;
-      const long long Jb = (long long)t * MX_TILE_N + j;
-      uint4 tg[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-      if (Jb < NB) {
-        const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * hc);
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nq) tg[q] = __ldg(row + q);
-      }
-      if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
-        *sAbort = 1;
-        atomicExch(err, 1);
+    bool ok = true;
+    for (long long i = 0; i < nloc && ok; ++i) {
+      const int buf = (int)(i & 1);
+      int *acc = accb + buf * NB4;
+      const float fscale = ldexpf(1.f, sx_of((blockIdx.x + i * gridDim.x) / NA));
+      if (!__all_sync(0xffffffffu, mbar_wait_ab(&accReady[buf], (uint32_t)((i >> 1) & 1), sAbort))) {
+        fail();
         break;
       }
-      tc_fence_after();
-      const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * hc);
+      for (int t = 0; t < ntiles; ++t) {
+        const long long gt = i * ntiles + t;
+        const int b = (int)(gt % WS_ACC);
+        const long long ub = gt / WS_ACC;
+        const long long Jb = (long long)t * MX_TILE_N + j;
+        uint4 tg[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (q >= nq) break;
-        uint32_t r[8];
-        tmem_ld8(taddr + 8 * q, r);
-        tmem_wait_ld();
-        const uint4 tq = tg[q];
-        const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
+        for (int q = 0; q < 8; ++q) tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+        if (Jb < NB) {
+          const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * hc);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const uint32_t en = (i & 1) ? (wv[i >> 1] >> 16) : (wv[i >> 1] & 0xFFFFu);
-          // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
-          // conversion instruction, which would run on the narrow FP64 /
-          // conversion pipe.  The reduction is skipped (not predicated) for
-          // invalid entries: issued reductions, even predicated off, are what
-          // limits this loop.
-          if (en != 0xFFFFu) {
-            const float t = fmaf(__uint_as_float(r[i]), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
-            atomicAdd(&acc[en & 0x3FFFu], __float_as_int(t) - 0x4B400000);
+          for (int q = 0; q < 8; ++q)
+            if (q < nq) tg[q] = __ldg(row + q);
+        }
+        if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
+          fail();
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * hc);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q >= nq) break;
+          uint32_t r[8];
+          tmem_ld8(taddr + 8 * q, r);
+          tmem_wait_ld();
+          const uint4 tq = tg[q];
+          const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const uint32_t en = (c & 1) ? (wv[c >> 1] >> 16) : (wv[c >> 1] & 0xFFFFu);
+            // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
+            // conversion instruction, which would run on the narrow FP64 /
+            // conversion pipe.  The reduction is skipped (not predicated) for
+            // invalid entries: issued reductions, even predicated off, are what
+            // limits this loop.
+            if (en != 0xFFFFu) {
+              const float tv = fmaf(__uint_as_float(r[c]), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
+              atomicAdd(&acc[en & 0x3FFFu], __float_as_int(tv) - 0x4B400000);
+            }
           }
         }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
       }
-      tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[b]);
+      if (ok && lane == 0) mbar_arrive(&accDone[buf]);
     }
   }
   __syncthreads();
-  if (*sAbort) {
-    // wait (bounded) for this CTA's MMAs still in flight before TMEM is released
-    if (warp == 4 && lane == 0) {
-      for (int tt = (issued >= WS_ACC ? issued - WS_ACC : 0); tt < issued; ++tt)
-        mbar_wait(&tfull[tt % WS_ACC], (uint32_t)((tt / WS_ACC) & 1));
-    }
-  } else {
-    const float *ss = Sss + v * v64 + Ia * NB;
-    TO *out = S + v * v64 + Ia * NB;
-    for (long long i = tid; i < NB; i += MX_THREADS) {
-      out[i] = (TO)((double)ss[i] + ldexp((double)acc[i], -Sx));
-    }
+  if (*sAbort && warp == 4 && lane == 0) {
+    mma_commit(drain);  // tracks every MMA this thread issued
+    mbar_wait(drain, 0u);
   }
   tc_fence_before();
   __syncthreads();
@@ -417,8 +496,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 // ------------------------------------------------------------ host side
 
 static size_t mx_smem_bytes(long long NB) {
-  return 1024 + WS_OFF_ACC + sizeof(int) * (size_t)((NB + 3) & ~3LL) + 64 * 4 + 64 + 64 + 16 +
-         8 * (2 * WS_STAGES + 2 * WS_ACC) + 16 + 64;
+  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 2 * 64 * 4 + 16 +
+         8 * (2 * WS_STAGES + 2 * WS_ACC + 9) + 16 + 64;
 }
 
 int mixed_setup(forte_ctx *ctx) {
@@ -499,20 +578,23 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
       set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;
     }
-    dim3 grid((unsigned)NA, (unsigned)nvec);
+    int nsm = 0;
+    FORTE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const long long nitems = NA * nvec;
+    dim3 grid((unsigned)std::min<long long>(nitems, nsm));
     if (mode == FORTE_BF16X2) {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2, T>));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
       k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                              ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                             ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
+                                                             ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32, T>));
       FORTE_PROF(ctx, "ab_mma_tf32");
       k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
                                                            ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                           ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, ctx->d_err);
+                                                           ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     }
   } else if (sizeof(T) == 8) {
