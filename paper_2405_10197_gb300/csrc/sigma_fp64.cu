@@ -462,7 +462,11 @@ __global__ void __launch_bounds__(SS_THREADS) k_ss_spmm_df(const int *__restrict
 
 // sigma_ab in double-FP32 for one alpha string Ia (blockIdx.x) and one vector
 // (blockIdx.y): k_ab_fp64 with (hi, lo) operands; the output row stays FP64.
-__global__ void __launch_bounds__(AB_THREADS) k_ab_df(const Repl *__restrict__ listA, int nkA,
+// 16 warps and 32-string tiles: two CTAs fit on an SM, so the tile gathers of one
+// overlap the shared-memory-bound inner products of the other.
+constexpr int AB_DF_THREADS = 512;
+constexpr int AB_DF_TJ = 32;
+__global__ void __launch_bounds__(AB_DF_THREADS) k_ab_df(const Repl *__restrict__ listA, int nkA,
                                                       const Repl *__restrict__ listB, int nkB, long long NB,
                                                       const float2 *__restrict__ gpair2, int npair,
                                                       const float2 *__restrict__ C2, double *__restrict__ S,
@@ -477,26 +481,26 @@ __global__ void __launch_bounds__(AB_THREADS) k_ab_df(const Repl *__restrict__ l
   double *Sv = S + (long long)blockIdx.y * vstride;
   const Repl *la = listA + Ia * nkA;
   __shared__ int s_J[80];
-  for (int e = threadIdx.x; e < nkA; e += AB_THREADS) s_J[e] = la[e].J;
-  for (int i = threadIdx.x; i < nkA * npair; i += AB_THREADS) {
+  for (int e = threadIdx.x; e < nkA; e += AB_DF_THREADS) s_J[e] = la[e].J;
+  for (int i = threadIdx.x; i < nkA * npair; i += AB_DF_THREADS) {
     const int e = i / npair, rs = i % npair;
     const Repl r = la[e];
     float2 g = gpair2[(size_t)r.pair * npair + rs];
     if (r.sgn < 0) g = make_float2(-g.x, -g.y);
     Gs[i] = g;
   }
-  for (long long i = threadIdx.x; i < NB; i += AB_THREADS) srow[i] = 0.0;
+  for (long long i = threadIdx.x; i < NB; i += AB_DF_THREADS) srow[i] = 0.0;
   __syncthreads();
   for (long long j0 = 0; j0 < NB; j0 += TJ) {
     const int tj = (int)min((long long)TJ, NB - j0);
-    for (int i = threadIdx.x; i < nkA * tj; i += AB_THREADS) {
+    for (int i = threadIdx.x; i < nkA * tj; i += AB_DF_THREADS) {
       const int e = i / tj, j = i % tj;
       D[e * TJ + j] = Cv[(long long)s_J[e] * NB + j0 + j];
     }
-    for (int i = threadIdx.x; i < tj * nkB; i += AB_THREADS) Lb[i] = listB[j0 * nkB + i];
+    for (int i = threadIdx.x; i < tj * nkB; i += AB_DF_THREADS) Lb[i] = listB[j0 * nkB + i];
     __syncthreads();
     const int npairs_tile = tj * nkB;
-    for (int w = threadIdx.x; w < npairs_tile; w += AB_THREADS) {
+    for (int w = threadIdx.x; w < npairs_tile; w += AB_DF_THREADS) {
       const int j = w / nkB;
       const Repl rf = Lb[w];
       const float2 *g = Gs + rf.pair;
@@ -508,7 +512,7 @@ __global__ void __launch_bounds__(AB_THREADS) k_ab_df(const Repl *__restrict__ l
     }
     __syncthreads();
   }
-  for (long long i = threadIdx.x; i < NB; i += AB_THREADS) Sv[Ia * NB + i] += srow[i];
+  for (long long i = threadIdx.x; i < NB; i += AB_DF_THREADS) Sv[Ia * NB + i] += srow[i];
 }
 
 static int df_setup(forte_ctx *ctx) {
@@ -585,7 +589,7 @@ int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec) {
       set_error("alpha replacement list too long (%d)", nkA);
       return FORTE_ERR_ARG;
     }
-    int TJ = 64;
+    int TJ = AB_DF_TJ;
     size_t smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
     while (smem > 220 * 1024 && TJ > 8) {
       TJ /= 2;
@@ -598,7 +602,7 @@ int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec) {
     FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_df));
     dim3 grid((unsigned)NA, nvec);
     FORTE_PROF(ctx, "ab_df");
-    k_ab_df<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
+    k_ab_df<<<grid, AB_DF_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
                                             (const float2 *)ctx->d_gpair2, ctx->npair, C2, S, ND, TJ);
     FORTE_LAUNCH_CHECK();
   }
