@@ -240,7 +240,8 @@ def run_ours(args):
     cfg = WORKLOADS[args.workload]
     n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
-    modes = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}
+    modes = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2, "df32": fg.FORTE_DF32,
+             "oz64": fg.FORTE_OZ64}
     mode = modes[args.precision]
     stream = torch.cuda.current_stream()
 
@@ -336,7 +337,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "det/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "tf32": "tf32+f64", "bf16x2": "bf16x2+f64"}[args.precision],
+        "dtype": {"fp64": "f64", "tf32": "tf32+f64", "bf16x2": "bf16x2+f64", "df32": "df32",
+                  "oz64": "bf16-digits+df32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAMES[args.workload], "precision": args.precision, "nroots": nroots,
                    "tol": tol, "step": "Davidson-Liu to FP64 residual tol, then 1-/2-RDM of the root",
@@ -430,7 +432,8 @@ def run_kernel_case(args):
     cfg = WORKLOADS[args.workload]
     n, na, nb = cfg["norb"], cfg["nalpha"], cfg["nbeta"]
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
-    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}[args.precision]
+    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2, "df32": fg.FORTE_DF32,
+            "oz64": fg.FORTE_OZ64}[args.precision]
     prob = fg.CASProblem(n, na, nb, h, eri, precision=mode)
     C = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=12), device="cuda")
     out = {"case": args.kernel_case, "workload": args.workload, "precision": args.precision}
@@ -458,7 +461,8 @@ def run_batch(args):
     for q in inst:
         h, eri = si.integrals(q["norb"], q["n_l"], q["seed"])
         probs.append(dict(norb=q["norb"], nalpha=q["nalpha"], nbeta=q["nbeta"], nroots=q["nroots"], h=h, eri=eri))
-    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}[args.precision]
+    mode = {"fp64": fg.FORTE_FP64, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2, "df32": fg.FORTE_DF32,
+            "oz64": fg.FORTE_OZ64}[args.precision]
     fg.forte_batch_solve(probs[:8], precision=mode, tol=args.tol)  # warm-up (module load, code paths)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -634,7 +638,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cas1414")
-    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16x2"], default="bf16x2")
+    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16x2", "df32", "oz64"], default="bf16x2")
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--ref-seconds", type=float, default=10.0)

@@ -54,15 +54,24 @@ enum {
   FORTE_FP64 = 0,   /* every term in FP64 */
   FORTE_TF32 = 1,   /* tensor-core GEMMs (same-spin and alpha-beta) on TF32-rounded
                        operands, FP32 accumulate; Davidson phase on FP32 vectors,
-                       then refinement with the FORTE_DF32 sigma */
+                       then refinement with the FORTE_OZ64 sigma */
   FORTE_BF16X2 = 2, /* as FORTE_TF32 with split hi+lo BF16 operands
                        (hi*hi + hi*lo + lo*hi) */
-  FORTE_DF32 = 3    /* FP64-class sigma in double-FP32 arithmetic: every FP64
+  FORTE_DF32 = 3,   /* FP64-class sigma in double-FP32 arithmetic: every FP64
                        operand as an unevaluated sum of two FP32 values, exact
                        FP32 products via FMA, compensated sums; relative error
                        ~2^-46 per term.  Davidson as for FORTE_FP64 (FP64 vectors).
                        Not part of the paper's schemes: an FP64 substitute for
                        GPUs whose FP64 pipe is narrow. */
+  FORTE_OZ64 = 4    /* FP64-class sigma whose alpha-beta term is formed on the BF16
+                       tensor cores from exact products of 8-bit digit slices
+                       (integrals and C in 45-bit fixed point per row / 64-string tile,
+                       six digits, digit levels up to 8, 64-bit integer sums);
+                       same-spin terms as in FORTE_DF32.  Davidson as for
+                       FORTE_FP64; also the refinement sigma of FORTE_TF32 /
+                       FORTE_BF16X2.  Needs n(n+1)/2 <= 128 (n <= 15) and
+                       n_kl(alpha) <= 64; otherwise it is FORTE_DF32.  Not part
+                       of the paper's schemes. */
 };
 
 /* Build a CAS problem: string lists (a1), signed single-replacement tables
@@ -89,7 +98,7 @@ const char *forte_last_error(void);
  * default stream). */
 int forte_set_stream(forte_ctx *ctx, void *cuda_stream);
 
-/* Select FORTE_FP64, FORTE_TF32, FORTE_BF16X2 or FORTE_DF32 for forte_sigma,
+/* Select FORTE_FP64, FORTE_TF32, FORTE_BF16X2, FORTE_DF32 or FORTE_OZ64 for forte_sigma,
  * forte_davidson and forte_rdms (every mode but FORTE_FP64 forms the 2-RDM with
  * the tensor-core Gram).  Default FORTE_FP64.  FORTE_ERR_ARG for other values. */
 int forte_set_precision(forte_ctx *ctx, int mode);

@@ -31,6 +31,7 @@ FORTE_FP64 = 0
 FORTE_TF32 = 1
 FORTE_BF16X2 = 2
 FORTE_DF32 = 3
+FORTE_OZ64 = 4
 
 _ERRNAMES = {1: "FORTE_ERR_ARG", 2: "FORTE_ERR_ALLOC", 3: "FORTE_ERR_CUDA",
              4: "FORTE_ERR_NOT_CONVERGED", 5: "FORTE_ERR_NUMERIC", 6: "FORTE_ERR_TIMEOUT"}

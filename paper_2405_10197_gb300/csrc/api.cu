@@ -106,13 +106,17 @@ static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, 
     ctx->n_sigma_fp64 += nvec;
     return sigma_df(ctx, C, S, nvec);
   }
+  if (mode == FORTE_OZ64) {
+    ctx->n_sigma_fp64 += nvec;
+    return sigma_oz64(ctx, C, S, nvec);
+  }
   ctx->n_sigma_mixed += nvec;
   return sigma_mixed(ctx, C, S, nvec, mode);
 }
 
 static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
-  if (mode == FORTE_FP64 || mode == FORTE_DF32) {
+  if (mode == FORTE_FP64 || mode == FORTE_DF32 || mode == FORTE_OZ64) {
     set_error("FP32 vectors need a reduced-precision sigma");
     return FORTE_ERR_ARG;
   }
@@ -669,6 +673,7 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_roots); cudaFree(ctx->d_guess);
   cudaFree(ctx->d_gT_hi); cudaFree(ctx->d_gT_lo); cudaFree(ctx->d_gT_t32); cudaFree(ctx->d_err);
   cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp); cudaFree(ctx->d_gpair2);
+  cudaFree(ctx->d_ozG); cudaFree(ctx->d_ozGa); cudaFree(ctx->d_ozTabT);
   cudaFree(ctx->d_csr_val2[0]);
   if (!ctx->same_strings) cudaFree(ctx->d_csr_val2[1]);
   for (int s = 0; s < (ctx->same_strings ? 1 : 2); ++s) {
@@ -676,6 +681,7 @@ void forte_destroy(forte_ctx *ctx) {
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
+  ctx->sc_oz.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
@@ -689,7 +695,8 @@ int forte_set_stream(forte_ctx *ctx, void *s) {
 
 int forte_set_precision(forte_ctx *ctx, int mode) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
-  if (mode != FORTE_FP64 && mode != FORTE_TF32 && mode != FORTE_BF16X2 && mode != FORTE_DF32) {
+  if (mode != FORTE_FP64 && mode != FORTE_TF32 && mode != FORTE_BF16X2 && mode != FORTE_DF32 &&
+      mode != FORTE_OZ64) {
     set_error("unknown precision mode %d", mode);
     return FORTE_ERR_ARG;
   }
@@ -788,10 +795,11 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
   if (rc) return rc;
   DvResult res;
   ctx->nroots_done = 0;
-  if (ctx->precision == FORTE_FP64 || ctx->precision == FORTE_DF32) {
+  if (ctx->precision == FORTE_FP64 || ctx->precision == FORTE_DF32 || ctx->precision == FORTE_OZ64) {
     rc = davidson_run<double>(ctx, nroots, tol, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                               ctx->d_roots, res);
     if (rc) return rc;
+    if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = res.iters;
   } else {
     // Davidson with the reduced-precision sigma down to a residual the mixed
@@ -805,7 +813,9 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     if (rc) return rc;
     if ((rc = mixed_status(ctx))) return rc;
     int it_in = res.iters;
-    rc = refine_jd(ctx, nroots, tol, ctx->precision, FORTE_DF32, ctx->d_roots, ctx->d_roots, 30, res);
+    // outer sigma: FP64-class, with the tensor-core alpha-beta term where it applies
+    const int outer = oz_ab_supported(ctx) ? FORTE_OZ64 : FORTE_DF32;
+    rc = refine_jd(ctx, nroots, tol, ctx->precision, outer, ctx->d_roots, ctx->d_roots, 30, res);
     if (rc) return rc;
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = it_in + res.iters;

@@ -26,7 +26,8 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     set_error("forte_batch_solve: bad arguments");
     return FORTE_ERR_ARG;
   }
-  if (precision != FORTE_FP64 && precision != FORTE_TF32 && precision != FORTE_BF16X2 && precision != FORTE_DF32) {
+  if (precision != FORTE_FP64 && precision != FORTE_TF32 && precision != FORTE_BF16X2 && precision != FORTE_DF32 &&
+      precision != FORTE_OZ64) {
     set_error("forte_batch_solve: unknown precision %d", precision);
     return FORTE_ERR_ARG;
   }

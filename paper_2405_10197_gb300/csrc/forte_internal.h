@@ -122,6 +122,12 @@ struct forte_ctx {
   uint16_t *d_ozT = nullptr;    // [n*n][Nb padded to 64]: E_sr |Ib> of the beta strings (RDM Gram)
   double *d_g1tmp = nullptr;    // 1-RDM workspace of the tensor-core 2-RDM when the caller passes none
   float gmax = 0.f;             // max |(pq|rs)| (bounds the alpha-beta fixed-point scale)
+  // FP64-class tensor-core alpha-beta term: digits of the integrals
+  // [6][npair][128] (BF16 bits) and their row exponents [128]
+  uint16_t *d_ozG = nullptr;
+  int *d_ozGa = nullptr;
+  uint16_t *d_ozTabT = nullptr;  // [128][Nb padded to 64]: the beta scatter table, pair-major
+  double oz_gmax = 0.0;
 
   // Davidson controls and results
   int dv_max_sub = 12, dv_collapse = 2, dv_max_iter = 200;
@@ -141,6 +147,7 @@ struct forte_ctx {
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
   forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
+  forte::Scratch sc_oz;            // digit bytes and scales of the tensor-core FP64-class sigma
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -175,8 +182,14 @@ int upload_tables(forte_ctx *ctx);
 // sigma_fp64.cu
 int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
 int hdiag_build(forte_ctx *ctx);
-// FP64-class sigma in double-FP32 arithmetic (relative error ~2^-46 per term)
-int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec);
+// FP64-class sigma in double-FP32 arithmetic (relative error ~2^-46 per term);
+// with_ab = false leaves out the alpha-beta term (same-spin terms only)
+int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec, bool with_ab = true);
+
+// sigma_oz.cu: FP64-class sigma whose alpha-beta term is formed from exact digit
+// products on the tensor cores (precision mode FORTE_OZ64)
+bool oz_ab_supported(const forte_ctx *ctx);
+int sigma_oz64(forte_ctx *ctx, const double *C, double *S, int nvec);
 
 int same_spin_f32(forte_ctx *ctx, const float *C32, float *S32, float *T1, float *T2, int nvec);
 

@@ -22,7 +22,7 @@
 //    determinants the level sums  L_t = sum_{i+j=t} sum_k d_i(a,k) d_j(b,k),
 //    t = 2..8, are integers below 2^23 and are summed exactly by the MMA in FP32
 //    (one TMEM accumulator per level).  Pairs with i + j > 8 are dropped: their
-//    weight is below 2^-50 of the product of the two row maxima.  The epilogue
+//    weight is at most 2^-49.99 of 64 times the product of the two row maxima.  The epilogue
 //    folds the levels into one 64-bit integer per Gram element (units of 2^6 L_8,
 //    the only rounding being L_7 and L_8 to even integers and L_8 to units of
 //    2^5) and flushes it to an FP64 partial sum every 16 chunks.
@@ -38,14 +38,14 @@
 // Every mbarrier wait is bounded (the context status word is raised on expiry,
 // the other roles stop, TMEM is released).
 #include <algorithm>
+#include <type_traits>
 
 #include "forte_internal.h"
+#include "oz_digits.cuh"
 #include "tc_ptx.cuh"
 
 namespace forte {
 
-constexpr int OZ_DIGITS = 6;
-constexpr int OZ_TMAX = 8;
 constexpr int OZ_KC = 64;
 constexpr int OZ_SLOTS = 4;
 constexpr int OZ_PROD_WARPS = 3;
@@ -54,20 +54,7 @@ constexpr int OZ_RB = 4;                    // rows per producer load batch
 constexpr int OZ_EPI_WARPS = 16;
 constexpr int OZ_THREADS = 32 * (OZ_PROD_WARPS + 1 + OZ_EPI_WARPS);  // 20 warps: 96 registers
 constexpr int OZ_FLUSH = 16;
-constexpr int OZ_XBITS = 45;        // |X| <= 2^45 after the row shift
 constexpr int OZ_CBITS = 52;        // |C_fix| <= 2^52
-
-// Level shifts into the 64-bit accumulator (units of 2^6 L_8): L_t carries
-// weight 2^(8(8-t)) L_8, so the shift is 8(8-t) - 6; L_7 arrives in units of 2.
-__host__ __device__ constexpr int oz_shift(int t) { return t == 7 ? 3 : 8 * (8 - t) - 6; }
-// Sum over levels 2..7 of (magic bits << shift), modulo 2^64: the magic-number
-// rounding adds 0x4B400000 (1.5 2^23) or 0x4BC00000 (1.5 2^24) to every level.
-__host__ __device__ constexpr unsigned long long oz_bias() {
-  unsigned long long b = 0;
-  for (int t = 2; t <= 6; ++t) b += (unsigned long long)0x4B400000u << oz_shift(t);
-  b += (unsigned long long)0x4BC00000u << oz_shift(7);
-  return b;
-}
 
 template <int N>
 struct OzLayout {
@@ -218,12 +205,6 @@ __device__ __forceinline__ long long oz_scale(long long u, int sh) {
   return sh > 0 ? ((u + (1LL << (sh - 1))) >> sh) : (u << (-sh));
 }
 
-// FP32 bits of (byte k of w) - 128: the byte is placed under the exponent of
-// 1.5 2^23 and the bias is subtracted exactly.
-__device__ __forceinline__ uint32_t oz_dig(uint32_t w, uint32_t k) {
-  return __float_as_uint(__uint_as_float(__byte_perm(w, 0x4B400000u, 0x7650u | k)) - 12583040.0f);
-}
-
 // Six BF16 digit slices of X0 (column Ib) and X1 (column Ib+1), packed in pairs:
 // out[i] holds digit d_(i+1) of both columns.
 __device__ __forceinline__ void oz_digits2(long long X0, long long X1, uint32_t (&out)[OZ_DIGITS]) {
@@ -255,19 +236,6 @@ __device__ __forceinline__ void tmem_ldw(uint32_t taddr, uint32_t *r) {
     if constexpr ((W & 4) != 0) tmem_ld4(taddr + o, r + o);
   }
   tmem_wait_ld();
-}
-
-template <int T>
-__device__ __forceinline__ void oz_acc_level(unsigned long long &acc, uint32_t fbits) {
-  const float f = __uint_as_float(fbits);
-  if constexpr (T <= 6) {
-    acc += (unsigned long long)__float_as_uint(f + 12582912.0f) << oz_shift(T);
-  } else if constexpr (T == 7) {
-    acc += (unsigned long long)__float_as_uint(f + 25165824.0f) << oz_shift(7);
-  } else {
-    const int v = (int)(__float_as_uint(f + 25165824.0f) - 0x4BC00000u);  // L_8 / 2
-    acc += (unsigned long long)(long long)((v + 16) >> 5);
-  }
 }
 
 // One level of one chunk in the epilogue: wait for the accumulator, read this
@@ -469,27 +437,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t base = smem_u32(sm + st * L::STAGE);
-        bool ok = true;
-        for (int t = 2; t <= OZ_TMAX; ++t, ++q) {
+        const uint64_t base = desc_kmajor_sw128(smem_u32(sm + st * L::STAGE));
+        // one level: wait for its accumulator slot, issue its chain, commit
+        auto level = [&](auto tc) -> bool {
+          constexpr int T = decltype(tc)::value;
           const int slot = (int)(q % OZ_SLOTS);
-          if (q >= OZ_SLOTS && !mbar_wait_ab(&tempty[slot], (uint32_t)(((q / OZ_SLOTS) - 1) & 1), sAbort)) {
-            ok = false;
-            break;
-          }
+          if (q >= OZ_SLOTS && !mbar_wait_ab(&tempty[slot], (uint32_t)(((q / OZ_SLOTS) - 1) & 1), sAbort)) return false;
           tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(slot * N);
-          uint32_t accum = 0;
-          for (int ks = 0; ks < OZ_KC / 16; ++ks)
-            for (int i = max(1, t - OZ_DIGITS); i <= min(OZ_DIGITS, t - 1); ++i) {
-              const int j = t - i;
-              mma_issue<FORTE_BF16X2>(d, desc_kmajor_sw128(base + (uint32_t)((i - 1) * L::SLICE + 32 * ks)),
-                                      desc_kmajor_sw128(base + (uint32_t)((j - 1) * L::SLICE + 32 * ks)), idesc,
-                                      accum);
-              accum = 1;
-            }
+          oz_issue_level<T, L::SLICE / 16, L::SLICE / 16, OZ_KC / 16>(tmem + (uint32_t)(slot * N), base, base, idesc);
           mma_commit(&tfull[slot]);
-        }
+          ++q;
+          return true;
+        };
+        const bool ok = level(std::integral_constant<int, 2>{}) && level(std::integral_constant<int, 3>{}) &&
+                        level(std::integral_constant<int, 4>{}) && level(std::integral_constant<int, 5>{}) &&
+                        level(std::integral_constant<int, 6>{}) && level(std::integral_constant<int, 7>{}) &&
+                        level(std::integral_constant<int, 8>{});
         mma_commit(&empty[st]);  // also covers a chunk cut short by an abort
         issued = it + 1;
         if (!ok) {

@@ -536,7 +536,7 @@ static int df_setup(forte_ctx *ctx) {
   return FORTE_OK;
 }
 
-int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec) {
+int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec, bool with_ab) {
   int rc = df_setup(ctx);
   if (rc) return rc;
   cudaStream_t st = ctx->stream;
@@ -584,7 +584,7 @@ int sigma_df(forte_ctx *ctx, const double *C, double *S, int nvec) {
     }
   }
   const int nkA = ctx->sh[0].nk, nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
-  if (nkA > 0 && nkB > 0) {
+  if (with_ab && nkA > 0 && nkB > 0) {
     if (nkA > 80) {
       set_error("alpha replacement list too long (%d)", nkA);
       return FORTE_ERR_ARG;

@@ -393,18 +393,21 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(b * MX_TILE_N);
-          const uint32_t b0 = smem_u32(sB + s * MX_STAGE);
+          // descriptors of the operand bases; offsets in 16-byte units
+          const uint64_t bd = desc_kmajor_sw128(smem_u32(sB + s * MX_STAGE)), ad = desc_kmajor_sw128(a0);
           if (MODE == FORTE_BF16X2) {
             // hi*hi + lo*hi + hi*lo  (C part first, integral part second)
-            const uint32_t coff[3] = {0u, 16384u, 0u}, goff[3] = {0u, 0u, 16384u};
+            constexpr uint32_t coff[3] = {0u, 1024u, 0u}, goff[3] = {0u, 0u, 1024u};
+#pragma unroll
             for (int p = 0; p < 3; ++p)
+#pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                mma_issue<MODE>(d, desc_kmajor_sw128(b0 + coff[p] + 32u * ks),
-                                desc_kmajor_sw128(a0 + goff[p] + 32u * ks), idesc, (p | ks) != 0);
+                mma_issue<MODE>(d, bd + (coff[p] + 2u * ks), ad + (goff[p] + 2u * ks), idesc, (p | ks) != 0);
           } else {
+#pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
-              const uint32_t off = (uint32_t)(ks >> 2) * 16384u + 32u * (ks & 3);
-              mma_issue<MODE>(d, desc_kmajor_sw128(b0 + off), desc_kmajor_sw128(a0 + off), idesc, ks != 0);
+              const uint32_t off = (uint32_t)(ks >> 2) * 1024u + 2u * (ks & 3);
+              mma_issue<MODE>(d, bd + off, ad + off, idesc, ks != 0);
             }
           }
           mma_commit(&empty[s]);
