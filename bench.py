@@ -213,6 +213,11 @@ def kernel_work(name, prob, n_sig64, n_sigm, n_rdm, tables):
     if name == "ss_spmm_df":
         return (2.0 * (nnz_a * prob.nb + nnz_b * prob.na) * n_sig64, "TFLOP/s", "alu", DF32_PEAK_TFLOPS,
                 "FP32 pipe / 6 (12 FP32 operations per double-FP32 multiply-add)")
+    if name == "ab_oz":
+        # FORTE_OZ64 alpha-beta term: 26 BF16 digit-pair products of the contraction
+        # F[rs][Jb] = sum_k A[rs][k] B[Jb][k] over the n(n+1)/2 pairs and n_kl(alpha)
+        return (OZ_PAIRS * 2.0 * nd * npair * nka * n_sig64, "TFLOP/s", "tensor", bf16s,
+                f"bf16 dense sustained ({src})")
     if name in ("gram_oz_u", "gram_oz_v"):
         # 26 BF16 digit-pair products (i + j <= 8 of six digits) of the Gram of the
         # symmetric (n(n+1)/2 rows) or antisymmetric (n(n-1)/2 rows) one-body images
