@@ -48,9 +48,13 @@ template <int T>
 __device__ __forceinline__ void oz_acc_level(unsigned long long &acc, uint32_t fbits) {
   const float f = __uint_as_float(fbits);
   if constexpr (T <= 6) {
-    acc += (unsigned long long)__float_as_uint(f + 12582912.0f) << oz_shift(T);
+    const uint32_t m = __float_as_uint(f + 12582912.0f);
+    if constexpr (oz_shift(T) >= 32)
+      acc += (unsigned long long)(m << (oz_shift(T) - 32)) << 32;  // high word only
+    else
+      acc += (unsigned long long)m * (1ull << oz_shift(T));  // one wide multiply-add
   } else if constexpr (T == 7) {
-    acc += (unsigned long long)__float_as_uint(f + 25165824.0f) << oz_shift(7);
+    acc += (unsigned long long)__float_as_uint(f + 25165824.0f) * (1ull << oz_shift(7));
   } else {
     const int v = (int)(__float_as_uint(f + 25165824.0f) - 0x4BC00000u);  // L_8 / 2
     acc += (unsigned long long)(long long)((v + 16) >> 5);

@@ -420,8 +420,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     __syncwarp();
   } else {
     // ================= epilogue: thread = beta string j0 + j (accumulator lane),
-    //                   nN/2 pairs rs per warp half (accumulator columns), read
-    //                   in blocks of 8 columns
+    //                   nN/2 pairs rs per warp half (accumulator columns)
     const int e = warp - 8, lg = e & 3, half = e >> 2;
     const int j = lg * 32 + lane;
     const int hc = nN >> 1, nq = hc >> 3;
@@ -455,31 +454,41 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * hc);
+        // all of this warp's columns in one round trip, then the accumulator is released
+        // before the scatter (a load / wait per 8-column block left the warps waiting on
+        // tensor-memory latency and the MMA thread waiting on them)
+        uint32_t ra[32], rb[32];
+        tmem_ld32(taddr, ra);
+        if (hc == 64) {
+          tmem_ld32(taddr + 32, rb);
+        } else {
+          tmem_ld16(taddr + 32, rb);
+          tmem_ld8(taddr + 48, rb + 16);
+        }
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           if (q >= nq) break;
-          uint32_t r[8];
-          tmem_ld8(taddr + 8 * q, r);
-          tmem_wait_ld();
           const uint4 tq = tg[q];
           const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const uint32_t en = (c & 1) ? (wv[c >> 1] >> 16) : (wv[c >> 1] & 0xFFFFu);
+            const uint32_t rv = q < 4 ? ra[8 * q + c] : rb[8 * (q - 4) + c];
             // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
             // conversion instruction, which would run on the narrow FP64 /
             // conversion pipe.  The reduction is skipped (not predicated) for
             // invalid entries: issued reductions, even predicated off, are what
             // limits this loop.
             if (en != 0xFFFFu) {
-              const float tv = fmaf(__uint_as_float(r[c]), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
+              const float tv = fmaf(__uint_as_float(rv), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
               atomicAdd(&acc[en & 0x3FFFu], __float_as_int(tv) - 0x4B400000);
             }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[b]);
       }
       __syncwarp();
       if (ok && lane == 0) mbar_arrive(&accDone[buf]);
