@@ -492,7 +492,8 @@ def run_configs(args):
     import torch
     import paper_2405_10197_gb300 as fg
     torch.cuda.set_device(0)
-    modes = {"fp64": fg.FORTE_FP64, "df32": fg.FORTE_DF32, "tf32": fg.FORTE_TF32, "bf16x2": fg.FORTE_BF16X2}
+    modes = {"fp64": fg.FORTE_FP64, "df32": fg.FORTE_DF32, "oz64": fg.FORTE_OZ64, "tf32": fg.FORTE_TF32,
+             "bf16x2": fg.FORTE_BF16X2}
 
     def ev_time(fn, reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -538,7 +539,7 @@ def run_configs(args):
     h, eri = si.integrals(8, cfg["n_l"], cfg["seed"])
     prob = fg.CASProblem(8, 4, 4, h, eri)
     sr = sigma_rates(prob, 1, 50)
-    sv = solves(prob, 1, 1e-10, ["fp64", "df32", "bf16x2"])
+    sv = solves(prob, 1, 1e-10, ["fp64", "df32", "oz64", "bf16x2"])
     c0 = {"config": "C0 CAS(8,8) seed 0, 4,900 determinants", "sigma": sr, "davidson_1e-10": sv,
           "us_per_sigma_fp64": 1000 * sr["fp64"]["ms_per_launch"],
           "us_per_iteration_fp64": 1000 * sv["fp64"]["ms"] / max(1, sv["fp64"]["iterations"])}
@@ -550,11 +551,11 @@ def run_configs(args):
     prob = fg.CASProblem(12, 6, 6, h, eri)
     c1 = {"config": "C1 CAS(12,12) seed 1, 853,776 determinants, 4 roots",
           "sigma_nvec4": sigma_rates(prob, 4, 10),
-          "davidson_4roots_1e-10": solves(prob, 4, 1e-10, ["fp64", "df32", "tf32", "bf16x2"])}
+          "davidson_4roots_1e-10": solves(prob, 4, 1e-10, ["fp64", "df32", "oz64", "tf32", "bf16x2"])}
     prob.close()
     h, eri = si.hubbard_ring(12, 1.0, 4.0)
     prob = fg.CASProblem(12, 6, 6, h, eri)
-    c1["hubbard12_U4_davidson_1e-10"] = solves(prob, 1, 1e-10, ["fp64", "df32", "bf16x2"])
+    c1["hubbard12_U4_davidson_1e-10"] = solves(prob, 1, 1e-10, ["fp64", "df32", "oz64", "bf16x2"])
     prob.close()
     lines.append(c1)
     # C3: state-averaged gradient, forward + backward, central differences
