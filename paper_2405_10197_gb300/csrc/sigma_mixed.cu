@@ -306,10 +306,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             for (int r = 0; r < 2; ++r) {
               const int k = 2 * lane + r;
               if (k < nkA) {
+                // 32-byte loads (the row base and col0 are 64-byte aligned): half the
+                // L1TEX sector requests of 16-byte ones, each lane reading its own row
                 const uint16_t *src = (part ? Clo : Chi) + v * vpad + (long long)sJ[k] * NBp;
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                  if (col0 + 8 * c < NBp) g[part * 8 + r * 4 + c] = __ldg((const uint4 *)(src + col0 + 8 * c));
+                for (int c = 0; c < 4; c += 2)
+                  if (col0 + 8 * c < NBp) ldg256(src + col0 + 8 * c, g[part * 8 + r * 4 + c], g[part * 8 + r * 4 + c + 1]);
               }
             }
         } else {
@@ -319,8 +321,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
             if (k < nkA) {
               const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBp;
 #pragma unroll
-              for (int c = 0; c < 8; ++c)
-                if (col0 + 4 * c < NBp) g[atom * 8 + c] = __ldg((const uint4 *)(src + col0 + 4 * c));
+              for (int c = 0; c < 8; c += 2)
+                if (col0 + 4 * c < NBp) ldg256(src + col0 + 4 * c, g[atom * 8 + c], g[atom * 8 + c + 1]);
             }
           }
         }

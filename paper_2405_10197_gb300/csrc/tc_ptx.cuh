@@ -79,6 +79,12 @@ __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint6
         : "memory");
   }
 }
+// One 256-bit read-only global load (32-byte aligned address) into two uint4.
+__device__ __forceinline__ void ldg256(const void *p, uint4 &a, uint4 &b) {
+  asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+               : "l"(p));
+}
 // tcgen05.mma with the A operand in tensor memory (kind::f16, BF16 inputs): A row m
 // is TMEM lane m, 16-bit K elements packed two per 32-bit column (even k in the
 // low half); a_tmem addresses the column of the first K element of the step.
