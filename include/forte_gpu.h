@@ -133,7 +133,8 @@ int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
  * counter generator) so that closed-shell guesses still reach roots of every
  * spin-flip symmetry sector, orthonormalised; preconditioner
  * (theta - H_II)^-1 with |denominator| clamped to denom_guard; classical
- * Gram-Schmidt applied twice; subspace collapse (forte_set_davidson_params).
+ * Gram-Schmidt, with a second pass when the first removes more than half of
+ * the correction's squared norm; subspace collapse (forte_set_davidson_params).
  * In a mixed mode the inner iterations use that mode's sigma and the final
  * residuals and energies are refined with FP64 sigma builds until the FP64
  * residual meets tol.  Results stay in the context (forte_get_roots).

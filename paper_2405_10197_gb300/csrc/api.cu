@@ -400,14 +400,24 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       std::vector<double> h_d(65);
       FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, b, d_d0, N))) return rc;     // copy + B^T t + |t|^2
+      std::vector<double> h0(65);
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h0.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
       if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N))) return rc;    // CGS pass 1
-      if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N))) return rc;    // CGS pass 2
-      std::vector<double> n0(1);
-      FORTE_CUDA_TRY(cudaMemcpyAsync(n0.data(), d_d0 + k, sizeof(double), cudaMemcpyDeviceToHost, st));
-      FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d2, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+      // second pass only when the first removed more than half of |t|^2 (the
+      // criterion of Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30 (1976) 772:
+      // ||t1|| >= ||t0|| / sqrt(2), with ||t1||^2 = ||t0||^2 - ||B^T t0||^2)
+      double proj = 0.0;
+      for (int i = 0; i < k; ++i) proj += h0[i] * h0[i];
+      const double *dfin = d_d1;
+      if (!(h0[k] - proj >= 0.5 * h0[k])) {
+        if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N))) return rc;  // CGS pass 2
+        dfin = d_d2;
+      }
+      FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), dfin, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
       FORTE_CUDA_TRY(cudaStreamSynchronize(st));
       double nn = h_d[k];
-      if (!(nn > 1e-24 * n0[0]) || !(nn > 0.0)) continue;  // linearly dependent: drop
+      if (!(nn > 1e-24 * h0[k]) || !(nn > 0.0)) continue;  // linearly dependent: drop
       if ((rc = vk_scale(ctx, b, b, 1.0 / sqrt(nn), N))) return rc;
       ++k;
     }
@@ -574,11 +584,17 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       FORTE_CUDA_TRY(cudaMemcpyAsync(vk, px, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
       FORTE_CUDA_TRY(cudaMemsetAsync(d_a, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
-      if ((rc = fetch(d_b + k, 1, h.data()))) return rc;
-      const double n0 = h[0];
+      if ((rc = fetch(d_b, k + 1, h.data()))) return rc;
+      const double n0 = h[k];
+      double proj = 0.0;
+      for (int i = 0; i < k; ++i) proj += h[i] * h[i];
       if ((rc = vk_orth_update(ctx, V, k, N, d_b, vk, vk, d_a, N))) return rc;
-      if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
-      if ((rc = fetch(d_b + k, 1, h.data()))) return rc;
+      const double *dfin = d_a;
+      if (!(n0 - proj >= 0.5 * n0)) {  // second Gram-Schmidt pass only when needed (as in davidson_run)
+        if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
+        dfin = d_b;
+      }
+      if ((rc = fetch(dfin + k, 1, h.data()))) return rc;
       if (!(h[0] > 1e-24 * n0) || !(h[0] > 0.0)) continue;
       if ((rc = vk_scale(ctx, vk, vk, 1.0 / sqrt(h[0]), N))) return rc;
       ++k;
