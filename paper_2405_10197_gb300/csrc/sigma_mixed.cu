@@ -90,6 +90,44 @@ __global__ void k_split(const TI *__restrict__ C, float *__restrict__ C32, uint1
   }
 }
 
+// The same split for FP32 vectors (the reduced-precision Davidson phase): one
+// thread per padded element of one (vector, alpha string) row, FP32 arithmetic
+// (bit-identical to the FP64 route: the BF16 hi part is x rounded to nearest even,
+// x - hi is exact in FP32, the TF32 copy keeps 10 mantissa bits, nearest even).
+// grid = (column blocks, NA, vector).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_split_rows(const float *__restrict__ C, uint16_t *__restrict__ hi,
+                                                    uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA,
+                                                    long long NB, long long NBp, unsigned *__restrict__ cmax_bits) {
+  __shared__ unsigned red[8];
+  const long long v = blockIdx.z, row = blockIdx.y;
+  const long long b = (long long)blockIdx.x * 256 + threadIdx.x;
+  unsigned mx = 0u;
+  if (b < NBp) {
+    const float x = b < NB ? C[(v * NA + row) * NB + b] : 0.f;
+    mx = __float_as_uint(fabsf(x));
+    const long long o = (v * NA + row) * NBp + b;
+    if (MODE == FORTE_BF16X2) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      hi[o] = __bfloat16_as_ushort(h);
+      lo[o] = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    } else {
+      uint32_t u = __float_as_uint(x);
+      u += 0xFFFu + ((u >> 13) & 1u);
+      t32[o] = __uint_as_float(u & ~0x1FFFu);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned m = 0u;
+    for (int w = 0; w < 8; ++w) m = max(m, red[w]);
+    if (m) atomicMax(cmax_bits + v, m);
+  }
+}
+
 // gT[rs][pq] = (pq|rs) for rs < 128 (zero rows beyond npair), split/rounded.
 __global__ void k_split_g(const double *__restrict__ gpair, int npair, uint16_t *__restrict__ hi,
                           uint16_t *__restrict__ lo, float *__restrict__ t32) {
@@ -574,10 +612,18 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
     const long long per = NA * NBp;
     dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
-    if (mode == FORTE_BF16X2)
+    if (sizeof(T) == 4) {
+      const float *Cf = (const float *)(const void *)C;
+      dim3 g2((unsigned)((NBp + 255) / 256), (unsigned)NA, (unsigned)nvec);
+      if (mode == FORTE_BF16X2)
+        k_split_rows<FORTE_BF16X2><<<g2, 256, 0, st>>>(Cf, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+      else
+        k_split_rows<FORTE_TF32><<<g2, 256, 0, st>>>(Cf, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+    } else if (mode == FORTE_BF16X2) {
       k_split<FORTE_BF16X2, T><<<grid, 256, 0, st>>>(C, C32w, Chi, Clo, nullptr, NA, NB, NBp, cmax);
-    else
+    } else {
       k_split<FORTE_TF32, T><<<grid, 256, 0, st>>>(C, C32w, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+    }
     FORTE_LAUNCH_CHECK();
   }
   if (ssm)

@@ -288,6 +288,45 @@ __global__ void k_split_t(const TI *__restrict__ C, long long NA, long long NB, 
   }
 }
 
+// k_split_t for FP32 vectors: 64 x 64 tiles, each thread writes two consecutive
+// transposed elements as one 32-bit (BF16 pair) or 64-bit (TF32 pair) store.
+// Rounding as in k_split_rows.  grid = (NAp / 64, NB / 64, vector), block (32, 8).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_split_t64(const float *__restrict__ C, long long NA, long long NB,
+                                                   long long NAp, uint16_t *__restrict__ hi, uint16_t *__restrict__ lo,
+                                                   float *__restrict__ t32) {
+  __shared__ float tile[64][65];
+  const long long v = blockIdx.z;
+  const long long a0 = (long long)blockIdx.x * 64, b0 = (long long)blockIdx.y * 64;
+  const float *Cv = C + v * NA * NB;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int i = ty; i < 64; i += 8)
+    for (int j = tx; j < 64; j += 32) {
+      const long long a = a0 + i, b = b0 + j;
+      tile[i][j] = (a < NA && b < NB) ? Cv[a * NB + b] : 0.f;
+    }
+  __syncthreads();
+  const long long a = a0 + 2 * tx;
+  for (int i = ty; i < 64; i += 8) {
+    const long long b = b0 + i;
+    if (b >= NB || a >= NAp) continue;
+    const float x0 = tile[2 * tx][i], x1 = tile[2 * tx + 1][i];
+    const long long o = (v * NB + b) * NAp + a;  // even: NAp and a are even
+    if (MODE == FORTE_BF16X2) {
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+      *(uint32_t *)(hi + o) = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+      *(uint32_t *)(lo + o) = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    } else {
+      uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
+      u0 += 0xFFFu + ((u0 >> 13) & 1u);
+      u1 += 0xFFFu + ((u1 >> 13) & 1u);
+      *(float2 *)(t32 + o) = make_float2(__uint_as_float(u0 & ~0x1FFFu), __uint_as_float(u1 & ~0x1FFFu));
+    }
+  }
+}
+
 // ------------------------------------------------------------ host side
 
 static PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
@@ -377,10 +416,18 @@ static int same_spin_mma_t(forte_ctx *ctx, const TI *C, const uint16_t *Chi, con
   {
     dim3 tb(32, 8), g((unsigned)((NAp + 31) / 32), (unsigned)((NB + 31) / 32), (unsigned)nvec);
     FORTE_PROF(ctx, "split_t");
-    if (bf)
+    if (sizeof(TI) == 4) {
+      const float *Cf = (const float *)(const void *)C;
+      dim3 g64((unsigned)((NAp + 63) / 64), (unsigned)((NB + 63) / 64), (unsigned)nvec);
+      if (bf)
+        k_split_t64<FORTE_BF16X2><<<g64, tb, 0, st>>>(Cf, NA, NB, NAp, Thi, Tlo, nullptr);
+      else
+        k_split_t64<FORTE_TF32><<<g64, tb, 0, st>>>(Cf, NA, NB, NAp, nullptr, nullptr, Tt);
+    } else if (bf) {
       k_split_t<FORTE_BF16X2, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, Thi, Tlo, nullptr);
-    else
+    } else {
       k_split_t<FORTE_TF32, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, nullptr, nullptr, Tt);
+    }
     FORTE_LAUNCH_CHECK();
   }
   SsmMaps maps;
