@@ -32,7 +32,7 @@ def _small_batch(count, seed):
     return probs
 
 
-@pytest.mark.parametrize("precision", [fg.FORTE_FP64, fg.FORTE_BF16X2])
+@pytest.mark.parametrize("precision", [fg.FORTE_FP64, fg.FORTE_BF16X2, fg.FORTE_OZ64])
 def test_batch_matches_oracle_dense(precision):
     probs = _small_batch(40, seed=3)
     E, st = fg.forte_batch_solve(probs, precision=precision, tol=1e-10, nworkers=6)

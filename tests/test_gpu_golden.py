@@ -41,7 +41,7 @@ def _bound(g):
 
 
 @pytest.mark.parametrize("path", FILES, ids=[os.path.basename(f)[:-5] for f in FILES])
-@pytest.mark.parametrize("mode", [fg.FORTE_FP64, fg.FORTE_BF16X2])
+@pytest.mark.parametrize("mode", [fg.FORTE_FP64, fg.FORTE_BF16X2, fg.FORTE_OZ64])
 def test_golden_energies(path, mode):
     g = json.load(open(path))
     assert _bound(g) < 1e-10

@@ -116,3 +116,23 @@ def test_sa_gradient_cas1212_three_roots():
         ep = _energy(*args_p, n, na, nb, w, precision=fg.FORTE_BF16X2)
         em = _energy(*args_m, n, na, nb, w, precision=fg.FORTE_BF16X2)
         assert abs((ep - em) / (2 * step) - an) < 1e-6, kind
+
+def test_sa_gradient_oz64_mode_matches_fp64_mode():
+    """forte_sa_gradient after FORTE_OZ64 solves equals the FP64-mode gradient.  Both
+    solves stop at residual 1e-9, so the gradients agree to ~residual / gap (gaps
+    0.13 and 0.15 here); the energies differ by the sigma error of the mode (1e-12 of
+    max |sigma|, ~1e-11 Eh here)."""
+    n, na, nb = 8, 4, 4
+    h, eri = si.integrals(n, 16, seed=3)
+    w = [0.5, 0.5]
+    out = []
+    for mode in (fg.FORTE_FP64, fg.FORTE_OZ64):
+        ht = torch.tensor(h, requires_grad=True)
+        et = torch.tensor(eri, requires_grad=True)
+        E = fg.sa_energy(ht, et, n, na, nb, w, precision=mode, tol=1e-9)
+        E.backward()
+        out.append((float(E.detach()), ht.grad.numpy().copy(), et.grad.numpy().copy()))
+    de = abs(out[0][0] - out[1][0])
+    dh = np.abs(out[0][1] - out[1][1]).max()
+    dg = np.abs(out[0][2] - out[1][2]).max()
+    assert de < 1e-10 and dh < 1e-7 and dg < 1e-7, (de, dh, dg)
