@@ -157,37 +157,46 @@ __device__ __forceinline__ long long oz_value(int gram, int r, int s, long long 
 }
 
 // rowmax[g][a] = max over determinants of |u_a| (g = 0) and |v_a| (g = 1).
-// One block per alpha string; warp w takes rows a = w, w + 8, ...
+// One block per alpha string; warp w takes the pairs r >= s with index w, w + 8, ...
+// and forms D^{rs} and D^{sr} once for both u_rs = D^{rs} + D^{sr} and
+// v_rs = D^{rs} - D^{sr} (u_rr = D^{rr}).
 __global__ void __launch_bounds__(256) k_oz_rowmax(const long long *__restrict__ Cfix, const int *__restrict__ denseA,
                                                    const uint16_t *__restrict__ T, int n, long long NA, long long NB,
                                                    long long NbP, unsigned long long *__restrict__ rowmax) {
   extern __shared__ long long crow[];
   __shared__ int atab[256];
-  const int n2 = n * n, nU = n * (n + 1) / 2, nV = n * (n - 1) / 2;
+  const int n2 = n * n, nU = n * (n + 1) / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (long long Ia = blockIdx.x; Ia < NA; Ia += gridDim.x) {
     __syncthreads();
     for (long long i = threadIdx.x; i < NbP; i += blockDim.x) crow[i] = Cfix[Ia * NbP + i];
     for (int i = threadIdx.x; i < n2; i += blockDim.x) atab[i] = denseA[Ia * n2 + i];
     __syncthreads();
-    for (int ga = warp; ga < nU + nV; ga += 8) {
-      const int g = ga < nU ? 0 : 1, a = ga < nU ? ga : ga - nU;
+    for (int a = warp; a < nU; a += 8) {  // u row index a: pairs r > s first, then the diagonal
       int r, s;
       oz_row(a, n, r, s);
       const int e1 = atab[s * n + r], e2 = atab[r * n + s];
       const uint16_t *t1 = T + (size_t)(s * n + r) * NbP, *t2 = T + (size_t)(r * n + s) * NbP;
-      unsigned long long m = 0;
+      unsigned long long mu = 0, mv = 0;
       for (long long Ib = 2 * lane; Ib < NB; Ib += 64) {
         long long a0, a1, b0 = 0, b1 = 0;
         oz_pair(e1, *(const uint32_t *)(t1 + Ib), Cfix, NbP, Ib, crow, a0, a1);
         if (r != s) oz_pair(e2, *(const uint32_t *)(t2 + Ib), Cfix, NbP, Ib, crow, b0, b1);
-        const long long u0 = oz_value(g, r, s, a0, b0), u1 = oz_value(g, r, s, a1, b1);
-        m = max(m, (unsigned long long)(u0 < 0 ? -u0 : u0));
-        m = max(m, (unsigned long long)(u1 < 0 ? -u1 : u1));
+        const long long u0 = oz_value(0, r, s, a0, b0), u1 = oz_value(0, r, s, a1, b1);
+        const long long v0 = a0 - b0, v1 = a1 - b1;
+        mu = max(mu, (unsigned long long)(u0 < 0 ? -u0 : u0));
+        mu = max(mu, (unsigned long long)(u1 < 0 ? -u1 : u1));
+        mv = max(mv, (unsigned long long)(v0 < 0 ? -v0 : v0));
+        mv = max(mv, (unsigned long long)(v1 < 0 ? -v1 : v1));
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0 && m) atomicMax(rowmax + g * 128 + a, m);
+      for (int o = 16; o > 0; o >>= 1) {
+        mu = max(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        mv = max(mv, __shfl_xor_sync(0xffffffffu, mv, o));
+      }
+      if (lane == 0 && mu) atomicMax(rowmax + a, mu);
+      // the v rows are the pairs r > s in the same order (index a < n(n-1)/2)
+      if (lane == 0 && mv && r != s) atomicMax(rowmax + 128 + a, mv);
     }
   }
 }
