@@ -596,17 +596,21 @@ def run_configs(args):
     fg.forte_batch_solve(probs[:8], precision=fg.FORTE_BF16X2, tol=1e-6)
     c4 = {"config": f"C4 batched: first {len(probs)} of the 512 seeded instances (orbitals "
                     f"{sorted(set(q['norb'] for q in inst))}, 1-3 roots)", "roots": int(sum(q["nroots"] for q in inst))}
-    res = {}
+    res, sts = {}, {}
     for name in ("fp64", "bf16x2"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         E, st = fg.forte_batch_solve(probs, precision=modes[name], tol=1e-6, allow_not_converged=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        res[name] = E
-        c4[name] = {"seconds": dt, "solves_per_s": len(probs) / dt, "not_converged": int((st != 0).sum())}
-    c4["max_energy_diff_bf16x2_vs_fp64"] = float(max(np.max(np.abs(np.array(a) - np.array(b)))
-                                                    for a, b in zip(res["fp64"], res["bf16x2"])))
+        res[name], sts[name] = E, st
+        c4[name] = {"seconds": dt, "solves_per_s": len(probs) / dt, "not_converged": int((st != 0).sum()),
+                    "not_converged_instances": [int(i) for i in np.nonzero(st != 0)[0]]}
+    diffs = [float(np.max(np.abs(np.array(a) - np.array(b)))) for a, b in zip(res["fp64"], res["bf16x2"])]
+    both = [d for d, a, b in zip(diffs, sts["fp64"], sts["bf16x2"]) if a == 0 and b == 0]
+    c4["max_energy_diff_bf16x2_vs_fp64"] = max(diffs)
+    c4["max_energy_diff_where_both_converged"] = max(both) if both else None
+    c4["instance_of_max_diff"] = int(np.argmax(diffs))
     lines.append(c4)
     # oracle timings on the host (bounded samples)
     if not args.no_cpu_baseline:
