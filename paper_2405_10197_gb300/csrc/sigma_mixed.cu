@@ -90,13 +90,29 @@ __global__ void k_split(const TI *__restrict__ C, float *__restrict__ C32, uint1
   }
 }
 
-// The same split for FP32 vectors (the reduced-precision Davidson phase): one
-// thread per padded element of one (vector, alpha string) row, FP32 arithmetic
-// (bit-identical to the FP64 route: the BF16 hi part is x rounded to nearest even,
-// x - hi is exact in FP32, the TF32 copy keeps 10 mantissa bits, nearest even).
-// grid = (column blocks, NA, vector).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_split_rows(const float *__restrict__ C, uint16_t *__restrict__ hi,
+// The same split without 64-bit index arithmetic: one thread per padded element of
+// one (vector, alpha string) row.  The BF16 hi part is x rounded to nearest even,
+// x - hi is exact in the input precision, the TF32 copy keeps 10 mantissa bits
+// (nearest even): bit-identical to k_split.  grid = (column blocks, NA, vector).
+__device__ __forceinline__ void split_bf16(float x, uint16_t &h, uint16_t &l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+  h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
+}
+__device__ __forceinline__ void split_bf16(double x, uint16_t &h, uint16_t &l) {
+  const __nv_bfloat16 hb = __double2bfloat16(x);
+  h = __bfloat16_as_ushort(hb);
+  l = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(hb)));
+}
+__device__ __forceinline__ float tf32_rne(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & ~0x1FFFu);
+}
+__device__ __forceinline__ float tf32_rne(double x) { return (float)rne_drop(x, 42); }
+
+template <int MODE, typename TI>
+__global__ void __launch_bounds__(256) k_split_rows(const TI *__restrict__ C, uint16_t *__restrict__ hi,
                                                     uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA,
                                                     long long NB, long long NBp, unsigned *__restrict__ cmax_bits) {
   __shared__ unsigned red[8];
@@ -104,18 +120,13 @@ __global__ void __launch_bounds__(256) k_split_rows(const float *__restrict__ C,
   const long long b = (long long)blockIdx.x * 256 + threadIdx.x;
   unsigned mx = 0u;
   if (b < NBp) {
-    const float x = b < NB ? C[(v * NA + row) * NB + b] : 0.f;
-    mx = __float_as_uint(fabsf(x));
+    const TI x = b < NB ? C[(v * NA + row) * NB + b] : TI(0);
+    mx = __float_as_uint(fabsf((float)x));
     const long long o = (v * NA + row) * NBp + b;
-    if (MODE == FORTE_BF16X2) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      hi[o] = __bfloat16_as_ushort(h);
-      lo[o] = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
-    } else {
-      uint32_t u = __float_as_uint(x);
-      u += 0xFFFu + ((u >> 13) & 1u);
-      t32[o] = __uint_as_float(u & ~0x1FFFu);
-    }
+    if (MODE == FORTE_BF16X2)
+      split_bf16(x, hi[o], lo[o]);
+    else
+      t32[o] = tf32_rne(x);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -612,13 +623,12 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
     const long long per = NA * NBp;
     dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
-    if (sizeof(T) == 4) {
-      const float *Cf = (const float *)(const void *)C;
+    if (!C32w) {  // no FP32 copy wanted: the row kernel
       dim3 g2((unsigned)((NBp + 255) / 256), (unsigned)NA, (unsigned)nvec);
       if (mode == FORTE_BF16X2)
-        k_split_rows<FORTE_BF16X2><<<g2, 256, 0, st>>>(Cf, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+        k_split_rows<FORTE_BF16X2, T><<<g2, 256, 0, st>>>(C, Chi, Clo, nullptr, NA, NB, NBp, cmax);
       else
-        k_split_rows<FORTE_TF32><<<g2, 256, 0, st>>>(Cf, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+        k_split_rows<FORTE_TF32, T><<<g2, 256, 0, st>>>(C, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
     } else if (mode == FORTE_BF16X2) {
       k_split<FORTE_BF16X2, T><<<grid, 256, 0, st>>>(C, C32w, Chi, Clo, nullptr, NA, NB, NBp, cmax);
     } else {

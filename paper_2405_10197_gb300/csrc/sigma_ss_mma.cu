@@ -259,70 +259,57 @@ __global__ void k_dense_h(const int *__restrict__ ptr, const int *__restrict__ c
   }
 }
 
-// Transposed split: Ct[v][Ib][Ia] (pitch NAp, zero for Ia >= NA) from C[v][Ia][Ib].
-template <int MODE, typename TI>
-__global__ void k_split_t(const TI *__restrict__ C, long long NA, long long NB, long long NAp,
-                          uint16_t *__restrict__ hi, uint16_t *__restrict__ lo, float *__restrict__ t32) {
-  __shared__ double tile[32][33];
-  const long long v = blockIdx.z;
-  const long long a0 = (long long)blockIdx.x * 32, b0 = (long long)blockIdx.y * 32;
-  const TI *Cv = C + v * NA * NB;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long long a = a0 + i, b = b0 + threadIdx.x;
-    tile[i][threadIdx.x] = (a < NA && b < NB) ? (double)Cv[a * NB + b] : 0.0;
-  }
-  __syncthreads();
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const long long b = b0 + i, a = a0 + threadIdx.x;
-    if (b < NB && a < NAp) {
-      const double x = tile[threadIdx.x][i];
-      const long long o = (v * NB + b) * NAp + a;
-      if (MODE == FORTE_BF16X2) {
-        const double h = rne_drop(x, 45);
-        hi[o] = bf16_bits(h);
-        lo[o] = bf16_bits(rne_drop(x - h, 45));
-      } else {
-        t32[o] = (float)rne_drop(x, 42);
-      }
-    }
-  }
+// Transposed split copies of C for the same-spin GEMM: T[v][b][a] = split(C[v][a][b]),
+// a padded to NAp with zeros.  64 x 64 tiles, each thread writes two consecutive
+// transposed elements as one 32-bit (BF16 pair) or 64-bit (TF32 pair) store.  BF16:
+// hi = x rounded to nearest even, lo = the remainder rounded likewise; TF32: 10
+// mantissa bits, nearest even.  grid = (NAp / 64, NB / 64,
+// vector), block (32, 8).
+__device__ __forceinline__ uint32_t ssm_bf16_hi(float x, uint16_t &lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+  return __bfloat16_as_ushort(h);
 }
+__device__ __forceinline__ uint32_t ssm_bf16_hi(double x, uint16_t &lo) {
+  const __nv_bfloat16 h = __double2bfloat16(x);
+  lo = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(h)));
+  return __bfloat16_as_ushort(h);
+}
+__device__ __forceinline__ float ssm_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & ~0x1FFFu);
+}
+__device__ __forceinline__ float ssm_tf32(double x) { return (float)rne_drop(x, 42); }
 
-// k_split_t for FP32 vectors: 64 x 64 tiles, each thread writes two consecutive
-// transposed elements as one 32-bit (BF16 pair) or 64-bit (TF32 pair) store.
-// Rounding as in k_split_rows.  grid = (NAp / 64, NB / 64, vector), block (32, 8).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_split_t64(const float *__restrict__ C, long long NA, long long NB,
+template <int MODE, typename TI>
+__global__ void __launch_bounds__(256) k_split_t64(const TI *__restrict__ C, long long NA, long long NB,
                                                    long long NAp, uint16_t *__restrict__ hi, uint16_t *__restrict__ lo,
                                                    float *__restrict__ t32) {
-  __shared__ float tile[64][65];
+  __shared__ TI tile[64][65];
   const long long v = blockIdx.z;
   const long long a0 = (long long)blockIdx.x * 64, b0 = (long long)blockIdx.y * 64;
-  const float *Cv = C + v * NA * NB;
+  const TI *Cv = C + v * NA * NB;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int i = ty; i < 64; i += 8)
     for (int j = tx; j < 64; j += 32) {
       const long long a = a0 + i, b = b0 + j;
-      tile[i][j] = (a < NA && b < NB) ? Cv[a * NB + b] : 0.f;
+      tile[i][j] = (a < NA && b < NB) ? Cv[a * NB + b] : TI(0);
     }
   __syncthreads();
   const long long a = a0 + 2 * tx;
   for (int i = ty; i < 64; i += 8) {
     const long long b = b0 + i;
     if (b >= NB || a >= NAp) continue;
-    const float x0 = tile[2 * tx][i], x1 = tile[2 * tx + 1][i];
+    const TI x0 = tile[2 * tx][i], x1 = tile[2 * tx + 1][i];
     const long long o = (v * NB + b) * NAp + a;  // even: NAp and a are even
     if (MODE == FORTE_BF16X2) {
-      const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-      const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-      const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-      *(uint32_t *)(hi + o) = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-      *(uint32_t *)(lo + o) = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+      uint16_t l0, l1;
+      const uint32_t h0 = ssm_bf16_hi(x0, l0), h1 = ssm_bf16_hi(x1, l1);
+      *(uint32_t *)(hi + o) = h0 | (h1 << 16);
+      *(uint32_t *)(lo + o) = (uint32_t)l0 | ((uint32_t)l1 << 16);
     } else {
-      uint32_t u0 = __float_as_uint(x0), u1 = __float_as_uint(x1);
-      u0 += 0xFFFu + ((u0 >> 13) & 1u);
-      u1 += 0xFFFu + ((u1 >> 13) & 1u);
-      *(float2 *)(t32 + o) = make_float2(__uint_as_float(u0 & ~0x1FFFu), __uint_as_float(u1 & ~0x1FFFu));
+      *(float2 *)(t32 + o) = make_float2(ssm_tf32(x0), ssm_tf32(x1));
     }
   }
 }
@@ -414,20 +401,13 @@ static int same_spin_mma_t(forte_ctx *ctx, const TI *C, const uint16_t *Chi, con
   uint16_t *Thi = (uint16_t *)tw, *Tlo = Thi + (size_t)nvec * NB * NAp;
   float *Tt = (float *)tw;
   {
-    dim3 tb(32, 8), g((unsigned)((NAp + 31) / 32), (unsigned)((NB + 31) / 32), (unsigned)nvec);
+    dim3 tb(32, 8);
     FORTE_PROF(ctx, "split_t");
-    if (sizeof(TI) == 4) {
-      const float *Cf = (const float *)(const void *)C;
-      dim3 g64((unsigned)((NAp + 63) / 64), (unsigned)((NB + 63) / 64), (unsigned)nvec);
-      if (bf)
-        k_split_t64<FORTE_BF16X2><<<g64, tb, 0, st>>>(Cf, NA, NB, NAp, Thi, Tlo, nullptr);
-      else
-        k_split_t64<FORTE_TF32><<<g64, tb, 0, st>>>(Cf, NA, NB, NAp, nullptr, nullptr, Tt);
-    } else if (bf) {
-      k_split_t<FORTE_BF16X2, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, Thi, Tlo, nullptr);
-    } else {
-      k_split_t<FORTE_TF32, TI><<<g, tb, 0, st>>>(C, NA, NB, NAp, nullptr, nullptr, Tt);
-    }
+    dim3 g64((unsigned)((NAp + 63) / 64), (unsigned)((NB + 63) / 64), (unsigned)nvec);
+    if (bf)
+      k_split_t64<FORTE_BF16X2, TI><<<g64, tb, 0, st>>>(C, NA, NB, NAp, Thi, Tlo, nullptr);
+    else
+      k_split_t64<FORTE_TF32, TI><<<g64, tb, 0, st>>>(C, NA, NB, NAp, nullptr, nullptr, Tt);
     FORTE_LAUNCH_CHECK();
   }
   SsmMaps maps;
