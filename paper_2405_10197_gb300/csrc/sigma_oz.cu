@@ -10,14 +10,14 @@
 // integer digit products (oz_digits.cuh).  Row rs of the integrals is held in
 // fixed point relative to its own maximum, the columns Jb of a 64-string tile of C
 // relative to the maximum of |C| over that tile, both with |X| <= 2^45, six BF16
-// digits each; the levels
-// t = 2..8 (26 digit-pair MMAs per 16-deep K step) are exact.  Each F element is
-// an exact 64-bit integer up to the dropped levels (at most 2^-49.99 of K times
-// the product of the two scales); it is rounded once onto the 64-bit fixed-point grid of the output
-// row (2^-62 of the bound n_kl(alpha) n_kl(beta) max|g| max|C|) and added with
-// integer shared-memory reductions, so the sum does not depend on the order of
-// the atomics.  The quantisation of the operands to 45 bits (2^-46 of the row /
-// tile maximum) is the leading error.
+// digits each; the levels t = 2..8 (26 digit-pair MMAs per 16-deep K step) are
+// exact.  Each F element is an exact 64-bit integer up to the dropped levels (at
+// most 2^-49.99 of K times the product of the two scales); it is rounded once onto
+// the 64-bit fixed-point grid of the output row (2^-62 of the bound
+// n_kl(alpha) n_kl(beta) max|g| max|C|) and added with integer shared-memory
+// reductions, so the sum does not depend on the order of the atomics.  The
+// quantisation of the operands to 45 bits (2^-46 of the row / tile maximum) is the
+// leading error.
 //
 // Kernel structure (one CTA per SM, persistent over the items (vector, Ia);
 // 24 warps, warp-specialised).  Each 64-column MMA reads its B operand (2 KB) from
