@@ -20,6 +20,7 @@ from .driver import (  # noqa: F401
     solve_dense,
     davidson,
     rdm12,
+    rdm3,
     rdm2_elements,
     num_threads,
 )

@@ -9,8 +9,8 @@ Sources followed:
 * Davidson-Liu diagonalization: Sec. II.A.1 names the method only; the steps
   below are the textbook ones (subspace Rayleigh-Ritz, residual, diagonal
   preconditioner, Gram-Schmidt, collapse);
-* 1- and 2-RDM definitions: Sec. II.A.1, Eqs. for gamma_1 and gamma_2, summed
-  over spin into the spin-free (chemist-order) quantities.
+* 1-, 2- and 3-RDM definitions: Sec. II.A.1, Eqs. for gamma_1, gamma_2 and
+  gamma_3, summed over spin into the spin-free (chemist-order) quantities.
 """
 from __future__ import annotations
 
@@ -60,6 +60,7 @@ def _L():
             lib.ora_sigma.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_int, dp, dp,
                                                            ctypes.c_long, ctypes.c_void_p]
             lib.ora_rdm12.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_void_p, ctypes.c_void_p]
+            lib.ora_rdm3.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_void_p]
             lib.ora_rdm2_elements.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_long,
                                                                    ctypes.c_void_p, dp]
             lib.ora_num_threads.restype = ctypes.c_int
@@ -264,6 +265,17 @@ def rdm12(norb, nalpha, nbeta, bra, ket=None, one=True, two=True):
     _L().ora_rdm12(norb, nalpha, nbeta, _dp(bra), _dp(ket),
                    g1.ctypes.data if one else None, g2.ctypes.data if two else None)
     return g1, g2
+
+
+def rdm3(norb, nalpha, nbeta, bra, ket=None):
+    """Spin-free Gamma3 [n]*6: g3[p,q,r,s,t,u] = sum over spins of
+    <bra| a+_p a+_r a+_t a_u a_s a_q |ket> (pairs (p,q), (r,s), (t,u) share a spin),
+    by operator application on every determinant; bra = ket when ket is None."""
+    bra = _f64(bra).reshape(-1)
+    ket = bra if ket is None else _f64(ket).reshape(-1)
+    g3 = np.zeros((norb,) * 6)
+    _L().ora_rdm3(norb, nalpha, nbeta, _dp(bra), _dp(ket), g3.ctypes.data)
+    return g3
 
 
 def rdm2_elements(norb, nalpha, nbeta, vec, idx):

@@ -367,6 +367,58 @@ void ora_rdm12(int n, int na, int nb, const double *bra, const double *ket, doub
   space_free(&sp);
 }
 
+/* Spin-free 3-RDM (Sec. II.A.1, the three-body gamma_3 of the string CI codes,
+ * summed over spin):
+ *   g3[p][q][r][s][t][u] = sum_{s1 s2 s3} <bra| a+_{p s1} a+_{r s2} a+_{t s3} a_{u s3} a_{s s2} a_{q s1} |ket>
+ * (chemist-like order: creator p pairs with annihilator q, r with s, t with u).
+ * Like ora_rdm12: every element by applying the operator string to each ket
+ * determinant.  Cost n^6 * 8 * N_det: for small spaces only. */
+void ora_rdm3(int n, int na, int nb, const double *bra, const double *ket, double *g3) {
+  space_t sp;
+  space_init(&sp, n, na, nb);
+  long Nd = sp.Na * sp.Nb;
+  long *ma = (long *)malloc(sizeof(long) << n), *mb = (long *)malloc(sizeof(long) << n);
+  for (long m = 0; m < (1L << n); ++m) ma[m] = mb[m] = -1;
+  for (long i = 0; i < sp.Na; ++i) ma[sp.sa[i]] = i;
+  for (long i = 0; i < sp.Nb; ++i) mb[sp.sb[i]] = i;
+  uint64_t lowmask = (1ULL << n) - 1ULL;
+  long n3 = (long)n * n * n;
+#pragma omp parallel for schedule(dynamic)
+  for (long pqr = 0; pqr < n3; ++pqr) {
+    int p = (int)(pqr / (n * n)), q = (int)((pqr / n) % n), r = (int)(pqr % n);
+    for (int s_ = 0; s_ < n; ++s_)
+      for (int t = 0; t < n; ++t)
+        for (int u = 0; u < n; ++u) {
+          double acc = 0.0;
+          for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2)
+              for (int s3 = 0; s3 < 2; ++s3)
+                for (long j = 0; j < Nd; ++j) {
+                  double c = ket[j];
+                  if (c == 0.0) continue;
+                  uint64_t d = det_of(&sp, j / sp.Nb, j % sp.Nb);
+                  int s = op_ann(&d, q + s1 * n);
+                  if (!s) continue;
+                  s *= op_ann(&d, s_ + s2 * n);
+                  if (!s) continue;
+                  s *= op_ann(&d, u + s3 * n);
+                  if (!s) continue;
+                  s *= op_cre(&d, t + s3 * n);
+                  if (!s) continue;
+                  s *= op_cre(&d, r + s2 * n);
+                  if (!s) continue;
+                  s *= op_cre(&d, p + s1 * n);
+                  if (!s) continue;
+                  long ia = ma[d & lowmask], ib = mb[(d >> n) & lowmask];
+                  acc += s * bra[ia * sp.Nb + ib] * c;
+                }
+          g3[((((((size_t)p * n + q) * n + r) * n + s_) * n + t) * n) + u] = acc;
+        }
+  }
+  free(ma); free(mb);
+  space_free(&sp);
+}
+
 /* Selected 2-RDM elements: idx[4*e..4*e+3] = (p,q,r,s); out[e] = g2[p][q][r][s]. */
 void ora_rdm2_elements(int n, int na, int nb, const double *bra, const double *ket,
                        long nel, const int *idx, double *out) {

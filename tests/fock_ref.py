@@ -100,6 +100,35 @@ def rdms(n, na, nb, vec, E=None):
     return g1, g2
 
 
+def rdm3(n, na, nb, vec, E=None):
+    """Spin-free Gamma3_pqrstu (pairs (p,q), (r,s), (t,u) share a spin) from
+    expectation values of E-operator products and the normal-ordering identity
+    E_pq E_rs E_tu = g_pqrstu + d_qt e_purs + d_st e_pqru + d_qr E_ps E_tu,
+    with e the two-body operator of Gamma2 (e_pqrs = E_pq E_rs - d_qr E_ps):
+      Gamma3 = <E_pq E_rs E_tu> - d_qt G2_purs - d_st G2_pqru - d_qr (G2_pstu + d_st g1_pu)."""
+    if E is None:
+        E, _ = excitation_ops(n)
+    g1, g2 = rdms(n, na, nb, vec, E)
+    v = embed(n, na, nb, vec)
+    Ev = {(t, u): E[t][u] @ v for t in range(n) for u in range(n)}
+    left = {(p, q): E[p][q].T @ v for p in range(n) for q in range(n)}  # (E_pq)^T v: <v|E_pq = (E_pq^T v)^T
+    g3 = np.zeros((n,) * 6)
+    for r, s_, t, u in itertools.product(range(n), repeat=4):
+        w = E[r][s_] @ Ev[(t, u)]
+        for p, q in itertools.product(range(n), repeat=2):
+            val = left[(p, q)] @ w
+            if q == t:
+                val -= g2[p, u, r, s_]
+            if s_ == t:
+                val -= g2[p, q, r, u]
+            if q == r:
+                val -= g2[p, s_, t, u]
+                if s_ == t:
+                    val -= g1[p, u]
+            g3[p, q, r, s_, t, u] = val
+    return g3
+
+
 def s2_expectation(n, na, nb, vec):
     """<S^2> from spin operators S+ = sum_p a+_pa a_pb, Sz = (Na - Nb)/2."""
     a = annihilators(n)

@@ -27,6 +27,11 @@ MUTATIONS = {
          "s *= op_ann(&d, r + tg * n);\n                  if (!s) continue;\n                  s *= op_cre(&d, s_ + tg * n);"),
     "wrong sign of the one-body single element":
         ("double v = h_so(n, h, m, p);", "double v = -h_so(n, h, m, p);"),
+    "3-RDM creators applied in the wrong order":
+        ("s *= op_cre(&d, t + s3 * n);\n                  if (!s) continue;\n                  s *= op_cre(&d, r + s2 * n);",
+         "s *= op_cre(&d, r + s2 * n);\n                  if (!s) continue;\n                  s *= op_cre(&d, t + s3 * n);"),
+    "3-RDM annihilator paired with the wrong spin":
+        ("s *= op_ann(&d, u + s3 * n);", "s *= op_ann(&d, u + s2 * n);"),
     "exchange integral added instead of subtracted":
         ("return v_so(n, eri, P, Q, R, S) - v_so(n, eri, P, Q, S, R);",
          "return v_so(n, eri, P, Q, R, S) + v_so(n, eri, P, Q, S, R);"),

@@ -183,6 +183,57 @@ def test_rdm_invariants(n, na, nb):
     assert np.abs(g2 - g2.transpose(1, 0, 3, 2)).max() < 1e-13
 
 
+@pytest.mark.parametrize("n,na,nb", [(3, 2, 1), (4, 2, 2), (4, 1, 2)])
+def test_rdm3_matches_fock_space_identity(n, na, nb):
+    """The oracle's 3-RDM (operator strings on determinants) against expectation
+    values of E-operator products on the Fock space, reduced by the normal-ordering
+    identity (fock_ref.rdm3)."""
+    h, eri, w, V = _ground(n, na, nb, seed=61)
+    g3 = oracle.rdm3(n, na, nb, V[0])
+    f3 = fock_ref.rdm3(n, na, nb, V[0])
+    assert np.abs(g3 - f3).max() < 1e-13
+
+
+@pytest.mark.parametrize("n,na,nb", [(5, 3, 2), (6, 3, 3)])
+def test_rdm3_invariants(n, na, nb):
+    h, eri, w, V = _ground(n, na, nb, seed=71)
+    N = na + nb
+    g1, g2 = oracle.rdm12(n, na, nb, V[0])
+    g3 = oracle.rdm3(n, na, nb, V[0])
+    assert abs(np.einsum("pprrtt->", g3) - N * (N - 1) * (N - 2)) < 1e-10
+    assert np.abs(np.einsum("pqrstt->pqrs", g3) - (N - 2) * g2).max() < 1e-12
+    # the three (creator, annihilator) pairs commute as units
+    assert np.abs(g3 - g3.transpose(2, 3, 0, 1, 4, 5)).max() < 1e-13
+    assert np.abs(g3 - g3.transpose(4, 5, 2, 3, 0, 1)).max() < 1e-13
+    # Hermiticity for a real vector
+    assert np.abs(g3 - g3.transpose(1, 0, 3, 2, 5, 4)).max() < 1e-13
+
+
+def test_rdm3_of_a_single_determinant():
+    """For one determinant Gamma3 is the antisymmetrised product of occupations:
+    sum over spin assignments of det[[d_pq, d_ps, d_pu], [d_rq, d_rs, d_ru], [d_tq, d_ts, d_tu]]
+    restricted to occupied spin orbitals; checked on its diagonal and exchange elements."""
+    n, na, nb = 4, 2, 1  # |alpha 0,1 ; beta 0>
+    v = np.zeros(6 * 4)
+    v[0] = 1.0  # alpha string {0,1} (index 0) x beta string {0} (index 0)
+    g3 = oracle.rdm3(n, na, nb, v)
+    occ = {(0, 0), (1, 0), (0, 1)}  # (orbital, spin)
+    so = sorted(occ)
+    ref = np.zeros((n,) * 6)
+    import itertools as it
+    for (p, sp_), (r, sr), (t, st) in it.product(so, repeat=3):
+        for perm, sign in (((0, 1, 2), 1), ((1, 0, 2), -1), ((0, 2, 1), -1), ((2, 1, 0), -1), ((1, 2, 0), 1), ((2, 0, 1), 1)):
+            ann = [(p, sp_), (r, sr), (t, st)]
+            a_q, a_s, a_u = ann[perm[0]], ann[perm[1]], ann[perm[2]]
+            # pair spins must match: (p,q), (r,s), (t,u)
+            if a_q[1] != sp_ or a_s[1] != sr or a_u[1] != st:
+                continue
+            if len({(p, sp_), (r, sr), (t, st)}) < 3:
+                continue
+            ref[p, a_q[0], r, a_s[0], t, a_u[0]] += sign
+    assert np.abs(g3 - ref).max() < 1e-14
+
+
 def _s2_from_rdms(g1, g2, N):
     # <S^2> = -1/2 sum_pq Gamma_pqqp + N (4 - N) / 4 for spin-free RDMs.
     return -0.5 * np.einsum("pqqp->", g2) + N * (4 - N) / 4.0
