@@ -183,6 +183,19 @@ int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const 
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
 
+/* Spin-free 3-RDM of one normalised state C (device [N_alpha][N_beta]),
+ * Sec. II.A.1, Eq. (gamma_3) summed over spin:
+ *   g3 device [n]^6, g3[p][q][r][s][t][u] = sum_{s1 s2 s3}
+ *        <C| a+_{p s1} a+_{r s2} a+_{t s3} a_{u s3} a_{s s2} a_{q s1} |C>
+ *      = <E_pq E_rs E_tu> - d_qt Gamma_purs - d_st Gamma_pqru
+ *        - d_qr (Gamma_pstu + d_st gamma_pu)
+ * (chemist order: each pair (p,q), (r,s), (t,u) shares one spin sum).
+ * FP64 in every precision mode.  Workspace 2 n^2 N_det doubles plus 64 n^4;
+ * work n^2 Gram products of n^2 x n^2 over N_det, so it is meant for the
+ * active spaces where the 3-RDM is used (n up to ~10).  Asynchronous on the
+ * context stream; FORTE_ERR_ALLOC when the workspace cannot be allocated. */
+int forte_rdm3(forte_ctx *ctx, const double *C, double *g3);
+
 /* Batched solve of nprob independent problems (many ActiveSpaceMethod instances
  * of the ActiveSpaceSolver, Sec. III): for problem i, the nroots[i] lowest
  * eigenvalues of its Hamiltonian, written to E_out[offset_i .. offset_i +

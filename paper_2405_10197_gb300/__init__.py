@@ -76,6 +76,7 @@ def library():
         "forte_set_guess": [vp, vp, i],
         "forte_rdms": [vp, vp, vp, vp],
         "forte_tdm1": [vp, vp, vp, vp],
+        "forte_rdm3": [vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
@@ -227,6 +228,11 @@ def forte_tdm1(ctx, bra, ket, t1, norb):
                                        _ptr(t1, norb * norb)))
 
 
+def forte_rdm3(ctx, C, g3, norb):
+    na, nb = forte_get_sizes(ctx)
+    return _check(library().forte_rdm3(ctx, _ptr(C, na * nb), _ptr(g3, norb ** 6)))
+
+
 def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
     """Accumulate scale * d(sum_k w_k E_k)/d(h, eri) into the device tensors dh, deri."""
     na, nb = forte_get_sizes(ctx)
@@ -359,6 +365,12 @@ class CASProblem:
         g2 = torch.empty((self.norb,) * 4, dtype=torch.float64, device=self.device)
         forte_rdms(self.ctx, C.contiguous(), g1, g2, self.norb)
         return g1, g2
+
+    def rdm3(self, C):
+        import torch
+        g3 = torch.empty((self.norb,) * 6, dtype=torch.float64, device=self.device)
+        forte_rdm3(self.ctx, C.contiguous(), g3, self.norb)
+        return g3
 
     def tdm1(self, bra, ket):
         import torch

@@ -697,6 +697,7 @@ void forte_destroy(forte_ctx *ctx) {
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
+  ctx->sc_rdm3.release();
   ctx->sc_oz.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
@@ -871,6 +872,11 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2) {
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1) {
   if (!ctx || !bra || !ket || !t1) { set_error("NULL argument"); return FORTE_ERR_ARG; }
   return rdm12_fp64(ctx, bra, ket, t1, nullptr);
+}
+
+int forte_rdm3(forte_ctx *ctx, const double *C, double *g3) {
+  if (!ctx || !C || !g3) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  return rdm3_fp64(ctx, C, g3);
 }
 
 int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale,

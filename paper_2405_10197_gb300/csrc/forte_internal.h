@@ -146,6 +146,7 @@ struct forte_ctx {
   forte::Scratch sc_rdm;           // RDM intermediates
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
+  forte::Scratch sc_rdm3;          // 3-RDM intermediates
   forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
   forte::Scratch sc_oz;            // digit bytes and scales of the tensor-core FP64-class sigma
 
@@ -235,7 +236,9 @@ int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *
 int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host);
 
 // rdm.cu
-int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2);
+int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2,
+               bool tensor_ok = true);
+int rdm3_fp64(forte_ctx *ctx, const double *C, double *g3);
 // rdm_oz.cu: 2-RDM from the 1-RDM g1 and the tensor-core Gram of the
 // symmetric / antisymmetric one-body images (reduced-precision modes, bra == ket)
 bool rdm2_oz_supported(const forte_ctx *ctx);

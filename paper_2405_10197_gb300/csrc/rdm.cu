@@ -182,6 +182,28 @@ __global__ void k_finish_g2(const double *__restrict__ part, int nsplit, int n, 
   g2[i] = v;
 }
 
+// Gamma3[p][q][r][s][t][u] for one (t,u):
+//   sum_split part[split][(q,p)][(r,s)] - d_qt G2_purs - d_st G2_pqru - d_qr (G2_pstu + d_st g1_pu)
+// where part holds <E_qp C | E_rs E_tu C> (normal ordering of E_pq E_rs E_tu, Sec. II.A.1).
+__global__ void k_finish_g3(const double *__restrict__ part, int nsplit, int n, int t, int u,
+                            const double *__restrict__ g1, const double *__restrict__ g2,
+                            double *__restrict__ g3) {
+  const int m = n * n;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m * m) return;
+  int p = i / (n * n * n), q = (i / (n * n)) % n, r = (i / n) % n, s = i % n;
+  long long idx = (long long)(q * n + p) * m + (r * n + s);
+  double v = 0.0;
+  for (int k = 0; k < nsplit; ++k) v += part[(long long)k * m * m + idx];
+  if (q == t) v -= g2[((p * n + u) * n + r) * n + s];
+  if (s == t) v -= g2[((p * n + q) * n + r) * n + u];
+  if (q == r) {
+    v -= g2[((p * n + s) * n + t) * n + u];
+    if (s == t) v -= g1[p * n + u];
+  }
+  g3[(long long)i * m + t * n + u] = v;
+}
+
 // Adjoint of the state-averaged energy E_SA = sum_k w_k E_k (Sec. II.B):
 // dh += c1 gamma^k, deri += c2 Gamma^k for one state (c1 = scale w_k, c2 = scale w_k / 2).
 __global__ void k_sa_accum(const double *__restrict__ g1, const double *__restrict__ g2, int n, double c1,
@@ -213,7 +235,7 @@ int sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double
   return FORTE_OK;
 }
 
-int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2) {
+int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2, bool tensor_ok) {
   cudaStream_t st = ctx->stream;
   const int n = ctx->n, n2 = n * n;
   const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
@@ -228,7 +250,7 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
   // 2-RDM: D for ket (and bra when different), Gram partials; the reduced-precision
   // modes take the tensor-core Gram (rdm_oz.cu) for bra == ket
   const bool same = (bra == ket);
-  const bool oz = g2 && same && ctx->precision != FORTE_FP64 && rdm2_oz_supported(ctx);
+  const bool oz = tensor_ok && g2 && same && ctx->precision != FORTE_FP64 && rdm2_oz_supported(ctx);
   const int nsplit = 64;
   size_t off_D = (base_bytes + 255) & ~(size_t)255;
   size_t sz_D = (g2 && !oz) ? sizeof(double) * (size_t)n2 * ND * (same ? 1 : 2) : 0;
@@ -314,6 +336,59 @@ int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1,
     k_finish_g2<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(G, nsplit, n, sym, g1w, g2);
   FORTE_LAUNCH_CHECK();
   }
+  return FORTE_OK;
+}
+
+// Spin-free 3-RDM of one state (Sec. II.A.1, gamma_3 summed over spin), FP64:
+//   <E_pq E_rs E_tu> = <E_qp C | E_rs F^{tu}>,  F^{tu} = E_tu C = D^{tu},
+// so for each (t,u) the one-body images of F^{tu} are built and contracted with
+// D by the Gram kernel; the lower-rank terms of the normal ordering are then
+// taken off with the FP64 1- and 2-RDMs.  Cost n^2 (build_D + n^4 ND Gram).
+int rdm3_fp64(forte_ctx *ctx, const double *C, double *g3) {
+  cudaStream_t st = ctx->stream;
+  const int n = ctx->n, n2 = n * n;
+  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
+  const int nsplit = (int)std::min<long long>(64, std::max<long long>(1, ND / 256));
+  const size_t sz_g1 = sizeof(double) * n2, sz_g2 = sizeof(double) * n2 * n2;
+  const size_t sz_D = sizeof(double) * (size_t)n2 * ND;
+  const size_t off_g2 = (sz_g1 + 255) & ~(size_t)255;
+  const size_t off_D = (off_g2 + sz_g2 + 255) & ~(size_t)255;
+  const size_t off_F = (off_D + sz_D + 255) & ~(size_t)255;
+  const size_t off_P = (off_F + sz_D + 255) & ~(size_t)255;
+  int rc = ctx->sc_rdm3.ensure(off_P + sizeof(double) * (size_t)nsplit * n2 * n2 + 256);
+  if (rc) return rc;
+  char *w = (char *)ctx->sc_rdm3.ptr;
+  double *g1 = (double *)w, *g2 = (double *)(w + off_g2);
+  double *D = (double *)(w + off_D), *F = (double *)(w + off_F), *P = (double *)(w + off_P);
+  if ((rc = rdm12_fp64(ctx, C, C, g1, g2, false))) return rc;
+  const unsigned nbD = (unsigned)std::min<long long>((ND + 255) / 256, 152LL * 32);
+  {
+    FORTE_PROF(ctx, "build_D");
+    k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, C, NA, NB, D);
+    FORTE_LAUNCH_CHECK();
+  }
+  const int ntile = (n2 + GT - 1) / GT;
+  const long long kper = (ND + nsplit - 1) / nsplit;
+  const dim3 gg(ntile * ntile, nsplit);
+  for (int t = 0; t < n; ++t)
+    for (int u = 0; u < n; ++u) {
+      {
+        FORTE_PROF(ctx, "build_D");
+        k_build_D<<<nbD, 256, 0, st>>>(ctx->sd[0].dense, ctx->sd[1].dense, n, D + (size_t)(t * n + u) * ND, NA,
+                                       NB, F);
+        FORTE_LAUNCH_CHECK();
+      }
+      {
+        FORTE_PROF(ctx, "gram");
+        k_gram<<<gg, 256, 0, st>>>(D, F, n2, ND, kper, 0, P);
+        FORTE_LAUNCH_CHECK();
+      }
+      {
+        FORTE_PROF(ctx, "finish_g3");
+        k_finish_g3<<<(n2 * n2 + 255) / 256, 256, 0, st>>>(P, nsplit, n, t, u, g1, g2, g3);
+        FORTE_LAUNCH_CHECK();
+      }
+    }
   return FORTE_OK;
 }
 
