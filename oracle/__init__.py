@@ -24,3 +24,4 @@ from .driver import (  # noqa: F401
     rdm2_elements,
     num_threads,
 )
+from .gas import gas_allowed, sigma_gas, solve_dense_gas  # noqa: F401

@@ -35,6 +35,13 @@ MUTATIONS = {
     "exchange integral added instead of subtracted":
         ("return v_so(n, eri, P, Q, R, S) - v_so(n, eri, P, Q, S, R);",
          "return v_so(n, eri, P, Q, R, S) + v_so(n, eri, P, Q, S, R);"),
+    "occupation limit taken as strict upper bound":
+        ("keep &= (tot >= gmin[g]) & (tot <= gmax[g])", "keep &= (tot >= gmin[g]) & (tot < gmax[g])", "gas.py"),
+    "space boundaries shifted by one orbital":
+        ("        orb = 0\n", "        orb = 1\n", "gas.py"),
+    "restricted sigma without the projection of the input":
+        ("Cf = np.asarray(C, dtype=np.float64).reshape(C.shape[0], -1) * keep",
+         "Cf = np.asarray(C, dtype=np.float64).reshape(C.shape[0], -1)", "gas.py"),
 }
 
 
@@ -42,12 +49,12 @@ MUTATIONS = {
 def test_pins_catch_planted_mistake(name, tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("gcc not available")
-    src = open(os.path.join(ROOT, "oracle", "oracle_core.c")).read()
-    old, new = MUTATIONS[name]
-    assert old in src, "mutation anchor no longer present in oracle_core.c"
+    old, new, fname = (MUTATIONS[name] + ("oracle_core.c",))[:3]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
+    assert old in src, f"mutation anchor no longer present in {fname}"
     shutil.copytree(os.path.join(ROOT, "oracle"), tmp_path / "oracle",
                     ignore=shutil.ignore_patterns("*.so", "__pycache__"))
-    (tmp_path / "oracle" / "oracle_core.c").write_text(src.replace(old, new))
+    (tmp_path / "oracle" / fname).write_text(src.replace(old, new))
     shutil.copy(os.path.join(ROOT, "synth_inputs.py"), tmp_path)
     os.makedirs(tmp_path / "tests")
     for f in ("conftest.py", "fock_ref.py", "test_oracle_pins.py"):

@@ -290,3 +290,99 @@ def test_davidson_finds_roots_of_both_spin_flip_sectors(n, na, nb, seed, nroots)
     w_d, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=nroots)
     w, V, rn, it = oracle.davidson(n, na, nb, h, eri, nroots=nroots, tol=1e-10)
     assert np.abs(w - w_d).max() < 1e-10
+
+
+# ---------------------------------------------------------------- occupation-restricted CI
+# (Sec. II.A.1: GAS / RAS restrictions on the per-space occupations)
+GAS_SETS = [
+    # n, na, nb, spaces, gmin, gmax
+    (6, 3, 3, (2, 2, 2), (2, 0, 0), (4, 4, 2)),       # RAS: <= 2 holes in RAS1, <= 2 particles in RAS3
+    (6, 3, 2, (1, 3, 2), (1, 1, 0), (2, 5, 1)),
+    (6, 3, 3, (3, 3), (4, 0), (6, 2)),
+    (6, 2, 3, (2, 2, 2), (0, 1, 0), (3, 3, 3)),
+]
+
+
+@pytest.mark.parametrize("n,na,nb,spaces,gmin,gmax", GAS_SETS)
+def test_gas_size_matches_occupation_counting(n, na, nb, spaces, gmin, gmax):
+    # Number of kept determinants = sum over per-space occupations (a_g, b_g)
+    # obeying the limits of prod_g C(size_g, a_g) C(size_g, b_g).
+    count = 0
+    for a in itertools.product(*[range(s + 1) for s in spaces]):
+        if sum(a) != na:
+            continue
+        for b in itertools.product(*[range(s + 1) for s in spaces]):
+            if sum(b) != nb:
+                continue
+            if all(gmin[g] <= a[g] + b[g] <= gmax[g] for g in range(len(spaces))):
+                count += math.prod(math.comb(s, x) * math.comb(s, y) for s, x, y in zip(spaces, a, b))
+    keep = oracle.gas_allowed(n, na, nb, spaces, gmin, gmax)
+    assert int(keep.sum()) == count
+
+
+@pytest.mark.parametrize("n,na,nb,spaces,gmin,gmax", GAS_SETS)
+def test_gas_eigenvalues_match_fock_space_projection(n, na, nb, spaces, gmin, gmax):
+    # Independent route: the operator-product Hamiltonian on the (na, nb) sector,
+    # restricted to the Fock states whose per-space occupation (counted from the
+    # Fock bit masks) obeys the limits.
+    idx = fock_ref.sector_states(n, na, nb)
+    H = fock_ref.sector_matrix(n, na, nb, *si.integrals(n, 2 * n, seed=n + na))
+    ok = []
+    for m in idx:
+        m = int(m)
+        occ, start = [], 0
+        for s in spaces:
+            block = ((1 << s) - 1) << start
+            occ.append(bin(m & block).count("1") + bin((m >> n) & block).count("1"))
+            start += s
+        ok.append(all(gmin[g] <= occ[g] <= gmax[g] for g in range(len(spaces))))
+    ok = np.array(ok)
+    w_op = np.linalg.eigvalsh(H[np.ix_(ok, ok)])[:4]
+    h, eri = si.integrals(n, 2 * n, seed=n + na)
+    w, V = oracle.solve_dense_gas(n, na, nb, h, eri, spaces, gmin, gmax, nroots=4)
+    assert np.abs(w - w_op).max() < 1e-11
+    # eigenvectors vanish outside the restricted space and satisfy P H P v = w v
+    keep = oracle.gas_allowed(n, na, nb, spaces, gmin, gmax).reshape(-1)
+    assert np.all(V[:, ~keep] == 0.0)
+    S = oracle.sigma_gas(n, na, nb, h, eri, V, spaces, gmin, gmax)
+    assert np.abs(S - w[:, None] * V).max() < 1e-11
+    # the same kept set from both routes; P H P C for a vector with weight everywhere
+    assert np.array_equal(ok, keep)
+    C = np.random.default_rng(5).normal(size=(1, keep.size))
+    S = oracle.sigma_gas(n, na, nb, h, eri, C, spaces, gmin, gmax)[0]
+    assert np.all(S[~keep] == 0.0)
+    assert np.abs(S[keep] - H[np.ix_(ok, ok)] @ C[0, ok]).max() < 1e-11
+
+
+def test_gas_without_restriction_is_cas():
+    n, na, nb = 6, 3, 3
+    h, eri = si.integrals(n, 12, seed=8)
+    keep = oracle.gas_allowed(n, na, nb, (2, 4), (0, 0), (4, 8))
+    assert keep.all()
+    w, _ = oracle.solve_dense_gas(n, na, nb, h, eri, (2, 4), (0, 0), (4, 8), nroots=3)
+    w0, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=3)
+    assert np.abs(w - w0).max() < 1e-12
+
+
+def test_gas_frozen_doubly_occupied_space_closed_form():
+    # A space held at full occupation is a frozen core: E = E_core + CAS on the
+    # other orbitals with h'_pq = h_pq + sum_c [2 (pq|cc) - (pc|cq)] and
+    # E_core = sum_c 2 h_cc + sum_cd [2 (cc|dd) - (cd|dc)]  (textbook closed-shell energy).
+    n, na, nb, nc = 7, 4, 3, 2
+    h, eri = si.integrals(n, 14, seed=17)
+    w, _ = oracle.solve_dense_gas(n, na, nb, h, eri, (nc, n - nc), (2 * nc, 0), (2 * nc, 2 * (n - nc)), nroots=3)
+    c, a = slice(0, nc), slice(nc, n)
+    e_core = 2 * np.trace(h[c, c]) + 2 * np.einsum("ccdd->", eri[c, c, c, c]) - np.einsum("cddc->", eri[c, c, c, c])
+    h_eff = h[a, a] + 2 * np.einsum("pqcc->pq", eri[a, a, c, c]) - np.einsum("pccq->pq", eri[a, c, c, a])
+    w_act, _ = oracle.solve_dense(n - nc, na - nc, nb - nc, h_eff, eri[a, a, a, a].copy(), nroots=3)
+    assert np.abs(w - (e_core + w_act)).max() < 1e-11
+
+
+def test_gas_empty_space_deletes_orbitals():
+    # A space held empty removes its orbitals: CAS on the others with h, eri restricted.
+    n, na, nb = 7, 3, 3
+    h, eri = si.integrals(n, 14, seed=19)
+    w, _ = oracle.solve_dense_gas(n, na, nb, h, eri, (5, 2), (0, 0), (10, 0), nroots=3)
+    k = slice(0, 5)
+    w_sub, _ = oracle.solve_dense(5, na, nb, h[k, k].copy(), eri[k, k, k, k].copy(), nroots=3)
+    assert np.abs(w - w_sub).max() < 1e-12
