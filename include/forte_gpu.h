@@ -114,8 +114,27 @@ int forte_get_sizes(const forte_ctx *ctx, long long *n_alpha_str, long long *n_b
 int forte_get_string_tables(const forte_ctx *ctx, int spin, unsigned *strings, int *J,
                             signed char *sgn);
 
-/* Determinant diagonal <I|H|I>, device output [N_alpha][N_beta]. */
+/* Determinant diagonal <I|H|I>, device output [N_alpha][N_beta]; +inf at the
+ * determinants an occupation restriction (forte_set_gas) excludes. */
 int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
+
+/* Occupation-restricted CI (GAS; RAS as its three-space case), Sec. II.A.1:
+ * the n active orbitals are split into nspace consecutive spaces of size[g]
+ * orbitals (host arrays [nspace]; sizes >= 1 adding up to n), and only the
+ * determinants with
+ *     gmin[g] <= (alpha + beta electrons in space g) <= gmax[g]   for all g
+ * are kept.  Afterwards forte_sigma returns P H P C (P the projector onto the
+ * kept determinants: entries of C outside count as zero, those of S are zero),
+ * forte_davidson solves P H P in the kept space, and stored guesses are
+ * projected.  Vectors keep the full [N_alpha][N_beta] layout, zero outside.
+ * The RDM calls act on whatever vectors they are given.  nspace = 0 removes
+ * the restriction.  ndet_out (host, may be NULL) receives the number of kept
+ * determinants.  FORTE_ERR_ARG for inconsistent sizes or limits, or when no
+ * determinant is kept (the previous restriction then stays in force).  Not
+ * applied by forte_sigma_fp64_noalloc or forte_batch_solve.  Synchronises the
+ * context stream. */
+int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const int *gmax,
+                  long long *ndet_out);
 
 /* sigma = H C (Eq. 1 applied in the determinant basis), the hot step a5 + a6.
  *   C  device [nvec][N_alpha][N_beta] FP64 input

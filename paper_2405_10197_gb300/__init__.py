@@ -77,6 +77,7 @@ def library():
         "forte_rdms": [vp, vp, vp, vp],
         "forte_tdm1": [vp, vp, vp, vp],
         "forte_rdm3": [vp, vp, vp],
+        "forte_set_gas": [vp, i, vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
@@ -233,6 +234,19 @@ def forte_rdm3(ctx, C, g3, norb):
     return _check(library().forte_rdm3(ctx, _ptr(C, na * nb), _ptr(g3, norb ** 6)))
 
 
+def forte_set_gas(ctx, spaces, gmin, gmax):
+    """Occupation restriction (GAS / RAS): consecutive spaces of the given sizes,
+    per-space limits on the alpha + beta electron count.  Empty ``spaces``
+    removes it.  Returns the number of kept determinants."""
+    G = len(spaces)
+    if len(gmin) != G or len(gmax) != G:
+        raise ValueError("spaces, gmin and gmax need the same length")
+    arr = ctypes.c_int * max(G, 1)
+    nd = ctypes.c_longlong()
+    _check(library().forte_set_gas(ctx, G, arr(*spaces), arr(*gmin), arr(*gmax), ctypes.byref(nd)))
+    return nd.value
+
+
 def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
     """Accumulate scale * d(sum_k w_k E_k)/d(h, eri) into the device tensors dh, deri."""
     na, nb = forte_get_sizes(ctx)
@@ -345,6 +359,9 @@ class CASProblem:
         S = torch.empty_like(C)
         forte_sigma(self.ctx, C, S, C.shape[0])
         return S
+
+    def set_gas(self, spaces, gmin, gmax):
+        return forte_set_gas(self.ctx, spaces, gmin, gmax)
 
     def hdiag(self):
         import torch

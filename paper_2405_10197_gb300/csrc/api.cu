@@ -96,22 +96,26 @@ void sym_eig(int k, const double *A, double *w, double *U) {
   }
 }
 
+// Under an occupation restriction the input vectors lie in the kept space and
+// the output is projected onto it (sigma = P H P C).
 static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
+  int rc;
   if (mode == FORTE_FP64) {
     ctx->n_sigma_fp64 += nvec;
-    return sigma_fp64(ctx, C, S, nvec);
-  }
-  if (mode == FORTE_DF32) {  // FP64-class: counted with the FP64 ones
+    rc = sigma_fp64(ctx, C, S, nvec);
+  } else if (mode == FORTE_DF32) {  // FP64-class: counted with the FP64 ones
     ctx->n_sigma_fp64 += nvec;
-    return sigma_df(ctx, C, S, nvec);
-  }
-  if (mode == FORTE_OZ64) {
+    rc = sigma_df(ctx, C, S, nvec);
+  } else if (mode == FORTE_OZ64) {
     ctx->n_sigma_fp64 += nvec;
-    return sigma_oz64(ctx, C, S, nvec);
+    rc = sigma_oz64(ctx, C, S, nvec);
+  } else {
+    ctx->n_sigma_mixed += nvec;
+    rc = sigma_mixed(ctx, C, S, nvec, mode);
   }
-  ctx->n_sigma_mixed += nvec;
-  return sigma_mixed(ctx, C, S, nvec, mode);
+  if (rc) return rc;
+  return gas_mask(ctx, S, nvec);
 }
 
 static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
@@ -121,7 +125,9 @@ static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, in
     return FORTE_ERR_ARG;
   }
   ctx->n_sigma_mixed += nvec;
-  return sigma_mixed(ctx, C, S, nvec, mode);
+  int rc = sigma_mixed(ctx, C, S, nvec, mode);
+  if (rc) return rc;
+  return gas_mask(ctx, S, nvec);
 }
 
 // ----------------------------------------------------------------- Davidson
@@ -234,8 +240,9 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
                         int max_iter, double *out_roots, DvResult &res) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->Ndet;
+  const long long Nsp = space_dim(ctx);  // dimension of the (possibly restricted) space
   int maxsub = std::max(ctx->dv_max_sub * nroots, nroots + 1);
-  maxsub = (int)std::min<long long>(maxsub, N);
+  maxsub = (int)std::min<long long>(maxsub, Nsp);
   maxsub = std::min(maxsub, 63);
   if (maxsub < nroots) { set_error("subspace limit below nroots"); return FORTE_ERR_ARG; }
   int keep = std::max(nroots, std::min(ctx->dv_collapse * nroots, maxsub - 1));
@@ -298,6 +305,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
           k_guess<T><<<nbk, 256, 0, st>>>(b, N, idx[c], k, 0.02);
         FORTE_LAUNCH_CHECK();
         }
+        if ((rc = gas_mask(ctx, b, 1))) return rc;
       }
       if (k > 0) {
         // orthogonalise against the supplied guesses
@@ -365,14 +373,14 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     }
     res.iters = it;
     if (bad) { set_error("non-finite residual or eigenvalue in Davidson"); return FORTE_ERR_NUMERIC; }
-    bool stop = all || it >= max_iter || k >= N;
+    bool stop = all || it >= max_iter || k >= Nsp;
     if (stop) {
       coef.assign((size_t)k * nroots, 0.0);
       for (int i = 0; i < k; ++i)
         for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
       if ((rc = ritz_out(ctx, B, k, N, d_coef, nroots, W, out_roots))) return rc;
-      res.converged = all || (k >= N);
+      res.converged = all || (k >= Nsp);
       return FORTE_OK;
     }
     int nnew_want = 0;
@@ -697,7 +705,8 @@ void forte_destroy(forte_ctx *ctx) {
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
-  ctx->sc_rdm3.release();
+  ctx->sc_rdm3.release(); ctx->sc_gas.release();
+  gas_free(ctx);
   ctx->sc_oz.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
@@ -759,6 +768,14 @@ int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec) {
   const char *c0 = (const char *)C, *c1 = c0 + sizeof(double) * ctx->Ndet * nvec;
   const char *s0 = (const char *)S, *s1 = s0 + sizeof(double) * ctx->Ndet * nvec;
   if (c0 < s1 && s0 < c1) { set_error("S overlaps C"); return FORTE_ERR_ARG; }
+  if (ctx->gas_on) {  // P H P C: the entries of C outside the kept space count as zero
+    int rc = ctx->sc_gas.ensure(sizeof(double) * ctx->Ndet * nvec + 256);
+    if (rc) return rc;
+    double *Cp = (double *)ctx->sc_gas.ptr;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(Cp, C, sizeof(double) * ctx->Ndet * nvec, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((rc = gas_mask(ctx, Cp, nvec))) return rc;
+    return sigma_dispatch(ctx, Cp, S, nvec, ctx->precision);
+  }
   return sigma_dispatch(ctx, C, S, nvec, ctx->precision);
 }
 
@@ -785,7 +802,7 @@ int forte_set_guess(forte_ctx *ctx, const double *C, int nvec) {
   FORTE_CUDA_TRY(cudaMemcpyAsync(ctx->d_guess, C, sizeof(double) * ctx->Ndet * nvec, cudaMemcpyDeviceToDevice,
                                  ctx->stream));
   ctx->nguess = nvec;
-  return FORTE_OK;
+  return gas_mask(ctx, ctx->d_guess, nvec);
 }
 
 static int ensure_roots(forte_ctx *ctx, int nroots) {
@@ -805,7 +822,7 @@ static int ensure_roots(forte_ctx *ctx, int nroots) {
 
 int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
-  if (nroots < 1 || nroots > ctx->Ndet || nroots > 31) { set_error("nroots out of range"); return FORTE_ERR_ARG; }
+  if (nroots < 1 || nroots > space_dim(ctx) || nroots > 31) { set_error("nroots out of range"); return FORTE_ERR_ARG; }
   if (!(tol > 0)) { set_error("tol must be > 0"); return FORTE_ERR_ARG; }
   clear_error();
   int rc = ensure_roots(ctx, nroots);
@@ -872,6 +889,12 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2) {
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1) {
   if (!ctx || !bra || !ket || !t1) { set_error("NULL argument"); return FORTE_ERR_ARG; }
   return rdm12_fp64(ctx, bra, ket, t1, nullptr);
+}
+
+int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const int *gmax,
+                  long long *ndet_out) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  return gas_set(ctx, nspace, size, gmin, gmax, ndet_out);
 }
 
 int forte_rdm3(forte_ctx *ctx, const double *C, double *g3) {

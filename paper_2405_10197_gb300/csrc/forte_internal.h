@@ -147,8 +147,16 @@ struct forte_ctx {
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
   forte::Scratch sc_rdm3;          // 3-RDM intermediates
+  forte::Scratch sc_gas;           // projected copy of the input of forte_sigma under a restriction
   forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
   forte::Scratch sc_oz;            // digit bytes and scales of the tensor-core FP64-class sigma
+
+  // occupation restriction (GAS / RAS): string classes per spin, allowed class pairs
+  bool gas_on = false;
+  long long gas_ndet = 0;
+  int *d_gas_cls[2] = {nullptr, nullptr};  // [N_alpha], [N_beta]
+  int gas_nc[2] = {0, 0};
+  uint8_t *d_gas_ok = nullptr;             // [gas_nc[0]][gas_nc[1]]
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -234,6 +242,13 @@ int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, 
                    long long n);
 int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out);
 int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host);
+
+// gas.cu: occupation-restricted CI (P H P on the kept determinants)
+int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const int *gmax, long long *ndet_out);
+void gas_free(forte_ctx *ctx);
+int gas_mask(forte_ctx *ctx, double *x, int nvec);  // zero the excluded entries of nvec vectors
+int gas_mask(forte_ctx *ctx, float *x, int nvec);
+long long space_dim(const forte_ctx *ctx);           // kept determinants (N_det without a restriction)
 
 // rdm.cu
 int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2,
