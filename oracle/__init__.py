@@ -25,3 +25,4 @@ from .driver import (  # noqa: F401
     num_threads,
 )
 from .gas import gas_allowed, sigma_gas, solve_dense_gas  # noqa: F401
+from .spin import sector_basis, solve_dense_spin  # noqa: F401

@@ -42,6 +42,10 @@ MUTATIONS = {
     "restricted sigma without the projection of the input":
         ("Cf = np.asarray(C, dtype=np.float64).reshape(C.shape[0], -1) * keep",
          "Cf = np.asarray(C, dtype=np.float64).reshape(C.shape[0], -1)", "gas.py"),
+    "spin sector with the opposite exchange sign":
+        ("v[j * N + i] = parity / np.sqrt(2.0)", "v[j * N + i] = -parity / np.sqrt(2.0)", "spin.py"),
+    "odd spin sector keeps the diagonal determinants":
+        ("                if parity < 0:\n                    continue\n", "", "spin.py"),
 }
 
 

@@ -386,3 +386,39 @@ def test_gas_empty_space_deletes_orbitals():
     k = slice(0, 5)
     w_sub, _ = oracle.solve_dense(5, na, nb, h[k, k].copy(), eri[k, k, k, k].copy(), nroots=3)
     assert np.abs(w - w_sub).max() < 1e-12
+
+
+# ---------------------------------------------------------------- spin parity (Ms = 0)
+# (Sec. II.A.1: projection on states of well-defined total spin)
+@pytest.mark.parametrize("n,m", [(4, 2), (5, 2), (4, 1), (5, 3)])
+def test_spin_sectors_partition_the_spectrum_by_parity_of_s(n, m):
+    # Exchange of alpha and beta strings commutes with H: the two sectors together
+    # hold every eigenvalue once, and every state of the even (odd) sector has even
+    # (odd) total spin by the spin operators of the Fock-space route.
+    h, eri = si.integrals(n, 2 * n, seed=n + 7 * m)
+    N = math.comb(n, m)
+    w_all = np.linalg.eigvalsh(fock_ref.sector_matrix(n, m, m, h, eri))
+    both = []
+    for p in (1, -1):
+        dim = N * (N + p) // 2
+        assert oracle.sector_basis(N, p).shape == (dim, N * N)
+        w, V = oracle.solve_dense_spin(n, m, h, eri, p, nroots=dim)
+        both.append(w)
+        for k in range(min(dim, 6)):
+            s2 = fock_ref.s2_expectation(n, m, m, V[k])
+            S = (math.sqrt(1.0 + 4.0 * s2) - 1.0) / 2.0
+            assert abs(S - round(S)) < 1e-9 and (-1) ** round(S) == p
+    assert np.abs(np.sort(np.concatenate(both)) - w_all).max() < 1e-11
+
+
+@pytest.mark.parametrize("t,U", [(1.0, 4.0), (0.5, 1.0)])
+def test_spin_sectors_of_the_hubbard_dimer(t, U):
+    # Two sites, one electron of each spin: the even sector holds the singlets
+    # (lowest (U - sqrt(U^2 + 16 t^2)) / 2, then U, then (U + sqrt(...)) / 2), the odd
+    # sector the Ms = 0 triplet at energy 0.
+    h, eri = si.hubbard_ring(2, t, U)
+    r = math.sqrt(U * U + 16 * t * t)
+    w, _ = oracle.solve_dense_spin(2, 1, h, eri, 1, nroots=3)
+    assert np.abs(w - np.array([(U - r) / 2, U, (U + r) / 2])).max() < 1e-14
+    w, _ = oracle.solve_dense_spin(2, 1, h, eri, -1, nroots=1)
+    assert abs(w[0]) < 1e-14
