@@ -136,6 +136,19 @@ int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
 int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const int *gmax,
                   long long *ndet_out);
 
+/* Spin-parity sector of the Davidson solve (Sec. II.A.1: projection on states
+ * of well-defined total spin), for n_alpha == n_beta (Ms = 0) only.  Exchanging
+ * the alpha and beta strings commutes with H, and with alpha creators ordered
+ * first a state of total spin S has C[I_beta][I_alpha] = (-1)^S C[I_alpha][I_beta].
+ *   parity +1: forte_davidson returns the lowest even-S roots (S = 0, 2, ...)
+ *   parity -1: the lowest odd-S roots (S = 1, 3, ...)
+ *   parity  0: no restriction (default)
+ * Guesses and every new correction vector are projected, x <- (x + parity x^T)/2,
+ * so the roots satisfy C^T = parity C exactly.  forte_sigma is not affected.
+ * Combines with forte_set_gas.  FORTE_ERR_ARG for other values or n_alpha !=
+ * n_beta.  Synchronises the context stream. */
+int forte_set_spin_parity(forte_ctx *ctx, int parity);
+
 /* sigma = H C (Eq. 1 applied in the determinant basis), the hot step a5 + a6.
  *   C  device [nvec][N_alpha][N_beta] FP64 input
  *   S  device [nvec][N_alpha][N_beta] FP64 output, overwritten (not accumulated);

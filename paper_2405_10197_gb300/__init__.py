@@ -78,6 +78,7 @@ def library():
         "forte_tdm1": [vp, vp, vp, vp],
         "forte_rdm3": [vp, vp, vp],
         "forte_set_gas": [vp, i, vp, vp, vp, vp],
+        "forte_set_spin_parity": [vp, i],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
@@ -247,6 +248,11 @@ def forte_set_gas(ctx, spaces, gmin, gmax):
     return nd.value
 
 
+def forte_set_spin_parity(ctx, parity):
+    """Davidson sector C^T = parity C for Ms = 0: +1 even S, -1 odd S, 0 off."""
+    return _check(library().forte_set_spin_parity(ctx, int(parity)))
+
+
 def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
     """Accumulate scale * d(sum_k w_k E_k)/d(h, eri) into the device tensors dh, deri."""
     na, nb = forte_get_sizes(ctx)
@@ -362,6 +368,9 @@ class CASProblem:
 
     def set_gas(self, spaces, gmin, gmax):
         return forte_set_gas(self.ctx, spaces, gmin, gmax)
+
+    def set_spin_parity(self, parity):
+        forte_set_spin_parity(self.ctx, parity)
 
     def hdiag(self):
         import torch

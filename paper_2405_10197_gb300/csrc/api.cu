@@ -294,7 +294,9 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     // unit vectors at the lowest diagonal elements not already spanned
     int need = nroots - k;
     std::vector<long long> idx(nroots + ng + 1);
-    if ((rc = vk_argmin_k(ctx, ctx->d_hdiag, N, std::min<long long>(N, need + k), idx.data()))) return rc;
+    const double *hd = ctx->d_hdiag;
+    if (ctx->spin_parity && (rc = spin_guess_diag(ctx, &hd))) return rc;  // one candidate per mirror pair
+    if ((rc = vk_argmin_k(ctx, hd, N, std::min<long long>(N, need + k), idx.data()))) return rc;
     int used = 0;
     for (size_t c = 0; c < idx.size() && used < need && c < (size_t)std::min<long long>(N, need + k); ++c) {
       T *b = B + (size_t)k * N;
@@ -306,6 +308,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
         FORTE_LAUNCH_CHECK();
         }
         if ((rc = gas_mask(ctx, b, 1))) return rc;
+        if ((rc = spin_project(ctx, b, 1))) return rc;
       }
       if (k > 0) {
         // orthogonalise against the supplied guesses
@@ -405,6 +408,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       if (k >= maxsub) break;
       T *t = Tv + (size_t)r * N;
       T *b = B + (size_t)k * N;
+      if ((rc = spin_project(ctx, t, 1))) return rc;  // the sigma rounding leaves the sector slightly
       std::vector<double> h_d(65);
       FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, b, d_d0, N))) return rc;     // copy + B^T t + |t|^2
@@ -590,6 +594,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       // append the correction: orthonormalise against V[0..k)
       double *vk = V + (size_t)k * N;
       FORTE_CUDA_TRY(cudaMemcpyAsync(vk, px, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+      if ((rc = spin_project(ctx, vk, 1))) return rc;
       FORTE_CUDA_TRY(cudaMemsetAsync(d_a, 0, sizeof(double) * 64, st));
       if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
       if ((rc = fetch(d_b, k + 1, h.data()))) return rc;
@@ -705,7 +710,7 @@ void forte_destroy(forte_ctx *ctx) {
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
-  ctx->sc_rdm3.release(); ctx->sc_gas.release();
+  ctx->sc_rdm3.release(); ctx->sc_gas.release(); ctx->sc_spin.release();
   gas_free(ctx);
   ctx->sc_oz.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -802,7 +807,9 @@ int forte_set_guess(forte_ctx *ctx, const double *C, int nvec) {
   FORTE_CUDA_TRY(cudaMemcpyAsync(ctx->d_guess, C, sizeof(double) * ctx->Ndet * nvec, cudaMemcpyDeviceToDevice,
                                  ctx->stream));
   ctx->nguess = nvec;
-  return gas_mask(ctx, ctx->d_guess, nvec);
+  int rc = gas_mask(ctx, ctx->d_guess, nvec);
+  if (rc) return rc;
+  return spin_project(ctx, ctx->d_guess, nvec);
 }
 
 static int ensure_roots(forte_ctx *ctx, int nroots) {
@@ -895,6 +902,11 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
                   long long *ndet_out) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
   return gas_set(ctx, nspace, size, gmin, gmax, ndet_out);
+}
+
+int forte_set_spin_parity(forte_ctx *ctx, int parity) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  return spin_set(ctx, parity);
 }
 
 int forte_rdm3(forte_ctx *ctx, const double *C, double *g3) {

@@ -148,6 +148,7 @@ struct forte_ctx {
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
   forte::Scratch sc_rdm3;          // 3-RDM intermediates
   forte::Scratch sc_gas;           // projected copy of the input of forte_sigma under a restriction
+  forte::Scratch sc_spin;          // guess diagonal of a spin-parity sector
   forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
   forte::Scratch sc_oz;            // digit bytes and scales of the tensor-core FP64-class sigma
 
@@ -157,6 +158,9 @@ struct forte_ctx {
   int *d_gas_cls[2] = {nullptr, nullptr};  // [N_alpha], [N_beta]
   int gas_nc[2] = {0, 0};
   uint8_t *d_gas_ok = nullptr;             // [gas_nc[0]][gas_nc[1]]
+  long long gas_ndiag = 0;                 // kept determinants with I_alpha == I_beta (n_alpha == n_beta)
+  // spin-parity sector (Ms = 0): 0 off, +1 even S, -1 odd S
+  int spin_parity = 0;
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -248,7 +252,13 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
 void gas_free(forte_ctx *ctx);
 int gas_mask(forte_ctx *ctx, double *x, int nvec);  // zero the excluded entries of nvec vectors
 int gas_mask(forte_ctx *ctx, float *x, int nvec);
-long long space_dim(const forte_ctx *ctx);           // kept determinants (N_det without a restriction)
+long long space_dim(const forte_ctx *ctx);           // dimension of the space Davidson works in
+
+// spin.cu: spin-parity sectors C^T = parity C for Ms = 0
+int spin_set(forte_ctx *ctx, int parity);
+int spin_project(forte_ctx *ctx, double *x, int nvec);  // x <- (x + parity x^T) / 2 (no-op when off)
+int spin_project(forte_ctx *ctx, float *x, int nvec);
+int spin_guess_diag(forte_ctx *ctx, const double **hd);  // diagonal that names one guess per sector pair
 
 // rdm.cu
 int rdm12_fp64(forte_ctx *ctx, const double *bra, const double *ket, double *g1, double *g2,

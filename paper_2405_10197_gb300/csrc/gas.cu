@@ -49,7 +49,13 @@ static int gas_fill(forte_ctx *ctx, T *x, int nvec, T value) {
 int gas_mask(forte_ctx *ctx, double *x, int nvec) { return gas_fill<double>(ctx, x, nvec, 0.0); }
 int gas_mask(forte_ctx *ctx, float *x, int nvec) { return gas_fill<float>(ctx, x, nvec, 0.0f); }
 
-long long space_dim(const forte_ctx *ctx) { return ctx->gas_on ? ctx->gas_ndet : ctx->Ndet; }
+long long space_dim(const forte_ctx *ctx) {
+  const long long K = ctx->gas_on ? ctx->gas_ndet : ctx->Ndet;
+  if (ctx->spin_parity == 0) return K;
+  // the kept set is symmetric under I_alpha <-> I_beta: mirror pairs plus the diagonal
+  const long long D = ctx->gas_on ? ctx->gas_ndiag : ctx->Na;
+  return (K - D) / 2 + (ctx->spin_parity > 0 ? D : 0);
+}
 
 static void gas_release(forte_ctx *ctx) {
   for (int s = 0; s < 2; ++s) {
@@ -61,6 +67,7 @@ static void gas_release(forte_ctx *ctx) {
   ctx->d_gas_ok = nullptr;
   ctx->gas_on = false;
   ctx->gas_ndet = 0;
+  ctx->gas_ndiag = 0;
 }
 
 void gas_free(forte_ctx *ctx) { gas_release(ctx); }
@@ -114,6 +121,9 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
       if (keep) ndet += cnt[0][a] * cnt[1][b];
     }
   if (nspace > 0 && ndet == 0) { set_error("the occupation restriction keeps no determinant"); return FORTE_ERR_ARG; }
+  long long ndiag = 0;  // determinants |I>|I> (same string sets only)
+  if (nspace > 0 && ctx->same_strings)
+    for (size_t i = 0; i < cls[0].size(); ++i) ndiag += ok[(size_t)cls[0][i] * ncB + cls[1][i]];
 
   FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   gas_release(ctx);
@@ -140,6 +150,7 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
   ctx->gas_nc[0] = ncA;
   ctx->gas_nc[1] = ncB;
   ctx->gas_ndet = ndet;
+  ctx->gas_ndiag = ndiag;
   ctx->gas_on = true;
   if ((rc = gas_fill<double>(ctx, ctx->d_hdiag, 1, (double)INFINITY))) return rc;
   if (ctx->nguess > 0 && (rc = gas_mask(ctx, ctx->d_guess, ctx->nguess))) return rc;
