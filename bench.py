@@ -630,6 +630,91 @@ def run_configs(args):
     return 0
 
 
+def run_extensions(args):
+    """One JSON line per extension of the path: X1 the spin-free 3-RDM (FP64 Gram
+    work 2 n^6 N_det), X2 an occupation-restricted CAS(14,14) (RAS: at most two
+    holes in the lowest four orbitals and two particles in the highest four) and
+    X3 the even-S sector of CAS(14,14), each against the unrestricted solve."""
+    import torch
+    import paper_2405_10197_gb300 as fg
+    torch.cuda.set_device(0)
+    lines = []
+
+    def ev_ms(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # X1: 3-RDM of the ground state
+    x1 = {"config": "X1 spin-free 3-RDM (FP64, every precision mode)", "cases": []}
+    for n, cfg in ((8, si.CAS88), (10, None)):
+        h, eri = si.integrals(n, 2 * n, cfg["seed"] if cfg else 10)
+        prob = fg.CASProblem(n, n // 2, n // 2, h, eri)
+        E, C, rn, it = prob.davidson(nroots=1, tol=1e-8)
+        g3 = torch.empty((n,) * 6, dtype=torch.float64, device="cuda")
+        ms = ev_ms(lambda: fg.forte_rdm3(prob.ctx, C[0], g3, n), 3)
+        flop = 2.0 * n ** 6 * prob.ndet
+        x1["cases"].append({"workload": f"CAS({n},{n})", "n_det": prob.ndet, "ms": ms,
+                            "gram_fp64_tflops": flop / (ms * 1e-3) / 1e12,
+                            "frac_of_nominal_fp64_1.25": flop / (ms * 1e-3) / 1.25e12})
+        prob.close()
+    lines.append(x1)
+
+    cfg = si.CAS1414
+    h, eri = si.integrals(14, cfg["n_l"], cfg["seed"])
+    prob = fg.CASProblem(14, 7, 7, h, eri, precision=fg.FORTE_BF16X2)
+
+    def solve(tag):
+        prob.davidson(nroots=1, tol=1e-8)  # warm-up (scratch, tables)
+        fg.forte_profile_enable(prob.ctx, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E, C, rn, it = prob.davidson(nroots=1, tol=1e-8)
+        torch.cuda.synchronize()
+        dt = 1000 * (time.perf_counter() - t0)
+        out = {"ms": dt, "iterations": int(it), "energy": float(E[0]), "residual": float(rn[0])}
+        for k in ("gas_mask", "spin_proj"):
+            nl, kms = fg.forte_profile_query(prob.ctx, k)
+            if nl:
+                out[k] = {"launches": nl, "ms": kms, "share": kms / dt}
+        fg.forte_profile_enable(prob.ctx, 0)
+        return out
+
+    C1 = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=5), device="cuda")
+    S1 = torch.empty_like(C1)
+    fg.forte_set_precision(prob.ctx, fg.FORTE_OZ64)
+    sig_full = ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), 5)
+    fg.forte_set_precision(prob.ctx, fg.FORTE_BF16X2)
+    full = solve("full")
+    # X2: RAS(2h, 2p)
+    nd = prob.set_gas((4, 6, 4), (6, 0, 0), (8, 12, 2))
+    fg.forte_set_precision(prob.ctx, fg.FORTE_OZ64)
+    sig_gas = ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), 5)
+    fg.forte_set_precision(prob.ctx, fg.FORTE_BF16X2)
+    gas = solve("gas")
+    lines.append({"config": "X2 CAS(14,14) seed 2 under RAS(2 holes in orbitals 0-3, 2 particles in 10-13), "
+                            "BF16x2 Davidson refined to 1e-8", "kept_determinants": nd, "n_det": prob.ndet,
+                  "sigma_oz64_ms": {"unrestricted": sig_full, "restricted": sig_gas},
+                  "davidson": {"unrestricted": full, "restricted": gas}})
+    prob.set_gas((), (), ())
+    # X3: even-S sector
+    prob.set_spin_parity(1)
+    even = solve("even")
+    prob.set_spin_parity(0)
+    lines.append({"config": "X3 CAS(14,14) seed 2, even-S sector vs unrestricted, BF16x2 Davidson refined to 1e-8",
+                  "davidson": {"unrestricted": full, "even_S": even}})
+    prob.close()
+    for ln in lines:
+        print(json.dumps(ln))
+    return 0
+
+
 def fg_nnz(prob):
     """Stored entries of the alpha and beta same-spin string Hamiltonians: every
     string within two replacements of a row string (itself, singles, doubles)."""
@@ -661,6 +746,8 @@ def main():
                     help="measure the other configurations (C0, C1, C3, C4, oracle) instead of the headline step")
     ap.add_argument("--configs-batch", type=int, default=128, help="instances of the batched workload for --configs")
     ap.add_argument("--fd-dirs", type=int, default=4, help="central-difference directions for the C3 gradient check")
+    ap.add_argument("--extensions", action="store_true",
+                    help="measure the 3-RDM, the occupation restriction and the spin-parity sector")
     ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
                     help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
     args = ap.parse_args()
@@ -672,6 +759,8 @@ def main():
         return run_batch(args)
     if args.configs:
         return run_configs(args)
+    if args.extensions:
+        return run_extensions(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
