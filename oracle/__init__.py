@@ -26,3 +26,4 @@ from .driver import (  # noqa: F401
 )
 from .gas import gas_allowed, sigma_gas, solve_dense_gas  # noqa: F401
 from .spin import sector_basis, solve_dense_spin  # noqa: F401
+from .aci import aci, aci_epsilon, aci_excluded, aci_reference  # noqa: F401

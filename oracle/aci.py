@@ -1,0 +1,101 @@
+"""Adaptive configuration interaction (ACI) on the determinant grid of a CAS,
+for the oracle.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Sec. II.A.2 (determinantal and selected CI): ACI looks for a model space M
+whose variational energy E_M lies within about sigma of the CASCI energy.  It
+grows a reference space P and screens the determinants mu of P's first-order
+interacting space with the energy estimate of a 2 x 2 Hamiltonian built from
+the current state Psi_P and Phi_mu:
+    [[E_P, V_mu], [V_mu, H_mumu]],  V_mu = <Phi_mu|H|Psi_P>,
+    eps_mu = lowest eigenvalue - E_P = D/2 - sqrt((D/2)^2 + V_mu^2),  D = H_mumu - E_P,
+and excludes the determinants with the smallest |eps| as long as the sum of
+the excluded |eps| stays at most sigma; the energy can be corrected by the
+sum of the excluded eps.
+
+Readings used here (the paper gives the criterion, not every step):
+* determinants are the CAS grid I_alpha x I_beta (index I_alpha * N_beta + I_beta);
+* start: P = the determinant of lowest H_II (lowest index among equals);
+* F = every determinant outside P; those not connected to P have V = 0 and
+  eps = 0, so the criterion always excludes them;
+* excluded = {mu : S(|eps_mu|) <= sigma} with S(x) = sum of |eps_nu| over
+  |eps_nu| <= x: determinants with equal |eps| leave together or not at all;
+* M = P + (F - excluded), diagonalised exactly;
+* next P = the determinants of M with the largest c^2 whose weights reach
+  1 - gamma * sigma: {mu : T(c_mu^2) >= 1 - gamma sigma} for the largest such
+  threshold, T(y) = sum of c_nu^2 over c_nu^2 >= y (ties kept together);
+* stop when P repeats (or after max_iter cycles).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .driver import _fix_sign, hmat_dense
+
+
+def aci_epsilon(E, Hmm, V):
+    """Energy estimate of the 2 x 2 problem [[E, V], [V, Hmm]] (lowest root - E)."""
+    D = 0.5 * (np.asarray(Hmm, dtype=np.float64) - E)
+    return D - np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)
+
+
+def aci_excluded(abs_eps, sigma):
+    """Boolean mask of the excluded entries: |eps| <= x* for the largest value x*
+    of abs_eps whose cumulative sum S(x*) stays at most sigma."""
+    a = np.asarray(abs_eps, dtype=np.float64)
+    vals = np.unique(a)                       # ascending distinct values
+    sums = np.array([a[a <= v].sum() for v in vals])
+    ok = vals[sums <= sigma]
+    if ok.size == 0:
+        return np.zeros(a.shape, dtype=bool)
+    return a <= ok.max()
+
+
+def aci_reference(c2, gamma_sigma):
+    """Boolean mask of the next reference space: c^2 >= y* for the largest value
+    y* of c2 whose weight T(y*) = sum(c2[c2 >= y*]) reaches 1 - gamma_sigma."""
+    c2 = np.asarray(c2, dtype=np.float64)
+    vals = np.unique(c2)[::-1]                # descending distinct values
+    target = 1.0 - gamma_sigma
+    for v in vals:
+        if c2[c2 >= v].sum() >= target:
+            return c2 >= v
+    return c2 >= vals[-1]
+
+
+def _lowest(H, idx):
+    w, U = np.linalg.eigh(H[np.ix_(idx, idx)])
+    return w[0], U[:, 0]
+
+
+def aci(norb, nalpha, nbeta, h, eri, sigma, gamma=1.0, max_iter=50):
+    """ACI on the CAS grid.  Returns dict(E=E_M, E_corrected=E_M + sum of the
+    excluded eps, M=bool mask, P=bool mask, C=Psi_M over the grid, cycles)."""
+    H = hmat_dense(norb, nalpha, nbeta, h, eri)
+    Nd = H.shape[0]
+    d = np.diag(H)
+    P = np.zeros(Nd, dtype=bool)
+    P[int(np.argmin(d))] = True
+    seen = []
+    for cycle in range(1, max_iter + 1):
+        ip = np.flatnonzero(P)
+        E_P, cp = _lowest(H, ip)
+        psi = np.zeros(Nd)
+        psi[ip] = cp
+        V = H @ psi                              # <Phi_mu|H|Psi_P> for every mu
+        eps = aci_epsilon(E_P, d, V)
+        eps[P] = 0.0
+        excl = aci_excluded(np.where(P, np.inf, np.abs(eps)), sigma) & ~P
+        M = ~excl
+        im = np.flatnonzero(M)
+        E_M, cm = _lowest(H, im)
+        C = np.zeros(Nd)
+        C[im] = cm
+        C = _fix_sign(C)
+        newP = aci_reference(np.where(M, C * C, 0.0), gamma * sigma) & M
+        key = newP.tobytes()
+        if key in seen or cycle == max_iter:
+            return dict(E=E_M, E_corrected=E_M + eps[excl].sum(), M=M, P=newP, C=C, cycles=cycle)
+        seen.append(key)
+        P = newP

@@ -571,6 +571,9 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       const int max_inner = 25;
       for (int it = 0; it < max_inner; ++it) {
         if ((rc = sigma_dispatch(ctx, pp, pq, 1, inner_mode))) return rc;
+        // in a spin-parity sector, drop the other sector's part of the reduced-precision
+        // error: states there may lie below theta, where H - theta is not positive
+        if ((rc = spin_project(ctx, pq, 1))) return rc;
         if ((rc = vk_axpby(ctx, -theta, pp, 1.0, pq, N))) return rc;
         if ((rc = project(pq, nroots))) return rc;
         if ((rc = vk_multidot(ctx, pp, 1, N, pq, N, d_s))) return rc;

@@ -46,6 +46,13 @@ MUTATIONS = {
         ("v[j * N + i] = parity / np.sqrt(2.0)", "v[j * N + i] = -parity / np.sqrt(2.0)", "spin.py"),
     "odd spin sector keeps the diagonal determinants":
         ("                if parity < 0:\n                    continue\n", "", "spin.py"),
+    "2x2 estimate takes the upper root":
+        ("return D - np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)",
+         "return D + np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)", "aci.py"),
+    "2x2 estimate without the half of the diagonal gap":
+        ("D = 0.5 * (np.asarray(Hmm, dtype=np.float64) - E)", "D = (np.asarray(Hmm, dtype=np.float64) - E)", "aci.py"),
+    "model space without the reference determinants":
+        ("        M = ~excl\n", "        M = ~excl & ~P\n", "aci.py"),
 }
 
 

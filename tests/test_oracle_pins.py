@@ -422,3 +422,60 @@ def test_spin_sectors_of_the_hubbard_dimer(t, U):
     assert np.abs(w - np.array([(U - r) / 2, U, (U + r) / 2])).max() < 1e-14
     w, _ = oracle.solve_dense_spin(2, 1, h, eri, -1, nroots=1)
     assert abs(w[0]) < 1e-14
+
+
+# ---------------------------------------------------------------- adaptive CI
+# (Sec. II.A.2: 2 x 2 energy estimates, exclusion of determinants whose summed
+# estimates stay below sigma, |E_M - E_CASCI| ~ sigma)
+def test_aci_epsilon_is_the_lowest_root_of_the_2x2_problem():
+    rng = np.random.default_rng(3)
+    E = -5.0
+    Hmm = E + rng.uniform(-1.0, 4.0, size=200)
+    V = rng.normal(0.0, 0.3, size=200)
+    V[:10] = 0.0
+    eps = oracle.aci_epsilon(E, Hmm, V)
+    ref = [np.linalg.eigvalsh(np.array([[E, v], [v, hm]]))[0] - E for hm, v in zip(Hmm, V)]
+    assert np.abs(eps - np.array(ref)).max() < 1e-13
+
+
+def test_aci_selection_rules_match_sorted_prefixes():
+    rng = np.random.default_rng(9)
+    a = rng.exponential(1e-4, size=500)
+    for sigma in (0.0, 1e-4, 3e-3, 1.0):
+        excl = oracle.aci_excluded(a, sigma)
+        order = np.argsort(a)
+        k = int(np.sum(np.cumsum(a[order]) <= sigma))
+        assert set(np.flatnonzero(excl)) == set(order[:k].tolist())
+    # equal values leave together or not at all
+    b = np.array([1.0, 1.0, 1.0, 5.0])
+    assert oracle.aci_excluded(b, 2.5).sum() == 0 and oracle.aci_excluded(b, 3.0).sum() == 3
+    c2 = rng.dirichlet(np.ones(300))
+    for gs in (0.5, 1e-2, 1e-4):
+        keep = oracle.aci_reference(c2, gs)
+        order = np.argsort(-c2)
+        k = int(np.searchsorted(np.cumsum(c2[order]), 1.0 - gs) + 1)
+        assert set(np.flatnonzero(keep)) == set(order[:k].tolist())
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(6, 3, 3, 1), (7, 3, 2, 5)])
+def test_aci_zero_threshold_reaches_casci(n, na, nb, seed):
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    w, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=1)
+    r = oracle.aci(n, na, nb, h, eri, 0.0)
+    assert abs(r["E"] - w[0]) < 1e-10
+
+
+@pytest.mark.parametrize("sigma", [1e-2, 1e-3, 1e-4])
+def test_aci_energy_error_tracks_sigma(sigma):
+    # Variational in M and within a few sigma of CASCI; E_M is the lowest root of
+    # the operator-product Hamiltonian restricted to M (independent route).
+    n, na, nb = 6, 3, 3
+    h, eri = si.integrals(n, 12, seed=1)
+    w, _ = oracle.solve_dense(n, na, nb, h, eri, nroots=1)
+    r = oracle.aci(n, na, nb, h, eri, sigma)
+    assert 0.0 <= r["E"] - w[0] <= 3.0 * sigma
+    assert abs(r["E_corrected"] - w[0]) < abs(r["E"] - w[0])
+    H = fock_ref.sector_matrix(n, na, nb, h, eri)
+    M = r["M"]
+    assert abs(np.linalg.eigvalsh(H[np.ix_(M, M)])[0] - r["E"]) < 1e-11
+    assert np.all(r["C"][~M] == 0.0) and np.all(r["P"] <= M)
