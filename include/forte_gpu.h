@@ -149,6 +149,32 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
  * n_beta.  Synchronises the context stream. */
 int forte_set_spin_parity(forte_ctx *ctx, int parity);
 
+/* Adaptive configuration interaction (ACI, Sec. II.A.2) on the determinant grid
+ * of this CAS, ground state.  Starting from the determinant of lowest H_II as
+ * the reference space P, each cycle
+ *   - solves H in P (Davidson to `tol`) for Psi_P, E_P;
+ *   - forms V = H Psi_P over the whole grid (one FP64-class sigma) and the 2 x 2
+ *     estimates eps_mu = D - sqrt(D^2 + V_mu^2), D = (H_mumu - E_P) / 2, for
+ *     every determinant outside P;
+ *   - excludes the determinants with the smallest |eps| while their summed
+ *     |eps| stays at most `sigma` (determinants with equal |eps| leave together);
+ *   - solves H in the model space M (every determinant not excluded);
+ *   - takes as the next P the determinants of M with the largest c^2 whose
+ *     summed c^2 reaches 1 - gamma * sigma (equal values stay together);
+ * and stops when P repeats or after max_cycles cycles.  For n_alpha == n_beta
+ * the alpha <-> beta mirror determinants have equal estimates and weights in
+ * exact arithmetic: both take the larger computed value, and the start P is
+ * the lowest determinant with its mirror.
+ * Outputs: E_out host [2] = {E_M, E_M + sum of the excluded eps}; C_out device
+ * [N_alpha][N_beta] or NULL (Psi_M, zero outside M); nM_out, nP_out, cycles_out
+ * host or NULL.  The Davidson solves use the context's precision mode; the
+ * screening sigma is FP64-class.  The determinant grid is the CAS itself
+ * (n <= 16); sigma and the P/M masks cost one grid sweep per Davidson step.
+ * FORTE_ERR_ARG for sigma < 0, gamma < 0, max_cycles < 1, tol <= 0, or an
+ * active forte_set_gas / spin parity.  Synchronises the context stream. */
+int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out,
+              double *C_out, long long *nM_out, long long *nP_out, int *cycles_out);
+
 /* sigma = H C (Eq. 1 applied in the determinant basis), the hot step a5 + a6.
  *   C  device [nvec][N_alpha][N_beta] FP64 input
  *   S  device [nvec][N_alpha][N_beta] FP64 output, overwritten (not accumulated);

@@ -25,7 +25,12 @@ Readings used here (the paper gives the criterion, not every step):
 * next P = the determinants of M with the largest c^2 whose weights reach
   1 - gamma * sigma: {mu : T(c_mu^2) >= 1 - gamma sigma} for the largest such
   threshold, T(y) = sum of c_nu^2 over c_nu^2 >= y (ties kept together);
-* stop when P repeats (or after max_iter cycles).
+* stop when P repeats (or after max_iter cycles);
+* for n_alpha = n_beta the exchange of alpha and beta strings commutes with H,
+  so mirror determinants (I_a, I_b) and (I_b, I_a) have equal |eps| and c^2 in
+  exact arithmetic; both are set to the larger of the two computed values (so
+  that rounding cannot split a mirror pair at a threshold), and the start P
+  holds the lowest determinant together with its mirror.
 """
 from __future__ import annotations
 
@@ -64,6 +69,15 @@ def aci_reference(c2, gamma_sigma):
     return c2 >= vals[-1]
 
 
+def _mirror_max(x, nalpha, nbeta):
+    """max(x[Ia, Ib], x[Ib, Ia]) for n_alpha = n_beta (x over the grid); x itself otherwise."""
+    if nalpha != nbeta:
+        return x
+    N = int(round(np.sqrt(x.size)))
+    X = x.reshape(N, N)
+    return np.maximum(X, X.T).reshape(-1)
+
+
 def _lowest(H, idx):
     w, U = np.linalg.eigh(H[np.ix_(idx, idx)])
     return w[0], U[:, 0]
@@ -77,6 +91,7 @@ def aci(norb, nalpha, nbeta, h, eri, sigma, gamma=1.0, max_iter=50):
     d = np.diag(H)
     P = np.zeros(Nd, dtype=bool)
     P[int(np.argmin(d))] = True
+    P = _mirror_max(P.astype(np.float64), nalpha, nbeta) > 0
     seen = []
     for cycle in range(1, max_iter + 1):
         ip = np.flatnonzero(P)
@@ -86,14 +101,14 @@ def aci(norb, nalpha, nbeta, h, eri, sigma, gamma=1.0, max_iter=50):
         V = H @ psi                              # <Phi_mu|H|Psi_P> for every mu
         eps = aci_epsilon(E_P, d, V)
         eps[P] = 0.0
-        excl = aci_excluded(np.where(P, np.inf, np.abs(eps)), sigma) & ~P
+        excl = aci_excluded(_mirror_max(np.where(P, np.inf, np.abs(eps)), nalpha, nbeta), sigma) & ~P
         M = ~excl
         im = np.flatnonzero(M)
         E_M, cm = _lowest(H, im)
         C = np.zeros(Nd)
         C[im] = cm
         C = _fix_sign(C)
-        newP = aci_reference(np.where(M, C * C, 0.0), gamma * sigma) & M
+        newP = aci_reference(_mirror_max(np.where(M, C * C, 0.0), nalpha, nbeta), gamma * sigma) & M
         key = newP.tobytes()
         if key in seen or cycle == max_iter:
             return dict(E=E_M, E_corrected=E_M + eps[excl].sum(), M=M, P=newP, C=C, cycles=cycle)

@@ -96,6 +96,12 @@ void sym_eig(int k, const double *A, double *w, double *U) {
   }
 }
 
+// sigma over the whole determinant grid (no restriction applied), FP64-class mode
+int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec) {
+  if (ctx->precision == FORTE_FP64) return sigma_fp64(ctx, C, S, nvec);
+  return oz_ab_supported(ctx) ? sigma_oz64(ctx, C, S, nvec) : sigma_df(ctx, C, S, nvec);
+}
+
 // Under an occupation restriction the input vectors lie in the kept space and
 // the output is projected onto it (sigma = P H P C).
 static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
@@ -713,7 +719,7 @@ void forte_destroy(forte_ctx *ctx) {
   }
   ctx->sc_t1.release(); ctx->sc_t2.release(); ctx->sc_dv.release();
   ctx->sc_small.release(); ctx->sc_rdm.release(); ctx->sc_mixed.release(); ctx->sc_grad.release(); ctx->sc_df.release();
-  ctx->sc_rdm3.release(); ctx->sc_gas.release(); ctx->sc_spin.release();
+  ctx->sc_rdm3.release(); ctx->sc_gas.release(); ctx->sc_spin.release(); ctx->sc_aci.release();
   gas_free(ctx);
   ctx->sc_oz.release();
   for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -905,6 +911,20 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
                   long long *ndet_out) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
   return gas_set(ctx, nspace, size, gmin, gmax, ndet_out);
+}
+
+int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out,
+              double *C_out, long long *nM_out, long long *nP_out, int *cycles_out) {
+  if (!ctx || !E_out) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  if (!(sigma >= 0) || !isfinite(sigma) || !(gamma >= 0) || !isfinite(gamma) || max_cycles < 1 || !(tol > 0)) {
+    set_error("invalid adaptive CI parameters");
+    return FORTE_ERR_ARG;
+  }
+  if (ctx->gas_on || ctx->spin_parity) {
+    set_error("adaptive CI runs on the unrestricted determinant grid (no forte_set_gas / spin parity)");
+    return FORTE_ERR_ARG;
+  }
+  return aci_run(ctx, sigma, gamma, max_cycles, tol, E_out, C_out, nM_out, nP_out, cycles_out);
 }
 
 int forte_set_spin_parity(forte_ctx *ctx, int parity) {

@@ -149,6 +149,7 @@ struct forte_ctx {
   forte::Scratch sc_rdm3;          // 3-RDM intermediates
   forte::Scratch sc_gas;           // projected copy of the input of forte_sigma under a restriction
   forte::Scratch sc_spin;          // guess diagonal of a spin-parity sector
+  forte::Scratch sc_aci;           // adaptive CI: masks, estimates, pristine diagonal, histograms
   forte::Scratch sc_df;            // (hi, lo) copy of the input of the double-FP32 sigma
   forte::Scratch sc_oz;            // digit bytes and scales of the tensor-core FP64-class sigma
 
@@ -161,6 +162,10 @@ struct forte_ctx {
   long long gas_ndiag = 0;                 // kept determinants with I_alpha == I_beta (n_alpha == n_beta)
   // spin-parity sector (Ms = 0): 0 off, +1 even S, -1 odd S
   int spin_parity = 0;
+  // arbitrary determinant mask [Ndet] (the P and M spaces of adaptive CI)
+  bool detmask_on = false;
+  long long detmask_n = 0;
+  uint8_t *d_detmask = nullptr;
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
   bool prof_on = false;
@@ -253,6 +258,12 @@ void gas_free(forte_ctx *ctx);
 int gas_mask(forte_ctx *ctx, double *x, int nvec);  // zero the excluded entries of nvec vectors
 int gas_mask(forte_ctx *ctx, float *x, int nvec);
 long long space_dim(const forte_ctx *ctx);           // dimension of the space Davidson works in
+int det_mask_fill(forte_ctx *ctx, double *x, int nvec, double value);  // value at the masked-out entries
+int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec);  // api.cu: unrestricted FP64-class sigma
+
+// aci.cu: adaptive CI on the determinant grid
+int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out, double *C_out,
+            long long *nM_out, long long *nP_out, int *cycles_out);
 
 // spin.cu: spin-parity sectors C^T = parity C for Ms = 0
 int spin_set(forte_ctx *ctx, int parity);

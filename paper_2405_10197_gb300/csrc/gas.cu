@@ -33,9 +33,26 @@ __global__ void k_gas_fill(T *__restrict__ x, long long rows, long long NA, long
   }
 }
 
+// x[v][i] = value wherever mask[i] == 0 (an arbitrary determinant mask).
+template <typename T>
+__global__ void k_det_fill(T *__restrict__ x, long long total, long long nd, const uint8_t *__restrict__ mask,
+                           T value) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!mask[i % nd]) x[i] = value;
+}
+
 template <typename T>
 static int gas_fill(forte_ctx *ctx, T *x, int nvec, T value) {
-  if (!ctx->gas_on || nvec <= 0) return FORTE_OK;
+  if (nvec <= 0) return FORTE_OK;
+  if (ctx->detmask_on) {
+    const long long total = (long long)nvec * ctx->Ndet;
+    const unsigned nb = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
+    FORTE_PROF(ctx, "det_mask");
+    k_det_fill<T><<<nb, 256, 0, ctx->stream>>>(x, total, ctx->Ndet, ctx->d_detmask, value);
+    FORTE_LAUNCH_CHECK();
+  }
+  if (!ctx->gas_on) return FORTE_OK;
   const long long rows = (long long)nvec * ctx->Na;
   const unsigned nb = (unsigned)std::min<long long>(rows, 152LL * 16);
   const int nt = ctx->Nb >= 256 ? 256 : (ctx->Nb >= 64 ? 64 : 32);
@@ -49,7 +66,10 @@ static int gas_fill(forte_ctx *ctx, T *x, int nvec, T value) {
 int gas_mask(forte_ctx *ctx, double *x, int nvec) { return gas_fill<double>(ctx, x, nvec, 0.0); }
 int gas_mask(forte_ctx *ctx, float *x, int nvec) { return gas_fill<float>(ctx, x, nvec, 0.0f); }
 
+int det_mask_fill(forte_ctx *ctx, double *x, int nvec, double value) { return gas_fill<double>(ctx, x, nvec, value); }
+
 long long space_dim(const forte_ctx *ctx) {
+  if (ctx->detmask_on) return ctx->detmask_n;  // (used alone: no restriction or sector besides it)
   const long long K = ctx->gas_on ? ctx->gas_ndet : ctx->Ndet;
   if (ctx->spin_parity == 0) return K;
   // the kept set is symmetric under I_alpha <-> I_beta: mirror pairs plus the diagonal
