@@ -479,3 +479,16 @@ def test_aci_energy_error_tracks_sigma(sigma):
     M = r["M"]
     assert abs(np.linalg.eigvalsh(H[np.ix_(M, M)])[0] - r["E"]) < 1e-11
     assert np.all(r["C"][~M] == 0.0) and np.all(r["P"] <= M)
+
+
+def test_aci_spaces_are_mirror_symmetric_for_equal_spin_counts():
+    # n_alpha = n_beta: H commutes with the alpha <-> beta exchange, so the model and
+    # reference spaces are closed under it (mirror determinants share estimates).
+    n, na, nb = 6, 3, 3
+    h, eri = si.integrals(n, 12, seed=1)
+    N = math.comb(n, na)
+    for sigma in (1e-2, 1e-3):
+        r = oracle.aci(n, na, nb, h, eri, sigma)
+        for key in ("M", "P"):
+            X = r[key].reshape(N, N)
+            assert np.array_equal(X, X.T)
