@@ -30,13 +30,18 @@ Readings used here (the paper gives the criterion, not every step):
   so mirror determinants (I_a, I_b) and (I_b, I_a) have equal |eps| and c^2 in
   exact arithmetic; both are set to the larger of the two computed values (so
   that rounding cannot split a mirror pair at a threshold), and the start P
-  holds the lowest determinant together with its mirror.
+  holds the lowest determinant together with its mirror;
+* optional exchange-parity sector (n_alpha = n_beta, parity +1: even S, -1:
+  odd S): the P and M solves take the lowest state with C^T = parity C, and the
+  start P is the lowest determinant that can carry weight there (for parity -1
+  one with I_a != I_b) with its mirror.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .driver import _fix_sign, hmat_dense
+from .spin import sector_basis
 
 
 def aci_epsilon(E, Hmm, V):
@@ -83,30 +88,46 @@ def _lowest(H, idx):
     return w[0], U[:, 0]
 
 
-def aci(norb, nalpha, nbeta, h, eri, sigma, gamma=1.0, max_iter=50):
+def _lowest_grid(H, mask, parity):
+    """Lowest eigenpair of H restricted to the determinants in `mask` (and to the
+    exchange-parity sector when parity != 0); the vector over the whole grid."""
+    Nd = H.shape[0]
+    if parity == 0:
+        idx = np.flatnonzero(mask)
+        E, c = _lowest(H, idx)
+        v = np.zeros(Nd)
+        v[idx] = c
+        return E, v
+    N = int(round(np.sqrt(Nd)))
+    Q = sector_basis(N, parity, mask.reshape(N, N))
+    w, U = np.linalg.eigh(Q @ H @ Q.T)
+    return w[0], U[:, 0] @ Q
+
+
+def aci(norb, nalpha, nbeta, h, eri, sigma, gamma=1.0, max_iter=50, parity=0):
     """ACI on the CAS grid.  Returns dict(E=E_M, E_corrected=E_M + sum of the
     excluded eps, M=bool mask, P=bool mask, C=Psi_M over the grid, cycles)."""
+    if parity and nalpha != nbeta:
+        raise ValueError("an exchange-parity sector needs n_alpha == n_beta")
     H = hmat_dense(norb, nalpha, nbeta, h, eri)
     Nd = H.shape[0]
     d = np.diag(H)
     P = np.zeros(Nd, dtype=bool)
-    P[int(np.argmin(d))] = True
+    start = d.copy()
+    if parity < 0:  # determinants |I>|I> carry no weight in the odd sector
+        N = int(round(np.sqrt(Nd)))
+        start[np.arange(N) * (N + 1)] = np.inf
+    P[int(np.argmin(start))] = True
     P = _mirror_max(P.astype(np.float64), nalpha, nbeta) > 0
     seen = []
     for cycle in range(1, max_iter + 1):
-        ip = np.flatnonzero(P)
-        E_P, cp = _lowest(H, ip)
-        psi = np.zeros(Nd)
-        psi[ip] = cp
+        E_P, psi = _lowest_grid(H, P, parity)
         V = H @ psi                              # <Phi_mu|H|Psi_P> for every mu
         eps = aci_epsilon(E_P, d, V)
         eps[P] = 0.0
         excl = aci_excluded(_mirror_max(np.where(P, np.inf, np.abs(eps)), nalpha, nbeta), sigma) & ~P
         M = ~excl
-        im = np.flatnonzero(M)
-        E_M, cm = _lowest(H, im)
-        C = np.zeros(Nd)
-        C[im] = cm
+        E_M, C = _lowest_grid(H, M, parity)
         C = _fix_sign(C)
         newP = aci_reference(_mirror_max(np.where(M, C * C, 0.0), nalpha, nbeta), gamma * sigma) & M
         key = newP.tobytes()

@@ -492,3 +492,19 @@ def test_aci_spaces_are_mirror_symmetric_for_equal_spin_counts():
         for key in ("M", "P"):
             X = r[key].reshape(N, N)
             assert np.array_equal(X, X.T)
+
+
+@pytest.mark.parametrize("parity", [1, -1])
+def test_aci_in_a_parity_sector_reaches_the_sector_casci(parity):
+    # sigma = 0 in the even (odd) sector ends at the lowest even-S (odd-S) root, and the
+    # vector has the sector's exchange symmetry.
+    n, m = 6, 3
+    h, eri = si.integrals(n, 12, seed=1)
+    w, _ = oracle.solve_dense_spin(n, m, h, eri, parity, nroots=1)
+    r = oracle.aci(n, m, m, h, eri, 0.0, parity=parity)
+    assert abs(r["E"] - w[0]) < 1e-10
+    N = math.comb(n, m)
+    C = r["C"].reshape(N, N)
+    assert np.abs(C - parity * C.T).max() < 1e-12
+    r = oracle.aci(n, m, m, h, eri, 1e-3, parity=parity)
+    assert 0.0 <= r["E"] - w[0] <= 3e-3
