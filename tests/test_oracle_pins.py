@@ -508,3 +508,21 @@ def test_aci_in_a_parity_sector_reaches_the_sector_casci(parity):
     assert np.abs(C - parity * C.T).max() < 1e-12
     r = oracle.aci(n, m, m, h, eri, 1e-3, parity=parity)
     assert 0.0 <= r["E"] - w[0] <= 3e-3
+
+
+def test_spin_sectors_partition_an_occupation_restricted_spectrum():
+    # The restriction acts on alpha + beta counts, so the kept set is closed under the
+    # exchange; the two sectors over it hold the restricted spectrum exactly once.
+    n, m = 6, 3
+    spaces, gmin, gmax = (2, 2, 2), (2, 0, 0), (4, 4, 2)
+    h, eri = si.integrals(n, 12, seed=6)
+    keep = oracle.gas_allowed(n, m, m, spaces, gmin, gmax)
+    assert np.array_equal(keep, keep.T)
+    nd = int(keep.sum())
+    w_all, _ = oracle.solve_dense_gas(n, m, m, h, eri, spaces, gmin, gmax, nroots=nd)
+    both = []
+    for p in (1, -1):
+        dim = oracle.sector_basis(keep.shape[0], p, keep).shape[0]
+        w, _ = oracle.solve_dense_spin(n, m, h, eri, p, nroots=dim, keep=keep)
+        both.append(w)
+    assert np.abs(np.sort(np.concatenate(both)) - w_all).max() < 1e-11
