@@ -164,15 +164,19 @@ int forte_set_spin_parity(forte_ctx *ctx, int parity);
  * and stops when P repeats or after max_cycles cycles.  For n_alpha == n_beta
  * the alpha <-> beta mirror determinants have equal estimates and weights in
  * exact arithmetic: both take the larger computed value, and the start P is
- * the lowest determinant with its mirror.
+ * the lowest determinant with its mirror.  parity (+1 even S, -1 odd S, 0 none;
+ * n_alpha == n_beta only) holds the P and M solves to the exchange-parity
+ * sector C^T = parity C of the target state; the start determinant is then the
+ * lowest one that can carry weight there (I_alpha != I_beta for -1).
  * Outputs: E_out host [2] = {E_M, E_M + sum of the excluded eps}; C_out device
  * [N_alpha][N_beta] or NULL (Psi_M, zero outside M); nM_out, nP_out, cycles_out
  * host or NULL.  The Davidson solves use the context's precision mode; the
  * screening sigma is FP64-class.  The determinant grid is the CAS itself
  * (n <= 16); sigma and the P/M masks cost one grid sweep per Davidson step.
- * FORTE_ERR_ARG for sigma < 0, gamma < 0, max_cycles < 1, tol <= 0, or an
- * active forte_set_gas / spin parity.  Synchronises the context stream. */
-int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out,
+ * FORTE_ERR_ARG for sigma < 0, gamma < 0, max_cycles < 1, tol <= 0, a parity
+ * other than -1/0/+1 or with n_alpha != n_beta, or an active forte_set_gas /
+ * forte_set_spin_parity.  Synchronises the context stream. */
+int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
               double *C_out, long long *nM_out, long long *nP_out, int *cycles_out);
 
 /* sigma = H C (Eq. 1 applied in the determinant basis), the hot step a5 + a6.

@@ -79,7 +79,7 @@ def library():
         "forte_rdm3": [vp, vp, vp],
         "forte_set_gas": [vp, i, vp, vp, vp, vp],
         "forte_set_spin_parity": [vp, i],
-        "forte_aci": [vp, d, d, i, d, vp, vp, vp, vp, vp],
+        "forte_aci": [vp, d, d, i, d, i, vp, vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
@@ -254,13 +254,14 @@ def forte_set_spin_parity(ctx, parity):
     return _check(library().forte_set_spin_parity(ctx, int(parity)))
 
 
-def forte_aci(ctx, sigma, gamma=1.0, max_cycles=50, tol=1e-10, C=None):
+def forte_aci(ctx, sigma, gamma=1.0, max_cycles=50, tol=1e-10, C=None, parity=0):
     """Adaptive CI on the CAS grid: returns (E_M, E_corrected, nM, nP, cycles);
-    Psi_M goes into the device tensor C when given."""
+    Psi_M goes into the device tensor C when given.  parity: exchange-parity
+    sector of the target (+1 even S, -1 odd S, 0 none)."""
     na, nb = forte_get_sizes(ctx)
     E = (ctypes.c_double * 2)()
     nM, nP, cyc = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
-    _check(library().forte_aci(ctx, float(sigma), float(gamma), int(max_cycles), float(tol), E,
+    _check(library().forte_aci(ctx, float(sigma), float(gamma), int(max_cycles), float(tol), int(parity), E,
                                _ptr(C, na * nb) if C is not None else None, ctypes.byref(nM), ctypes.byref(nP),
                                ctypes.byref(cyc)))
     return E[0], E[1], nM.value, nP.value, cyc.value
@@ -385,11 +386,11 @@ class CASProblem:
     def set_spin_parity(self, parity):
         forte_set_spin_parity(self.ctx, parity)
 
-    def aci(self, sigma, gamma=1.0, max_cycles=50, tol=1e-10):
+    def aci(self, sigma, gamma=1.0, max_cycles=50, tol=1e-10, parity=0):
         """(E_M, E_corrected, Psi_M [N_alpha][N_beta], nM, nP, cycles)."""
         import torch
         C = torch.empty(self.na, self.nb, dtype=torch.float64, device=self.device)
-        e, ec, nm, np_, cyc = forte_aci(self.ctx, sigma, gamma, max_cycles, tol, C)
+        e, ec, nm, np_, cyc = forte_aci(self.ctx, sigma, gamma, max_cycles, tol, C, parity)
         return e, ec, C, nm, np_, cyc
 
     def hdiag(self):

@@ -11,7 +11,9 @@
 //   5. Psi_M, E_M: Davidson in M = all determinants not excluded;
 //   6. next P: the largest-c^2 determinants of M whose weights reach
 //      1 - gamma sigma (equal values stay together).
-// Stops when P repeats.  For n_alpha = n_beta the alpha <-> beta exchange
+// Stops when P repeats.  With a parity sector (n_alpha = n_beta) the P and M
+// solves keep C^T = parity C, which picks the target spin parity and makes Psi_P
+// unique where the two sectors' lowest states are (nearly) degenerate.  For n_alpha = n_beta the alpha <-> beta exchange
 // commutes with H: mirror determinants carry equal |eps| and c^2 in exact
 // arithmetic, so both take the larger computed value (rounding must not split
 // a mirror pair at a threshold), and the start P is the lowest determinant with
@@ -66,26 +68,39 @@ __global__ void k_aci_hist(const double *__restrict__ a, long long N, int shift,
     }
 }
 
-// maskM[i] = key(a[i]) >= kM; counts and sums the excluded eps
-__global__ void k_aci_mask_m(const double *__restrict__ a, const double *__restrict__ eps, long long N,
+// maskM[i] = key(a[i]) >= kM; counts the kept entries (and those with I_a == I_b
+// when N1 > 0, the side of a square grid) and sums the excluded eps
+__global__ void k_aci_mask_m(const double *__restrict__ a, const double *__restrict__ eps, long long N, long long N1,
                              unsigned long long kM, uint8_t *__restrict__ maskM, unsigned long long *__restrict__ nM,
                              double *__restrict__ eps_excl) {
-  unsigned long long c = 0;
+  unsigned long long c = 0, cd = 0;
   double s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const bool keep = (unsigned long long)__double_as_longlong(a[i]) >= kM;
     maskM[i] = keep;
-    if (keep) ++c;
-    else s += eps[i];
+    if (keep) {
+      ++c;
+      if (N1 > 0 && i / N1 == i % N1) ++cd;
+    } else {
+      s += eps[i];
+    }
   }
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
+    cd += __shfl_xor_sync(0xffffffffu, cd, o);
     s += __shfl_xor_sync(0xffffffffu, s, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(nM, c);
+    atomicAdd(nM + 2, cd);
     atomicAdd(eps_excl, s);
   }
+}
+
+// x[i][i] = v on a square grid of side N1
+__global__ void k_aci_diag_fill(double *__restrict__ x, long long N1, double v) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N1; i += (long long)gridDim.x * blockDim.x)
+    x[i * N1 + i] = v;
 }
 
 // y[ia][ib] = max(x[ia][ib], x[ib][ia]) on a square grid
@@ -119,26 +134,30 @@ __global__ void k_aci_pert(double *__restrict__ x, long long N, unsigned long lo
     x[i] = (double)(aci_mix((unsigned long long)i + key) >> 11) * 0x1.0p-53 - 0.5;
 }
 
-// maskP[i] = maskM[i] && (all || key(c2[i]) >= kP); count and an order-free hash of the set
+// maskP[i] = maskM[i] && (all || key(c2[i]) >= kP); count, an order-free hash of
+// the set and (N1 > 0) the count of entries with I_a == I_b; nP[0..2] = count, hash, diagonal
 __global__ void k_aci_mask_p(const double *__restrict__ c2, const uint8_t *__restrict__ maskM, long long N,
-                             unsigned long long kP, int all, uint8_t *__restrict__ maskP,
-                             unsigned long long *__restrict__ nP, unsigned long long *__restrict__ hash) {
-  unsigned long long c = 0, h = 0;
+                             long long N1, unsigned long long kP, int all, uint8_t *__restrict__ maskP,
+                             unsigned long long *__restrict__ nP) {
+  unsigned long long c = 0, h = 0, cd = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const bool keep = maskM[i] && (all || (unsigned long long)__double_as_longlong(c2[i]) >= kP);
     maskP[i] = keep;
     if (keep) {
       ++c;
       h += aci_mix((unsigned long long)i);
+      if (N1 > 0 && i / N1 == i % N1) ++cd;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
     c += __shfl_xor_sync(0xffffffffu, c, o);
     h += __shfl_xor_sync(0xffffffffu, h, o);
+    cd += __shfl_xor_sync(0xffffffffu, cd, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(nP, c);
-    atomicAdd(hash, h);
+    atomicAdd(nP + 1, h);
+    atomicAdd(nP + 2, cd);
   }
 }
 
@@ -200,8 +219,8 @@ int radix_walk(forte_ctx *ctx, const double *a, long long N, double limit, bool 
 
 }  // namespace
 
-int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out, double *C_out,
-            long long *nM_out, long long *nP_out, int *cycles_out) {
+int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
+            double *C_out, long long *nM_out, long long *nP_out, int *cycles_out) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->Ndet;
   const size_t vd = ((sizeof(double) * N + 255) / 256) * 256, vb = ((size_t)N + 255) / 256 * 256;
@@ -220,7 +239,7 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
   w.mPn = (uint8_t *)p; p += vb;
   w.cnt = (unsigned long long *)p; p += sizeof(unsigned long long) * 260;
   w.sum = (double *)p;
-  unsigned long long *d_n = w.cnt + 256, *d_hash = w.cnt + 257;
+  unsigned long long *d_n = w.cnt + 256;  // [0] count, [1] hash, [2] diagonal count
   double *d_es = w.sum + 256;
 
   // the unrestricted diagonal, kept while the masks change d_hdiag
@@ -230,21 +249,24 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
     ctx->detmask_on = false;
     ctx->d_detmask = nullptr;
     ctx->detmask_n = 0;
+    ctx->detmask_ndiag = 0;
+    ctx->spin_parity = 0;
     cudaMemcpyAsync(ctx->d_hdiag, w.hd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     forte_set_guess(ctx, nullptr, 0);
     ctx->nroots_done = 0;
   };
-  auto install = [&](uint8_t *mask, long long cnt) -> int {
+  auto install = [&](uint8_t *mask, long long cnt, long long ndiag) -> int {
     ctx->d_detmask = mask;
     ctx->detmask_n = cnt;
+    ctx->detmask_ndiag = ndiag;
     ctx->detmask_on = true;
     FORTE_CUDA_TRY(cudaMemcpyAsync(ctx->d_hdiag, w.hd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     return det_mask_fill(ctx, ctx->d_hdiag, 1, (double)INFINITY);
   };
   unsigned long long pert_key = 0x2545F4914F6CDD1Dull;
-  auto solve = [&](uint8_t *mask, long long cnt, bool guess, double *E) -> int {
+  auto solve = [&](uint8_t *mask, long long cnt, long long ndiag, bool guess, double *E) -> int {
     int r;
-    if ((r = install(mask, cnt))) return r;
+    if ((r = install(mask, cnt, ndiag))) return r;
     if (guess) {  // [previous state, perturbation]; both projected onto the space
       pert_key += 0x9E3779B97F4A7C15ull;
       k_aci_pert<<<grid_for(N), 256, 0, st>>>(w.psi + N, N, pert_key);
@@ -267,25 +289,37 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
     FORTE_LAUNCH_CHECK();
     return FORTE_OK;
   };
+  // the start determinant: lowest diagonal (outside I_a == I_b for the odd sector)
   long long i0 = 0;
-  if ((rc = vk_argmin_k(ctx, w.hd, N, 1, &i0))) return rc;
+  const double *hstart = w.hd;
+  if (parity < 0) {
+    FORTE_CUDA_TRY(cudaMemcpyAsync(w.V, w.hd, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    k_aci_diag_fill<<<grid_for(ctx->Na), 256, 0, st>>>(w.V, ctx->Na, (double)INFINITY);
+    FORTE_LAUNCH_CHECK();
+    hstart = w.V;
+  }
+  if ((rc = vk_argmin_k(ctx, hstart, N, 1, &i0))) return rc;
   FORTE_CUDA_TRY(cudaMemsetAsync(w.mP, 0, (size_t)N, st));
   const uint8_t one = 1;
   FORTE_CUDA_TRY(cudaMemcpyAsync(w.mP + i0, &one, 1, cudaMemcpyHostToDevice, st));
-  long long nP = 1, nM = 0;
+  long long nP = 1, nM = 0, nPd = 0, nMd = 0;
   if (mirror) {
     const long long i1 = (i0 % ctx->Nb) * ctx->Nb + i0 / ctx->Nb;
     if (i1 != i0) {
       FORTE_CUDA_TRY(cudaMemcpyAsync(w.mP + i1, &one, 1, cudaMemcpyHostToDevice, st));
       nP = 2;
+    } else {
+      nPd = 1;
     }
   }
+  const long long N1 = mirror ? ctx->Na : 0;
+  ctx->spin_parity = parity;  // the P / M solves run in the sector; reset by uninstall()
   bool have_psi = false;
   std::vector<std::pair<long long, unsigned long long>> seen;
   double E_M = 0.0, eps_excl = 0.0;
   for (int cycle = 1;; ++cycle) {
     double E_P;
-    if ((rc = solve(w.mP, nP, have_psi, &E_P))) return fail(rc);
+    if ((rc = solve(w.mP, nP, nPd, have_psi, &E_P))) return fail(rc);
     // V = H Psi_P over the grid, estimates, exclusion
     if ((rc = sigma_grid(ctx, ctx->d_roots, w.V, 1))) return fail(rc);
     {
@@ -302,21 +336,22 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
     bool fM = false;
     if ((rc = radix_walk(ctx, aa, N, sigma, true, w, &kM, &fM))) return fail(rc);
     if (!fM) kM = 0x7FF0000000000000ull;  // every finite estimate is excluded
-    FORTE_CUDA_TRY(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long), st));
+    FORTE_CUDA_TRY(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long) * 3, st));
     FORTE_CUDA_TRY(cudaMemsetAsync(d_es, 0, sizeof(double), st));
     {
       FORTE_PROF(ctx, "aci_mask");
-      k_aci_mask_m<<<grid_for(N), 256, 0, st>>>(aa, w.eps, N, kM, w.mM, d_n, d_es);
+      k_aci_mask_m<<<grid_for(N), 256, 0, st>>>(aa, w.eps, N, N1, kM, w.mM, d_n, d_es);
       FORTE_LAUNCH_CHECK();
     }
-    unsigned long long hn = 0;
-    FORTE_CUDA_TRY(cudaMemcpyAsync(&hn, d_n, sizeof(hn), cudaMemcpyDeviceToHost, st));
+    unsigned long long hn[3];
+    FORTE_CUDA_TRY(cudaMemcpyAsync(hn, d_n, sizeof(hn), cudaMemcpyDeviceToHost, st));
     FORTE_CUDA_TRY(cudaMemcpyAsync(&eps_excl, d_es, sizeof(double), cudaMemcpyDeviceToHost, st));
     FORTE_CUDA_TRY(cudaStreamSynchronize(st));
-    nM = (long long)hn;
+    nM = (long long)hn[0];
+    nMd = (long long)hn[2];
     // Psi_M (started from Psi_P)
     FORTE_CUDA_TRY(cudaMemcpyAsync(w.psi, ctx->d_roots, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    if ((rc = solve(w.mM, nM, true, &E_M))) return fail(rc);
+    if ((rc = solve(w.mM, nM, nMd, true, &E_M))) return fail(rc);
     FORTE_CUDA_TRY(cudaMemcpyAsync(w.psi, ctx->d_roots, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     // next reference space
     {
@@ -332,17 +367,18 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
     unsigned long long kP = 0;
     bool fP = false;
     if ((rc = radix_walk(ctx, c2, N, 1.0 - gamma * sigma, false, w, &kP, &fP))) return fail(rc);
-    FORTE_CUDA_TRY(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long) * 2, st));
+    FORTE_CUDA_TRY(cudaMemsetAsync(d_n, 0, sizeof(unsigned long long) * 3, st));
     {
       FORTE_PROF(ctx, "aci_mask");
-      k_aci_mask_p<<<grid_for(N), 256, 0, st>>>(c2, w.mM, N, kP, fP ? 0 : 1, w.mPn, d_n, d_hash);
+      k_aci_mask_p<<<grid_for(N), 256, 0, st>>>(c2, w.mM, N, N1, kP, fP ? 0 : 1, w.mPn, d_n);
       FORTE_LAUNCH_CHECK();
     }
-    unsigned long long hv[2];
+    unsigned long long hv[3];
     FORTE_CUDA_TRY(cudaMemcpyAsync(hv, d_n, sizeof(hv), cudaMemcpyDeviceToHost, st));
     FORTE_CUDA_TRY(cudaStreamSynchronize(st));
     const std::pair<long long, unsigned long long> key((long long)hv[0], hv[1]);
     nP = (long long)hv[0];
+    nPd = (long long)hv[2];
     std::swap(w.mP, w.mPn);
     have_psi = true;
     if (std::find(seen.begin(), seen.end(), key) != seen.end() || cycle >= max_cycles) {

@@ -913,7 +913,7 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
   return gas_set(ctx, nspace, size, gmin, gmax, ndet_out);
 }
 
-int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out,
+int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
               double *C_out, long long *nM_out, long long *nP_out, int *cycles_out) {
   if (!ctx || !E_out) { set_error("NULL argument"); return FORTE_ERR_ARG; }
   if (!(sigma >= 0) || !isfinite(sigma) || !(gamma >= 0) || !isfinite(gamma) || max_cycles < 1 || !(tol > 0)) {
@@ -924,7 +924,9 @@ int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double
     set_error("adaptive CI runs on the unrestricted determinant grid (no forte_set_gas / spin parity)");
     return FORTE_ERR_ARG;
   }
-  return aci_run(ctx, sigma, gamma, max_cycles, tol, E_out, C_out, nM_out, nP_out, cycles_out);
+  if (parity != 0 && parity != 1 && parity != -1) { set_error("parity must be -1, 0 or +1"); return FORTE_ERR_ARG; }
+  if (parity != 0 && ctx->na != ctx->nb) { set_error("a parity sector needs n_alpha == n_beta"); return FORTE_ERR_ARG; }
+  return aci_run(ctx, sigma, gamma, max_cycles, tol, parity, E_out, C_out, nM_out, nP_out, cycles_out);
 }
 
 int forte_set_spin_parity(forte_ctx *ctx, int parity) {

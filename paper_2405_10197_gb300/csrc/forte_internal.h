@@ -165,6 +165,7 @@ struct forte_ctx {
   // arbitrary determinant mask [Ndet] (the P and M spaces of adaptive CI)
   bool detmask_on = false;
   long long detmask_n = 0;
+  long long detmask_ndiag = 0;  // masked-in determinants |I>|I> (square grids)
   uint8_t *d_detmask = nullptr;
 
   long long n_sigma_fp64 = 0, n_sigma_mixed = 0;
@@ -262,8 +263,8 @@ int det_mask_fill(forte_ctx *ctx, double *x, int nvec, double value);  // value 
 int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec);  // api.cu: unrestricted FP64-class sigma
 
 // aci.cu: adaptive CI on the determinant grid
-int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, double *E_out, double *C_out,
-            long long *nM_out, long long *nP_out, int *cycles_out);
+int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
+            double *C_out, long long *nM_out, long long *nP_out, int *cycles_out);
 
 // spin.cu: spin-parity sectors C^T = parity C for Ms = 0
 int spin_set(forte_ctx *ctx, int parity);

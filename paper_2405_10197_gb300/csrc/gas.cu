@@ -69,7 +69,11 @@ int gas_mask(forte_ctx *ctx, float *x, int nvec) { return gas_fill<float>(ctx, x
 int det_mask_fill(forte_ctx *ctx, double *x, int nvec, double value) { return gas_fill<double>(ctx, x, nvec, value); }
 
 long long space_dim(const forte_ctx *ctx) {
-  if (ctx->detmask_on) return ctx->detmask_n;  // (used alone: no restriction or sector besides it)
+  if (ctx->detmask_on) {  // (no occupation restriction besides it; the mask is mirror-closed with a sector)
+    if (ctx->spin_parity == 0) return ctx->detmask_n;
+    const long long D = ctx->detmask_ndiag;
+    return (ctx->detmask_n - D) / 2 + (ctx->spin_parity > 0 ? D : 0);
+  }
   const long long K = ctx->gas_on ? ctx->gas_ndet : ctx->Ndet;
   if (ctx->spin_parity == 0) return K;
   // the kept set is symmetric under I_alpha <-> I_beta: mirror pairs plus the diagonal

@@ -38,6 +38,25 @@ def test_aci_matches_oracle(n, na, nb, seed, sigma):
         prob.close()
 
 
+@pytest.mark.parametrize("parity", [1, -1])
+@pytest.mark.parametrize("n,m,seed,sigma", [(6, 3, 1, 1e-2), (6, 3, 1, 1e-3), (7, 3, 8, 1e-3)])
+def test_aci_parity_sector_matches_oracle(n, m, seed, sigma, parity):
+    h, eri = si.integrals(n, 2 * n, seed=seed)
+    ref = oracle.aci(n, m, m, h, eri, sigma, parity=parity)
+    prob = fg.CASProblem(n, m, m, h, eri)
+    try:
+        E, Ec, C, nM, nP, cyc = prob.aci(sigma, tol=1e-11, parity=parity)
+        assert abs(E - ref["E"]) < 1e-9 and abs(Ec - ref["E_corrected"]) < 1e-9
+        assert nM == int(ref["M"].sum()) and nP == int(ref["P"].sum()) and cyc == ref["cycles"]
+        Cn = C.cpu().numpy()
+        assert np.abs(Cn - parity * Cn.T).max() <= 1e-15
+        # the sector is left again afterwards
+        E0, _, _, _ = prob.davidson(nroots=1, tol=1e-10)
+        assert E0[0] <= E + 1e-10
+    finally:
+        prob.close()
+
+
 def test_aci_tensor_core_precision_mode():
     n, na, nb = 7, 3, 3
     h, eri = si.integrals(n, 14, seed=8)
@@ -57,6 +76,8 @@ def test_aci_arguments():
     try:
         with pytest.raises(fg.ForteError):
             prob.aci(-1.0)
+        with pytest.raises(fg.ForteError):
+            prob.aci(1e-3, parity=2)
         prob.set_gas((2, 4), (2, 0), (4, 8))
         with pytest.raises(fg.ForteError):
             prob.aci(1e-3)
