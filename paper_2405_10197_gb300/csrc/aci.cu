@@ -219,8 +219,9 @@ int radix_walk(forte_ctx *ctx, const double *a, long long N, double limit, bool 
 
 }  // namespace
 
-int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
-            double *C_out, long long *nM_out, long long *nP_out, int *cycles_out) {
+static int aci_body(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity,
+                    double *E_out, double *C_out, long long *nM_out, long long *nP_out, int *cycles_out,
+                    const double **hd_saved) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->Ndet;
   const size_t vd = ((sizeof(double) * N + 255) / 256) * 256, vb = ((size_t)N + 255) / 256 * 256;
@@ -245,6 +246,7 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
   // the unrestricted diagonal, kept while the masks change d_hdiag
   if ((rc = hdiag_build(ctx))) return rc;
   FORTE_CUDA_TRY(cudaMemcpyAsync(w.hd, ctx->d_hdiag, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  *hd_saved = w.hd;
   auto uninstall = [&]() {
     ctx->detmask_on = false;
     ctx->d_detmask = nullptr;
@@ -395,6 +397,23 @@ int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double t
     }
     seen.push_back(key);
   }
+}
+
+int aci_run(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,
+            double *C_out, long long *nM_out, long long *nP_out, int *cycles_out) {
+  const double *hd = nullptr;
+  const int rc = aci_body(ctx, sigma, gamma, max_cycles, tol, parity, E_out, C_out, nM_out, nP_out, cycles_out, &hd);
+  // on every exit, also the early ones: the context is unrestricted again
+  ctx->detmask_on = false;
+  ctx->d_detmask = nullptr;
+  ctx->detmask_n = 0;
+  ctx->detmask_ndiag = 0;
+  ctx->spin_parity = 0;
+  ctx->nroots_done = 0;
+  if (hd) cudaMemcpyAsync(ctx->d_hdiag, hd, sizeof(double) * ctx->Ndet, cudaMemcpyDeviceToDevice, ctx->stream);
+  forte_set_guess(ctx, nullptr, 0);
+  cudaStreamSynchronize(ctx->stream);
+  return rc;
 }
 
 }  // namespace forte
