@@ -23,6 +23,8 @@ from .driver import (  # noqa: F401
     rdm3,
     rdm2_elements,
     num_threads,
+    det_words,
+    sci_sigma,
 )
 from .gas import gas_allowed, sigma_gas, solve_dense_gas  # noqa: F401
 from .spin import sector_basis, solve_dense_spin  # noqa: F401

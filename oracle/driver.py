@@ -63,6 +63,8 @@ def _L():
             lib.ora_rdm3.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_void_p]
             lib.ora_rdm2_elements.argtypes = [ctypes.c_int] * 3 + [dp, dp, ctypes.c_long,
                                                                    ctypes.c_void_p, dp]
+            lib.ora_sci_sigma.argtypes = [ctypes.c_int, ctypes.c_long, ctypes.c_void_p, dp, dp, ctypes.c_int,
+                                          dp, dp]
             lib.ora_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -253,6 +255,24 @@ def davidson(norb, nalpha, nbeta, h, eri, nroots=1, tol=1e-10, max_iter=200,
         SA = sigma(norb, nalpha, nbeta, h, eri, A)
         B = np.vstack([B, A])
         S = np.vstack([S, SA])
+
+
+def det_words(norb, alpha_strings, beta_strings):
+    """64-bit determinant words: alpha orbital p at bit p, beta orbital p at bit norb + p."""
+    a = np.asarray(alpha_strings, dtype=np.uint64)
+    b = np.asarray(beta_strings, dtype=np.uint64)
+    return a | (b << np.uint64(norb))
+
+
+def sci_sigma(norb, dets, h, eri, C):
+    """Sigma over an arbitrary list of determinants (64-bit words, norb <= 32):
+    S[v][i] = sum_j <D_i|H|D_j> C[v][j].  C has shape [nvec, len(dets)]."""
+    h, eri = _f64(h), _f64(eri)
+    dets = np.ascontiguousarray(dets, dtype=np.uint64)
+    Cf = _f64(np.atleast_2d(C))
+    S = np.zeros_like(Cf)
+    _L().ora_sci_sigma(norb, len(dets), dets.ctypes.data, _dp(h), _dp(eri), Cf.shape[0], _dp(Cf), _dp(S))
+    return S
 
 
 def rdm12(norb, nalpha, nbeta, bra, ket=None, one=True, two=True):

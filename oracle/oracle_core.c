@@ -126,6 +126,23 @@ double ora_hij(int n, const double *h, const double *eri, uint64_t I, uint64_t J
   return 0.0;
 }
 
+/* Sigma over an arbitrary list of determinants (selected CI, Sec. II.A.2):
+ * S[v][i] = sum_j <D_i|H|D_j> C[v][j], the sum over the j within two
+ * replacements of i (every other element vanishes by the Slater-Condon rules).
+ * n <= 32 (2n spin orbitals in one 64-bit word). */
+void ora_sci_sigma(int n, long nd, const uint64_t *dets, const double *h, const double *eri, int nvec,
+                   const double *C, double *S) {
+#pragma omp parallel for schedule(dynamic, 8)
+  for (long i = 0; i < nd; ++i) {
+    for (int v = 0; v < nvec; ++v) S[(long)v * nd + i] = 0.0;
+    for (long j = 0; j < nd; ++j) {
+      if (popc64(dets[i] ^ dets[j]) > 4) continue;
+      const double hij = ora_hij(n, h, eri, dets[i], dets[j]);
+      for (int v = 0; v < nvec; ++v) S[(long)v * nd + i] += hij * C[(long)v * nd + j];
+    }
+  }
+}
+
 /* ---------- strings ---------- */
 
 /* All n-bit masks with k bits set, ascending; returns the count. */

@@ -46,6 +46,8 @@ MUTATIONS = {
         ("v[j * N + i] = parity / np.sqrt(2.0)", "v[j * N + i] = -parity / np.sqrt(2.0)", "spin.py"),
     "odd spin sector keeps the diagonal determinants":
         ("                if parity < 0:\n                    continue\n", "", "spin.py"),
+    "determinant-list sigma without the double replacements":
+        ("if (popc64(dets[i] ^ dets[j]) > 4) continue;", "if (popc64(dets[i] ^ dets[j]) > 2) continue;"),
     "2x2 estimate takes the upper root":
         ("return D - np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)",
          "return D + np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)", "aci.py"),

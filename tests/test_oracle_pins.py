@@ -526,3 +526,65 @@ def test_spin_sectors_partition_an_occupation_restricted_spectrum():
         w, _ = oracle.solve_dense_spin(n, m, h, eri, p, nroots=dim, keep=keep)
         both.append(w)
     assert np.abs(np.sort(np.concatenate(both)) - w_all).max() < 1e-11
+
+
+# ---------------------------------------------------------------- determinant-list sigma
+# (Sec. II.A.2: selected CI works on an arbitrary list of determinants)
+def test_sci_sigma_matches_fock_space_on_a_mixed_determinant_list():
+    # Random determinants from several (n_alpha, n_beta) sectors, in random order:
+    # sigma equals the operator-product Hamiltonian restricted to the list.
+    n = 5
+    h, eri = si.integrals(n, 10, seed=12)
+    rng = np.random.default_rng(4)
+    words = []
+    for na, nb in [(2, 2), (2, 3), (3, 2)]:
+        sa, sb = oracle.strings(n, na), oracle.strings(n, nb)
+        words += list(oracle.det_words(n, rng.choice(sa, 30), rng.choice(sb, 30)))
+    dets = np.unique(np.array(words, dtype=np.uint64))
+    rng.shuffle(dets)
+    C = rng.normal(size=(2, dets.size))
+    H = fock_ref.hamiltonian(n, h, eri)
+    idx = dets.astype(np.int64)
+    ref = (H[idx][:, idx] @ C.T).T
+    assert np.abs(oracle.sci_sigma(n, dets, h, eri, C) - ref).max() < 1e-12
+
+
+def _det_energy(h, eri, A, B):
+    """<D|H|D> from the closed-shell-style sums over occupied alpha (A) and beta (B) orbitals."""
+    e = sum(h[a, a] for a in A) + sum(h[b, b] for b in B)
+    for S in (A, B):
+        e += 0.5 * sum(eri[p, p, q, q] - eri[p, q, q, p] for p in S for q in S)
+    e += sum(eri[a, a, b, b] for a in A for b in B)
+    return e
+
+
+def test_sci_sigma_beyond_sixteen_orbitals():
+    # 20 orbitals (beta spin orbitals in bits 20..39): Hermiticity, the determinant
+    # energy and the single-replacement element in closed form.
+    n = 20
+    h, eri = si.integrals(n, 40, seed=3)
+    rng = np.random.default_rng(6)
+    A0, B0 = [0, 1, 2], [0, 1, 3]
+    base = sum(1 << a for a in A0) | (sum(1 << b for b in B0) << n)
+    singles = []
+    for s_ in A0:
+        for r in range(n):
+            if r not in A0:
+                singles.append((r, s_, base ^ (1 << s_) ^ (1 << r)))
+    others = [sum(1 << int(x) for x in rng.choice(n, 3, replace=False))
+              | (sum(1 << int(x) for x in rng.choice(n, 3, replace=False)) << n) for _ in range(40)]
+    dets = np.unique(np.array([base] + [d for _, _, d in singles] + others, dtype=np.uint64))
+    H = oracle.sci_sigma(n, dets, h, eri, np.eye(dets.size))
+    assert np.abs(H - H.T).max() < 1e-12
+    for k, d in enumerate(dets):
+        d = int(d)
+        A = [p for p in range(n) if (d >> p) & 1]
+        B = [p for p in range(n) if (d >> (n + p)) & 1]
+        assert abs(H[k, k] - _det_energy(h, eri, A, B)) < 1e-11
+    i0 = int(np.flatnonzero(dets == np.uint64(base))[0])
+    for r, s_, d in singles:
+        j = int(np.flatnonzero(dets == np.uint64(d))[0])
+        lo, hi = min(r, s_), max(r, s_)
+        sign = (-1) ** sum(1 for a in A0 if lo < a < hi)
+        v = h[r, s_] + sum(eri[r, s_, k, k] - eri[r, k, k, s_] for k in A0) + sum(eri[r, s_, k, k] for k in B0)
+        assert abs(H[j, i0] - sign * v) < 1e-12
