@@ -258,7 +258,10 @@ def davidson(norb, nalpha, nbeta, h, eri, nroots=1, tol=1e-10, max_iter=200,
 
 
 def det_words(norb, alpha_strings, beta_strings):
-    """64-bit determinant words: alpha orbital p at bit p, beta orbital p at bit norb + p."""
+    """64-bit determinant words: alpha orbital p at bit p, beta orbital p at bit norb + p
+    (2 norb <= 64 spin orbitals, so norb <= 32)."""
+    if not 1 <= norb <= 32:
+        raise ValueError("determinant words hold at most 32 orbitals")
     a = np.asarray(alpha_strings, dtype=np.uint64)
     b = np.asarray(beta_strings, dtype=np.uint64)
     return a | (b << np.uint64(norb))
@@ -266,7 +269,10 @@ def det_words(norb, alpha_strings, beta_strings):
 
 def sci_sigma(norb, dets, h, eri, C):
     """Sigma over an arbitrary list of determinants (64-bit words, norb <= 32):
-    S[v][i] = sum_j <D_i|H|D_j> C[v][j].  C has shape [nvec, len(dets)]."""
+    S[v][i] = sum_j <D_i|H|D_j> C[v][j].  C has shape [nvec, len(dets)].  The list
+    may mix (n_alpha, n_beta) sectors; determinants of different sectors do not couple."""
+    if not 1 <= norb <= 32:
+        raise ValueError("determinant words hold at most 32 orbitals")
     h, eri = _f64(h), _f64(eri)
     dets = np.ascontiguousarray(dets, dtype=np.uint64)
     Cf = _f64(np.atleast_2d(C))

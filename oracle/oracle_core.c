@@ -83,6 +83,11 @@ double ora_hij(int n, const double *h, const double *eri, uint64_t I, uint64_t J
   uint64_t x = I ^ J;
   int nd = popc64(x);
   int nso = 2 * n;
+  /* H of Eq. 1 conserves the number of alpha and of beta electrons: determinants
+   * of different sectors do not couple (and the replacement analysis below
+   * assumes equal counts). */
+  const uint64_t amask = (n >= 64) ? ~0ULL : ((1ULL << n) - 1ULL);
+  if (popc64(I & amask) != popc64(J & amask) || popc64(I & ~amask) != popc64(J & ~amask)) return 0.0;
   if (nd == 0) {
     double e = 0.0;
     for (int P = 0; P < nso; ++P) {

@@ -53,6 +53,8 @@ MUTATIONS = {
          "return D + np.sqrt(D * D + np.asarray(V, dtype=np.float64) ** 2)", "aci.py"),
     "2x2 estimate without the half of the diagonal gap":
         ("D = 0.5 * (np.asarray(Hmm, dtype=np.float64) - E)", "D = (np.asarray(Hmm, dtype=np.float64) - E)", "aci.py"),
+    "determinant diagonal stored beta-major":
+        ("    d[i] = ora_hij(n, h, eri, I, I);", "    d[(i % sp.Nb) * sp.Na + i / sp.Nb] = ora_hij(n, h, eri, I, I);"),
     "model space without the reference determinants":
         ("        M = ~excl\n", "        M = ~excl & ~P\n", "aci.py"),
 }

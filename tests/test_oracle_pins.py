@@ -537,7 +537,9 @@ def test_sci_sigma_matches_fock_space_on_a_mixed_determinant_list():
     h, eri = si.integrals(n, 10, seed=12)
     rng = np.random.default_rng(4)
     words = []
-    for na, nb in [(2, 2), (2, 3), (3, 2)]:
+    # sectors (3, 3), (4, 2) and (1, 1) differ from (2, 2) by two electrons, so their
+    # XOR with it can have 2 or 4 bits set while H must still give zero between them
+    for na, nb in [(2, 2), (2, 3), (3, 2), (3, 3), (4, 2), (1, 1)]:
         sa, sb = oracle.strings(n, na), oracle.strings(n, nb)
         words += list(oracle.det_words(n, rng.choice(sa, 30), rng.choice(sb, 30)))
     dets = np.unique(np.array(words, dtype=np.uint64))
@@ -556,6 +558,27 @@ def _det_energy(h, eri, A, B):
         e += 0.5 * sum(eri[p, p, q, q] - eri[p, q, q, p] for p in S for q in S)
     e += sum(eri[a, a, b, b] for a in A for b in B)
     return e
+
+
+def _masks(n, k):
+    """All k-of-n occupation masks in ascending order (string addresses, Sec. II.A.1)."""
+    return sorted(sum(1 << p for p in c) for c in itertools.combinations(range(n), k))
+
+
+@pytest.mark.parametrize("n,na,nb", [(5, 3, 1), (6, 2, 4), (6, 3, 3), (7, 4, 2), (4, 0, 2)])
+def test_hdiag_matches_closed_form_and_dense_diagonal(n, na, nb):
+    # The determinant diagonal (the Davidson preconditioner) at index
+    # I_alpha * N_beta + I_beta: the Slater-Condon diagonal written as sums over the
+    # occupied orbitals, and the diagonal of the Fock-space-pinned dense H.  Unequal
+    # alpha and beta counts make a transposed index visible.
+    h, eri = si.integrals(n, 2 * n, seed=40 + n + na)
+    d = oracle.hdiag(n, na, nb, h, eri)
+    sa, sb = _masks(n, na), _masks(n, nb)
+    assert d.shape == (len(sa) * len(sb),)
+    ref = np.array([_det_energy(h, eri, [p for p in range(n) if (a >> p) & 1],
+                                [p for p in range(n) if (b >> p) & 1]) for a in sa for b in sb])
+    assert np.abs(d - ref).max() < 1e-12
+    assert np.abs(d - np.diag(oracle.hmat_dense(n, na, nb, h, eri))).max() < 1e-13
 
 
 def test_sci_sigma_beyond_sixteen_orbitals():
