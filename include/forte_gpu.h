@@ -241,6 +241,16 @@ int forte_rdms(forte_ctx *ctx, const double *C, double *g1, double *g2);
 int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const double *C, double scale,
                       double *dh, double *deri);
 
+/* State-averaged energy E_SA = sum_k w_k E_k (Sec. II.B, the weighted sum over
+ * the states of the ensemble) of the first nstates roots of the last
+ * forte_davidson on this context.
+ *   weights  host [nstates] (any finite values; the paper's ensembles have
+ *            w_k >= 0 and sum w_k = 1)
+ *   E_sa     host output
+ * FORTE_ERR_ARG when nstates < 1 or exceeds the number of roots of the last
+ * solve.  Host arithmetic on the stored energies; no device work. */
+int forte_sa_energy(const forte_ctx *ctx, int nstates, const double *weights, double *E_sa);
+
 /* One-body transition density matrix between two states (Sec. II.A.1):
  *   t1 device [n][n], t1_pq = sum_s <bra|a+_ps a_qs|ket>.  FP64. */
 int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1);
@@ -285,9 +295,12 @@ int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *
  * Limit: nvec * N_alpha * N_beta <= 1,048,576 (e.g. one CAS(12,12) vector);
  * larger requests return FORTE_ERR_ARG without touching the GPU.
  * The first call on a device looks up the array's device address (with that
- * device made current); make that first call before any stream capture.  All
+ * device made current) and keeps it for the process; make that first call
+ * before any stream capture.  The address belongs to the device's primary
+ * context: do not call this entry point again after cudaDeviceReset.  All
  * calls share the array, so calls that overlap on the GPU (for instance on two
- * streams at once) race.  Asynchronous on the context stream. */
+ * streams at once) race.  Same kernels as forte_sigma in FP64 (traced like them
+ * under forte_profile_enable).  Asynchronous on the context stream. */
 int forte_sigma_fp64_noalloc(forte_ctx *ctx, const double *C, double *S, int nvec);
 
 /* Kernel tracing.  While enabled, every kernel this library launches for the

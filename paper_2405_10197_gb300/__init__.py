@@ -82,6 +82,7 @@ def library():
         "forte_aci": [vp, d, d, i, d, i, vp, vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
+        "forte_sa_energy": [vp, i, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
@@ -277,6 +278,14 @@ def forte_sa_gradient(ctx, nstates, weights, C, scale, dh, deri, norb):
                                               float(scale), _ptr(dh, norb * norb), _ptr(deri, norb ** 4)))
 
 
+def forte_sa_energy(ctx, weights):
+    """E_SA = sum_k w_k E_k over the first len(weights) roots of the last forte_davidson."""
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    out = ctypes.c_double()
+    _check(library().forte_sa_energy(ctx, int(w.size), w.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
 def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, nworkers=8, allow_not_converged=False):
     """Solve a list of independent problems.
 
@@ -437,7 +446,7 @@ def _make_sa_energy():
     class SAEnergy(torch.autograd.Function):
         """E_SA(h, eri) = sum_k w_k E_k over the lowest len(weights) roots.
 
-        forward: forte_cas_create + forte_davidson; backward: forte_sa_gradient,
+        forward: forte_cas_create + forte_davidson + forte_sa_energy; backward: forte_sa_gradient,
         the library's adjoint kernel (dE/dh = sum w gamma, dE/d(pq|rs) = 1/2 sum w Gamma).
         """
 
@@ -451,7 +460,7 @@ def _make_sa_energy():
             fctx.prob, fctx.C, fctx.w = prob, C, w
             fctx.meta = (h.device, h.dtype, eri.device, eri.dtype)
             fctx.energies, fctx.residuals = E, rn
-            return torch.tensor(float(w @ E), dtype=h.dtype, device=h.device)
+            return torch.tensor(forte_sa_energy(prob.ctx, w), dtype=h.dtype, device=h.device)
 
         @staticmethod
         def backward(fctx, grad):

@@ -948,6 +948,21 @@ int forte_sa_gradient(forte_ctx *ctx, int nstates, const double *weights, const 
   return sa_gradient(ctx, nstates, weights, C, scale, dh, deri);
 }
 
+int forte_sa_energy(const forte_ctx *ctx, int nstates, const double *weights, double *E_sa) {
+  if (!ctx || !weights || !E_sa) { set_error("NULL argument"); return FORTE_ERR_ARG; }
+  if (nstates < 1 || nstates > ctx->nroots_done) {
+    set_error("nstates = %d but the last Davidson solve holds %d roots", nstates, ctx->nroots_done);
+    return FORTE_ERR_ARG;
+  }
+  double e = 0.0;
+  for (int k = 0; k < nstates; ++k) {
+    if (!isfinite(weights[k])) { set_error("non-finite weight"); return FORTE_ERR_ARG; }
+    e += weights[k] * ctx->roots_E[k];
+  }
+  *E_sa = e;
+  return FORTE_OK;
+}
+
 int forte_get_counters(const forte_ctx *ctx, long long *fp64, long long *mixed) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
   if (fp64) *fp64 = ctx->n_sigma_fp64;

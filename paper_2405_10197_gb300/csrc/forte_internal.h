@@ -200,6 +200,8 @@ int upload_tables(forte_ctx *ctx);
 
 // sigma_fp64.cu
 int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec);
+// the same with caller-provided beta-beta scratch T1, T2 (nvec * Ndet doubles each)
+int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, double *T1, double *T2);
 int hdiag_build(forte_ctx *ctx);
 // FP64-class sigma in double-FP32 arithmetic (relative error ~2^-46 per term);
 // with_ab = false leaves out the alpha-beta term (same-spin terms only)

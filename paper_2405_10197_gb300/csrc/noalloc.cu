@@ -13,16 +13,16 @@
 // use the symbol's host-side name as a device address, so the first call on a
 // device looks up the real address with cudaGetSymbolAddress (with that device
 // current) and caches it; that first call should therefore come before any
-// stream capture.  All calls share the array: calls that overlap on the GPU
-// (e.g. issued concurrently on two streams) race on it.  Each call overwrites
-// the scratch it reads, so nothing needs clearing between calls.
+// stream capture.  The cached address belongs to the device's primary context:
+// after cudaDeviceReset (or any teardown of that context) it is stale and this
+// entry point must not be called again in the process.  All calls share the
+// array: calls that overlap on the GPU (e.g. issued concurrently on two streams)
+// race on it.  Each call overwrites the scratch it reads, so nothing needs
+// clearing between calls.  The kernels are those of forte_sigma in FP64 (one
+// shared host body), traced like them when forte_profile_enable is on.
 #include <mutex>
 
 #include "forte_internal.h"
-
-namespace forte {
-int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, double *T1, double *T2);
-}
 
 namespace {
 

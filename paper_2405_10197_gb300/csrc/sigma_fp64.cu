@@ -148,46 +148,52 @@ static size_t ab_smem_bytes(int nkA, int nkB, int npair, long long NB, int TJ) {
 }
 
 int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
+  // beta-beta scratch: T1 = C^T, T2 = H_bb T1 (grown on demand)
+  const long long ND = ctx->Ndet;
+  int rc = ctx->sc_t1.ensure(sizeof(double) * ND * nvec);
+  if (rc) return rc;
+  rc = ctx->sc_t2.ensure(sizeof(double) * ND * nvec);
+  if (rc) return rc;
+  return sigma_fp64_scratch(ctx, C, S, nvec, (double *)ctx->sc_t1.ptr, (double *)ctx->sc_t2.ptr);
+}
+
+// The FP64 sigma with caller-provided scratch T1, T2 (each >= nvec * Ndet
+// doubles); allocates nothing.  Shared by forte_sigma (context scratch) and
+// forte_sigma_fp64_noalloc (the library's fixed array).
+int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, double *T1, double *T2) {
   cudaStream_t st = ctx->stream;
   const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
   // alpha-alpha: S = H_aa C
   {
     int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
     dim3 grid((unsigned)(NA * nchunk), nvec);
-    {
-      FORTE_PROF(ctx, "ss_spmm");
-      k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
+    FORTE_PROF(ctx, "ss_spmm");
+    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
                                                    ctx->sd[0].csr_val, C, S, NA, NB, nchunk, ND, 0);
     FORTE_LAUNCH_CHECK();
-    }
   }
   // beta-beta: T1 = C^T, T2 = H_bb T1, S += T2^T
   {
-    int rc = ctx->sc_t1.ensure(sizeof(double) * ND * nvec);
-    if (rc) return rc;
-    rc = ctx->sc_t2.ensure(sizeof(double) * ND * nvec);
-    if (rc) return rc;
-    double *T1 = (double *)ctx->sc_t1.ptr, *T2 = (double *)ctx->sc_t2.ptr;
     dim3 tb(32, 8);
     dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
     {
       FORTE_PROF(ctx, "transpose");
       k_transpose<double><<<g1, tb, 0, st>>>(C, T1, NA, NB, ND, 0);
-    FORTE_LAUNCH_CHECK();
+      FORTE_LAUNCH_CHECK();
     }
     int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
     dim3 grid((unsigned)(NB * nchunk), nvec);
     {
       FORTE_PROF(ctx, "ss_spmm");
       k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
-                                                   ctx->sd[1].csr_val, T1, T2, NB, NA, nchunk, ND, 0);
-    FORTE_LAUNCH_CHECK();
+                                                     ctx->sd[1].csr_val, T1, T2, NB, NA, nchunk, ND, 0);
+      FORTE_LAUNCH_CHECK();
     }
     dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
     {
       FORTE_PROF(ctx, "transpose");
       k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
-    FORTE_LAUNCH_CHECK();
+      FORTE_LAUNCH_CHECK();
     }
   }
   // alpha-beta
@@ -209,60 +215,7 @@ int sigma_fp64(forte_ctx *ctx, const double *C, double *S, int nvec) {
     }
     FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_fp64));
     dim3 grid((unsigned)NA, nvec);
-    {
-      FORTE_PROF(ctx, "ab_fp64");
-      k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB,
-                                              ctx->d_gpair, ctx->npair, C, S, ND, TJ);
-    FORTE_LAUNCH_CHECK();
-    }
-  }
-  return FORTE_OK;
-}
-
-// The FP64 sigma with caller-provided scratch T1, T2 (each >= nvec * Ndet
-// doubles): the same kernels as sigma_fp64, no allocation and no tracing.
-int sigma_fp64_scratch(forte_ctx *ctx, const double *C, double *S, int nvec, double *T1, double *T2) {
-  cudaStream_t st = ctx->stream;
-  const long long NA = ctx->Na, NB = ctx->Nb, ND = ctx->Ndet;
-  {
-    int nchunk = (int)((NB + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
-    dim3 grid((unsigned)(NA * nchunk), nvec);
-    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
-                                                   ctx->sd[0].csr_val, C, S, NA, NB, nchunk, ND, 0);
-    FORTE_LAUNCH_CHECK();
-  }
-  {
-    dim3 tb(32, 8);
-    dim3 g1((unsigned)((NB + 31) / 32), (unsigned)((NA + 31) / 32), nvec);
-    k_transpose<double><<<g1, tb, 0, st>>>(C, T1, NA, NB, ND, 0);
-    FORTE_LAUNCH_CHECK();
-    int nchunk = (int)((NA + SS_THREADS * SS_CPT - 1) / (SS_THREADS * SS_CPT));
-    dim3 grid((unsigned)(NB * nchunk), nvec);
-    k_ss_spmm<double><<<grid, SS_THREADS, 0, st>>>(ctx->sd[1].csr_ptr, ctx->sd[1].csr_col,
-                                                   ctx->sd[1].csr_val, T1, T2, NB, NA, nchunk, ND, 0);
-    FORTE_LAUNCH_CHECK();
-    dim3 g2((unsigned)((NA + 31) / 32), (unsigned)((NB + 31) / 32), nvec);
-    k_transpose<double><<<g2, tb, 0, st>>>(T2, S, NB, NA, ND, 1);
-    FORTE_LAUNCH_CHECK();
-  }
-  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[ctx->same_strings ? 0 : 1].nk;
-  if (nkA > 0 && nkB > 0) {
-    if (nkA > 80) {
-      set_error("alpha replacement list too long (%d)", nkA);
-      return FORTE_ERR_ARG;
-    }
-    int TJ = 64;
-    size_t smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
-    while (smem > 220 * 1024 && TJ > 8) {
-      TJ /= 2;
-      smem = ab_smem_bytes(nkA, nkB, ctx->npair, NB, TJ);
-    }
-    if (smem > 220 * 1024) {
-      set_error("alpha-beta FP64 kernel needs %zu bytes of shared memory", smem);
-      return FORTE_ERR_ARG;
-    }
-    FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_fp64));
-    dim3 grid((unsigned)NA, nvec);
+    FORTE_PROF(ctx, "ab_fp64");
     k_ab_fp64<<<grid, AB_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, NB, ctx->d_gpair,
                                               ctx->npair, C, S, ND, TJ);
     FORTE_LAUNCH_CHECK();

@@ -1,6 +1,7 @@
 // Reduced-precision sigma build (steps a5, a6, a8 of the hot path).
 //
-//   same-spin terms: FP32 CSR gathers (the FP64 kernels instantiated in FP32);
+//   same-spin terms: one dense tensor-core GEMM (sigma_ss_mma.cu); FP32 CSR gathers
+//       only when the dense string Hamiltonians would exceed 4 GB;
 //   alpha-beta term: per alpha string Ia, on the 5th-generation tensor cores
 //       F[rs][Jb] = sum_k  A[rs][k] * B[Jb][k]
 //       A[rs][k]  = s_k (pq_k|rs)            k over L(Ia), the replacements of Ia

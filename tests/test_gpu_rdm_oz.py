@@ -121,17 +121,26 @@ def test_oz_rdms_cas1212_match_fp64_path_and_invariants():
         prob.close()
 
 
-def test_oz_rdms_cas1414_match_fp64_path():
-    """The CAS(14,14) workload: 11.8 M determinants, 105 + 91 Gram rows."""
+def test_oz_rdms_cas1414_match_fp64_path_and_oracle_elements():
+    """The CAS(14,14) workload: 11.8 M determinants, 105 + 91 Gram rows.  The
+    tensor-core 2-RDM equals the FP64 path everywhere and the oracle's operator
+    application on sampled elements (random ones, and the diagonal-type
+    Gamma_ppqq / Gamma_pqqp that carry the largest values)."""
     cfg = si.CAS1414
     n = 14
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
     prob = fg.CASProblem(n, 7, 7, h, eri)
     try:
-        C = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=11)[0], device="cuda")
+        Ch = si.random_vectors(1, prob.na, prob.nb, seed=11)[0]
+        C = torch.tensor(Ch, device="cuda")
         _, g2d = _rdms(prob, C, fg.FORTE_FP64)
         _, g2o = _rdms(prob, C, fg.FORTE_BF16X2)
         assert np.abs(g2o - g2d).max() < TOL
+        rng = np.random.default_rng(14)
+        idx = np.vstack([rng.integers(0, n, size=(12, 4)),
+                         [[0, 0, 13, 13], [5, 5, 5, 5], [2, 9, 9, 2], [13, 6, 6, 13]]])
+        ref = oracle.rdm2_elements(n, 7, 7, Ch, idx)
+        assert np.abs(g2o[tuple(idx.T)] - ref).max() < TOL
     finally:
         prob.close()
 
