@@ -269,18 +269,41 @@ int forte_tdm1(forte_ctx *ctx, const double *bra, const double *ket, double *t1)
 int forte_rdm3(forte_ctx *ctx, const double *C, double *g3);
 
 /* Batched solve of nprob independent problems (many ActiveSpaceMethod instances
- * of the ActiveSpaceSolver, Sec. III): for problem i, the nroots[i] lowest
- * eigenvalues of its Hamiltonian, written to E_out[offset_i .. offset_i +
- * nroots[i]) with offset_i = sum_{j<i} nroots[j] (host).  Inputs per problem as
- * for forte_cas_create (host arrays h[i], eri[i]).  precision, tol as for
- * forte_set_precision / forte_davidson.  nworkers host threads (<= 0: 8), each
- * with its own CUDA stream, take problems largest first; every context is freed
- * after its solve.  status_out (host [nprob], may be NULL) gets each problem's
- * status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED keeps energies).
- * Synchronous. */
+ * of the ActiveSpaceSolver, Sec. III; CASCI of Sec. II.A.1 for each): for problem
+ * i, the nroots[i] lowest eigenvalues of its Hamiltonian, written to
+ * E_out[offset_i .. offset_i + nroots[i]) with offset_i = sum_{j<i} nroots[j] (host).
+ * Inputs per problem as for forte_cas_create (host arrays h[i], eri[i]).
+ * Problems with equal (norb, nalpha, nbeta) form a size class sharing strings,
+ * replacement lists and the same-spin sparsity pattern; each class is one kernel
+ * launch with one CTA per problem that runs the whole Davidson-Liu solve on the
+ * device, the class launches are captured in one CUDA graph, and the batch makes
+ * one device allocation.  Before the solve an autotuner times the per-CTA sigma
+ * of every class for each (threads per CTA, beta tile width) candidate and keeps
+ * the fastest (forte_batch_tuning reports the choices).
+ *   precision  FORTE_FP64: FP64 sigma; FORTE_DF32 / FORTE_OZ64: double-FP32
+ *              (FP64-class) sigma; FORTE_TF32 / FORTE_BF16X2: FP32 sigma down to
+ *              a residual of max(tol, 3e-4), then the double-FP32 sigma.  Vectors,
+ *              subspace and eigenproblem are FP64 in every mode.
+ *   tol        max residual 2-norm per root; max_iter the iteration cap (<= 0: 400)
+ * Davidson as forte_davidson (guess, preconditioner, 12 vectors per root,
+ * collapse to 2 per root).  Problems with more than 4,000,000 determinants or
+ * more than 3 roots take the single-problem path (forte_cas_create /
+ * forte_davidson, one after another).  status_out (host [nprob], may be NULL)
+ * gets each problem's status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED
+ * keeps energies); FORTE_ERR_ALLOC when the pooled workspace (about
+ * (2 * 12 * nroots + 2 * nroots + 4) * N_det doubles per problem) cannot be
+ * allocated.  Synchronous. */
 int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *nbeta, const int *nroots,
                       const double *const *h, const double *const *eri, int precision, double tol,
-                      int nworkers, double *E_out, int *status_out);
+                      int max_iter, double *E_out, int *status_out);
+
+/* Autotuner choices of the last forte_batch_solve, one entry per size class
+ * (host outputs of length max_classes, any may be NULL; *nclass = number of
+ * classes): orbital and electron counts, threads per CTA, beta tile width of the
+ * alpha-beta term, and the measured time (ms) of one sigma build of the class's
+ * first problems (one CTA each) with the chosen candidate. */
+int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads, int *tile,
+                       double *sigma_ms);
 
 /* FP64 sigma = H C that allocates no device memory (the paper has no
  * counterpart; this is a service for callers of the library).  It is meant for

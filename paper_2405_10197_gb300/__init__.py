@@ -84,6 +84,7 @@ def library():
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_sa_energy": [vp, i, vp, vp],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
+        "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -286,8 +287,8 @@ def forte_sa_energy(ctx, weights):
     return out.value
 
 
-def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, nworkers=8, allow_not_converged=False):
-    """Solve a list of independent problems.
+def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, max_iter=400, allow_not_converged=False):
+    """Solve a list of independent problems (one CTA per problem, one launch per size class).
 
     problems: sequence of dicts with norb, nalpha, nbeta, nroots, h, eri (host arrays).
     Returns (list of energy arrays, per-problem status array)."""
@@ -306,13 +307,27 @@ def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, nworkers=8, allo
     st = np.zeros(P, dtype=np.int32)
     code = library().forte_batch_solve(P, norb.ctypes.data, na.ctypes.data, nb.ctypes.data, nr.ctypes.data,
                                        ctypes.cast(hp, ctypes.c_void_p), ctypes.cast(ep, ctypes.c_void_p),
-                                       int(precision), float(tol), int(nworkers), E.ctypes.data, st.ctypes.data)
+                                       int(precision), float(tol), int(max_iter), E.ctypes.data, st.ctypes.data)
     _check(code, (FORTE_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     out, o = [], 0
     for k in nr:
         out.append(E[o:o + k].copy())
         o += k
     return out, st
+
+
+def forte_batch_tuning():
+    """Autotuner choices of the last forte_batch_solve: list of dicts per size class."""
+    cap = 64
+    nc = ctypes.c_int()
+    arrs = [np.zeros(cap, dtype=np.int32) for _ in range(5)]
+    ms = np.zeros(cap)
+    _check(library().forte_batch_tuning(cap, ctypes.byref(nc), *[a.ctypes.data for a in arrs], ms.ctypes.data))
+    out = []
+    for k in range(min(nc.value, cap)):
+        out.append(dict(norb=int(arrs[0][k]), nalpha=int(arrs[1][k]), nbeta=int(arrs[2][k]),
+                        threads=int(arrs[3][k]), tile=int(arrs[4][k]), sigma_ms=float(ms[k])))
+    return out
 
 
 def forte_profile_enable(ctx, on):

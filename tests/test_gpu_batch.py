@@ -1,7 +1,10 @@
-"""Batched solve (forte_batch_solve) of independent active-space problems of
-uneven size and root count, against the oracle (dense diagonalisation) and,
-for the batch workload's larger instances, across precisions."""
+"""Batched solve (forte_batch_solve): one launch per size class, one CTA per
+problem running the whole Davidson solve, against the oracle (dense
+diagonalisation, stored oracle energies) and across precisions."""
+import glob
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -16,6 +19,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2405_10197_gb300 as fg  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def _small_batch(count, seed):
@@ -34,31 +39,67 @@ def _small_batch(count, seed):
 
 @pytest.mark.parametrize("precision", [fg.FORTE_FP64, fg.FORTE_BF16X2, fg.FORTE_OZ64])
 def test_batch_matches_oracle_dense(precision):
+    # mixed classes, empty spins (n_alpha or n_beta = 0), spaces smaller than the subspace
     probs = _small_batch(40, seed=3)
-    E, st = fg.forte_batch_solve(probs, precision=precision, tol=1e-10, nworkers=6)
+    E, st = fg.forte_batch_solve(probs, precision=precision, tol=1e-10)
     assert np.all(st == 0)
     for p, e in zip(probs, E):
         w, _ = oracle.solve_dense(p["norb"], p["nalpha"], p["nbeta"], p["h"], p["eri"], nroots=p["nroots"])
-        assert np.abs(e - w).max() < 1e-9, p
+        assert np.abs(e - w).max() < 1e-10, p
 
 
-def test_batch_workload_head_fp64_vs_mixed():
-    # first instances of the batched workload (orbital counts {6,8,10,12}, 1-3 roots)
-    inst = si.batch_instances()[:16]
+def _workload(count, max_norb=12):
     probs = []
-    for q in inst:
+    for q in si.batch_instances():
+        if len(probs) == count:
+            break
+        if q["norb"] > max_norb:
+            continue
         h, eri = si.integrals(q["norb"], q["n_l"], q["seed"])
         probs.append(dict(norb=q["norb"], nalpha=q["nalpha"], nbeta=q["nbeta"], nroots=q["nroots"], h=h, eri=eri))
-    E64, st64 = fg.forte_batch_solve(probs, precision=fg.FORTE_FP64, tol=1e-6)
-    Em, stm = fg.forte_batch_solve(probs, precision=fg.FORTE_BF16X2, tol=1e-6)
+    return probs
+
+
+def test_batch_workload_head_fp64_vs_mixed_and_oracle():
+    # the first instances of the batched workload with up to 10 orbitals (1-3 roots):
+    # FP64 and mixed agree; the n = 6 and n = 8 instances match the oracle's dense
+    # diagonalisation to 1e-9 Eh
+    probs = _workload(16, max_norb=10)
+    E64, st64 = fg.forte_batch_solve(probs, precision=fg.FORTE_FP64, tol=1e-7)
+    Em, stm = fg.forte_batch_solve(probs, precision=fg.FORTE_BF16X2, tol=1e-7)
     assert np.all(st64 == 0) and np.all(stm == 0)
     for a, b in zip(E64, Em):
-        assert np.abs(a - b).max() < 1e-8
-    # the n = 6 instances also against the oracle
+        assert np.abs(a - b).max() < 1e-9
+    checked = 0
     for p, e in zip(probs, E64):
-        if p["norb"] == 6:
-            w, _ = oracle.solve_dense(6, 3, 3, p["h"], p["eri"], nroots=p["nroots"])
+        if p["norb"] <= 8:
+            w, _ = oracle.solve_dense(p["norb"], p["nalpha"], p["nbeta"], p["h"], p["eri"], nroots=p["nroots"])
             assert np.abs(e - w).max() < 1e-9
+            checked += 1
+    assert checked >= 4
+
+
+def test_batch_autotuner_reports_every_class():
+    probs = _workload(12, max_norb=10)
+    fg.forte_batch_solve(probs, precision=fg.FORTE_BF16X2, tol=1e-6)
+    tun = fg.forte_batch_tuning()
+    classes = {(p["norb"], p["nalpha"], p["nbeta"]) for p in probs}
+    assert {(t["norb"], t["nalpha"], t["nbeta"]) for t in tun} == classes
+    for t in tun:
+        assert t["threads"] in (128, 256, 512) and t["tile"] in (16, 32, 64) and t["sigma_ms"] > 0
+
+
+@pytest.mark.parametrize("name", ["cas1010_seed5_3roots", "cas1212_seed1_4roots"])
+def test_batch_matches_stored_oracle_energies(name):
+    # the stored oracle energies (residual bound below 5e-12 Eh) of CAS(10,10) and
+    # CAS(12,12), solved as members of a batch (three roots each), mixed precision
+    g = json.load(open(os.path.join(HERE, "golden", name + ".json")))
+    h, eri = si.integrals(g["norb"], g["n_l"], g["seed"])
+    small = _workload(6, max_norb=8)
+    probs = small + [dict(norb=g["norb"], nalpha=g["nalpha"], nbeta=g["nbeta"], nroots=3, h=h, eri=eri)]
+    E, st = fg.forte_batch_solve(probs, precision=fg.FORTE_BF16X2, tol=1e-8)
+    assert np.all(st == 0)
+    np.testing.assert_allclose(E[-1], np.array(g["energies"][:3]), rtol=0, atol=1e-10)
 
 
 def test_batch_reports_bad_input():
