@@ -326,6 +326,24 @@ int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int
  * under forte_profile_enable).  Asynchronous on the context stream. */
 int forte_sigma_fp64_noalloc(forte_ctx *ctx, const double *C, double *S, int nvec);
 
+/* Status of the bounded device waits (no counterpart in the paper: failure
+ * reporting of this library).  The tensor-core kernels (alpha-beta, same-spin,
+ * digit-slice sigma and 2-RDM Gram) bound every pipeline wait by a clock budget;
+ * when one expires the CTA raises the context's device status flag, the other
+ * roles stop, the CTA waits (with the fixed default budget) for its own MMAs and
+ * copies in flight, frees its tensor memory and exits -- it never traps the GPU.
+ * forte_get_status synchronises the context stream and returns FORTE_ERR_TIMEOUT
+ * (and clears the flag) when such a wait expired since the last check, else
+ * FORTE_OK; forte_davidson and forte_rdms check it themselves.  The outputs of the
+ * affected call are undefined; the context stays usable. */
+int forte_get_status(forte_ctx *ctx);
+
+/* Clock budget (cycles) of one pipeline wait of the context's tensor-core kernels;
+ * 0 restores the default (4e9 cycles, about two seconds).  Meant for tests of the
+ * failure path: a budget of a few cycles makes the waits expire.  Synchronises the
+ * context stream. */
+int forte_set_wait_budget(forte_ctx *ctx, unsigned long long cycles);
+
 /* Kernel tracing.  While enabled, every kernel this library launches for the
  * context is bracketed by CUDA events on the context stream (on = 1 also
  * clears earlier records; on = 0 stops recording and keeps them). */

@@ -83,6 +83,8 @@ def library():
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
         "forte_sa_gradient": [vp, i, vp, vp, d, vp, vp],
         "forte_sa_energy": [vp, i, vp, vp],
+        "forte_get_status": [vp],
+        "forte_set_wait_budget": [vp, ctypes.c_ulonglong],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
         "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp],
         "forte_profile_enable": [vp, i],
@@ -285,6 +287,15 @@ def forte_sa_energy(ctx, weights):
     out = ctypes.c_double()
     _check(library().forte_sa_energy(ctx, int(w.size), w.ctypes.data, ctypes.byref(out)))
     return out.value
+
+
+def forte_get_status(ctx, allow=()):
+    """FORTE_OK, or FORTE_ERR_TIMEOUT when a bounded device wait expired (raises unless allowed)."""
+    return _check(library().forte_get_status(ctx), allow)
+
+
+def forte_set_wait_budget(ctx, cycles):
+    return _check(library().forte_set_wait_budget(ctx, int(cycles)))
 
 
 def forte_batch_solve(problems, precision=FORTE_FP64, tol=1e-8, max_iter=400, allow_not_converged=False):

@@ -96,6 +96,15 @@ void sym_eig(int k, const double *A, double *w, double *U) {
   }
 }
 
+int err_word_setup(forte_ctx *ctx) {
+  if (!ctx->d_err) FORTE_CUDA_TRY(cudaMalloc(&ctx->d_err, 4 * sizeof(int)));
+  const unsigned long long b = ctx->wait_budget ? ctx->wait_budget : 4000000000ull;
+  const int w[4] = {0, 0, (int)(unsigned)(b & 0xFFFFFFFFull), (int)(unsigned)(b >> 32)};
+  FORTE_CUDA_TRY(cudaMemcpyAsync(ctx->d_err, w, sizeof(w), cudaMemcpyHostToDevice, ctx->stream));
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return FORTE_OK;
+}
+
 // sigma over the whole determinant grid (no restriction applied), FP64-class mode
 int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec) {
   if (ctx->precision == FORTE_FP64) return sigma_fp64(ctx, C, S, nvec);
@@ -712,6 +721,8 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_gT_hi); cudaFree(ctx->d_gT_lo); cudaFree(ctx->d_gT_t32); cudaFree(ctx->d_err);
   cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp); cudaFree(ctx->d_gpair2);
   cudaFree(ctx->d_ozG); cudaFree(ctx->d_ozGa); cudaFree(ctx->d_ozTabT);
+  cudaFree(ctx->d_abPosOf); cudaFree(ctx->d_abStrOf); cudaFree(ctx->d_abTab); cudaFree(ctx->d_abTabL);
+  cudaFree(ctx->d_gTT_hi); cudaFree(ctx->d_gTT_lo);
   cudaFree(ctx->d_csr_val2[0]);
   if (!ctx->same_strings) cudaFree(ctx->d_csr_val2[1]);
   for (int s = 0; s < (ctx->same_strings ? 1 : 2); ++s) {
@@ -848,7 +859,7 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
   if (ctx->precision == FORTE_FP64 || ctx->precision == FORTE_DF32 || ctx->precision == FORTE_OZ64) {
     rc = davidson_run<double>(ctx, nroots, tol, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                               ctx->d_roots, res);
-    if (rc) return rc;
+    if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;  // an expired wait explains the failure
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = res.iters;
   } else {
@@ -860,13 +871,13 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     double tol_in = std::max(tol, ctx->precision == FORTE_TF32 ? 1e-2 : 1e-3);
     rc = davidson_run<float>(ctx, nroots, tol_in, ctx->precision, ctx->d_guess, ctx->nguess, ctx->dv_max_iter,
                              ctx->d_roots, res);
-    if (rc) return rc;
+    if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;
     if ((rc = mixed_status(ctx))) return rc;
     int it_in = res.iters;
     // outer sigma: FP64-class, with the tensor-core alpha-beta term where it applies
     const int outer = oz_ab_supported(ctx) ? FORTE_OZ64 : FORTE_DF32;
     rc = refine_jd(ctx, nroots, tol, ctx->precision, outer, ctx->d_roots, ctx->d_roots, 30, res);
-    if (rc) return rc;
+    if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = it_in + res.iters;
   }
@@ -961,6 +972,19 @@ int forte_sa_energy(const forte_ctx *ctx, int nstates, const double *weights, do
   }
   *E_sa = e;
   return FORTE_OK;
+}
+
+int forte_set_wait_budget(forte_ctx *ctx, unsigned long long cycles) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  ctx->wait_budget = cycles;
+  return err_word_setup(ctx);
+}
+
+int forte_get_status(forte_ctx *ctx) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  FORTE_CUDA_TRY(cudaGetLastError());
+  return mixed_status(ctx);
 }
 
 int forte_get_counters(const forte_ctx *ctx, long long *fp64, long long *mixed) {

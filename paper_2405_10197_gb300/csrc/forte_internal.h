@@ -112,7 +112,17 @@ struct forte_ctx {
   // gT[rs][pq] = (pq|rs) split into BF16 hi + lo, and rounded to TF32
   uint16_t *d_gT_hi = nullptr, *d_gT_lo = nullptr;
   float *d_gT_t32 = nullptr;
-  int *d_err = nullptr;         // device status word of bounded waits (0 = ok)
+  int *d_err = nullptr;         // device status of bounded waits: [0] flag (0 = ok), [2..3] wait budget
+  unsigned long long wait_budget = 0;  // clock cycles of one pipeline wait (0: the default)
+  // beta-string positions of the tensor-core alpha-beta kernel: strings grouped by a
+  // linear 5-bit hash of their masks, one string per hash value in each aligned group
+  // of 32 positions, so that the scatter of one warp meets 32 distinct banks
+  long long ab_NBpos = 0;       // positions (multiple of 32); padding has no string
+  uint16_t *d_abPosOf = nullptr;  // [N_beta]: position of each beta string
+  int *d_abStrOf = nullptr;       // [ab_NBpos]: string at each position, -1 for padding
+  uint16_t *d_abTab = nullptr;    // [tiles * 128][128]: position of E_rs (string at pos) | sign << 14
+  uint16_t *d_abTabL = nullptr;   // the same entries lane-contiguous: [tiles][4][16 chunks][32 lanes][8]
+  uint16_t *d_gTT_hi = nullptr, *d_gTT_lo = nullptr;  // [npair][128]: gT transposed (pair-major)
   // dense same-spin string Hamiltonians for the tensor-core same-spin sigma,
   // [N][N padded to 16] per spin (aliases when alpha and beta strings coincide)
   uint16_t *d_hd_hi[2] = {nullptr, nullptr}, *d_hd_lo[2] = {nullptr, nullptr};
@@ -227,6 +237,8 @@ int sigma_mixed(forte_ctx *ctx, const double *C, double *S, int nvec, int mode);
 int sigma_mixed(forte_ctx *ctx, const float *C, float *S, int nvec, int mode);  // FP32 vectors
 int mixed_setup(forte_ctx *ctx);
 int mixed_status(forte_ctx *ctx);
+// Allocate the device status array of the bounded waits (once) and write the wait budget.
+int err_word_setup(forte_ctx *ctx);
 
 // vec_kernels.cu: Davidson building blocks on FP64 vectors and on the FP32 vectors
 // of the reduced-precision phase (HBM-bound; FP32 ones accumulate per warp in

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(&tempty[i], OZ_EPI_WARPS);
     }
     mbar_init(rowbar, OZ_PROD_WARPS);
-    *sAbort = 0;
+    abort_word_init(sAbort, err);
     fence_mbar_init();
   }
   if (tid < 128) {
@@ -362,9 +362,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       for (int kc = 0; kc < nchunk; ++kc, ++it) {
         const int st = (int)(it & 1);
-        if (it >= 2 && !mbar_wait_ab(&empty[st], (uint32_t)(((it >> 1) - 1) & 1), sAbort)) {
+        if (it >= 2 && !__all_sync(0xffffffffu, mbar_wait_ab(&empty[st], (uint32_t)(((it >> 1) - 1) & 1), sAbort))) {
           *sAbort = 1;
-          atomicExch(err, 1);
+          atomicOr(err, 8);
           ok = false;
           break;
         }
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const int st = (int)(it & 1);
         if (!mbar_wait_ab(&full[st], (uint32_t)((it >> 1) & 1), sAbort)) {
           *sAbort = 1;
-          atomicExch(err, 1);
+          atomicOr(err, 8);
           break;
         }
         tc_fence_after();
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         issued = it + 1;
         if (!ok) {
           *sAbort = 1;
-          atomicExch(err, 1);
+          atomicOr(err, 8);
           break;
         }
       }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
            oz_epi_level<8, N>(tbase, lane, q, tfull, tempty, sAbort, acc);
       if (!ok) {
         *sAbort = 1;
-        atomicExch(err, 1);
+        atomicOr(err, 8);
         break;
       }
       if (++nch == OZ_FLUSH || it + 1 == total) {
@@ -589,7 +589,7 @@ static int oz_pad16(int x) { return ((x + 15) / 16) * 16; }
 template <int N>
 static size_t oz_smem(long long NbP) {
   return 1024 + (size_t)OzLayout<N>::OFF_CROW + 8 * (size_t)NbP + 4 * 256 + 128 + 128 + 4 * 128 +
-         8 * (5 + 2 * OZ_SLOTS) + 16;
+         8 * (5 + 2 * OZ_SLOTS) + 32;
 }
 
 static size_t oz_smem_n(int N, long long NbP) {
@@ -649,8 +649,8 @@ int rdm2_oz(forte_ctx *ctx, const double *C, const double *g1, double *g2) {
   FORTE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   const int ncta = (int)std::min<long long>(nsm, NA);
   if (!ctx->d_err) {
-    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_err, sizeof(int)));
-    FORTE_CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    const int rc_err = err_word_setup(ctx);
+    if (rc_err) return rc_err;
   }
   if (!ctx->d_ozT) {
     FORTE_CUDA_TRY(cudaMalloc(&ctx->d_ozT, sizeof(uint16_t) * (size_t)n2 * NbP));

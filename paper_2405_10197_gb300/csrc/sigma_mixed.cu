@@ -7,8 +7,19 @@
 //       A[rs][k]  = s_k (pq_k|rs)            k over L(Ia), the replacements of Ia
 //       B[Jb][k]  = C[J_k][Jb]               gathered rows of C
 //     followed by the signed scatter  sigma[Ia][E_rs Jb] += s F[rs][Jb]  over the
-//     replacement list L(Jb).  A is M=128 (symmetric pairs rs, zero padded),
-//     B is N=128 (a tile of beta strings), K=64 (n_kl <= 64, zero padded).
+//     replacement list L(Jb).  In the MMA the gathered C tile is M=128 (128 beta
+//     strings), the integral block N=112/128 (symmetric pairs rs, zero padded),
+//     K=64 (n_kl <= 64, zero padded).
+//
+// Bank-conflict-free scatter.  The beta strings are placed at "positions": a
+// linear 5-bit hash h(J) = XOR of per-orbital codes over the occupied orbitals
+// sorts them into 32 classes, and position 32 g + c holds the g-th string of
+// class c (positions without a string are padding).  Tiles, the fixed-point
+// accumulator row and the scatter table all use positions.  A replacement flips
+// two occupations, E_rs J = J xor {r, s}, so h(E_rs J) = h(J) xor h({r, s}): for a
+// fixed pair rs the 32 lanes of a warp (32 strings of distinct classes) reach 32
+// distinct classes, i.e. 32 distinct shared-memory banks, and every integer
+// reduction of the scatter is a single wavefront.
 //
 // Operands: FORTE_BF16X2 splits x = hi + lo (hi = RNE_bf16(x), lo = RNE_bf16(x - hi))
 // and forms hi*hi + hi*lo + lo*hi (kind::f16, FP32 accumulate); FORTE_TF32 rounds to
@@ -36,13 +47,19 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <string>
 
 #include "forte_internal.h"
 #include "tc_ptx.cuh"
 
 namespace forte {
 
-constexpr int MX_THREADS = 512;
+// epilogue warps (a multiple of 4: the same number per TMEM lane quarter)
+#ifndef FORTE_AB_EPI_WARPS
+#define FORTE_AB_EPI_WARPS 16
+#endif
+constexpr int MX_EPI = FORTE_AB_EPI_WARPS;
+constexpr int MX_THREADS = (8 + MX_EPI) * 32;  // producers, MMA, set-up, epilogue
 constexpr int MX_TILE_N = 128;
 constexpr int MX_STAGE = 32768;               // one B stage: 32 KB
 
@@ -112,15 +129,21 @@ __device__ __forceinline__ float tf32_rne(float x) {
 }
 __device__ __forceinline__ float tf32_rne(double x) { return (float)rne_drop(x, 42); }
 
+// Besides the row-padded copy it writes the copy in beta positions (row length
+// NBpos, strOf[b] = string at position b, -1 for padding) that the alpha-beta
+// kernel gathers; its rounding is the same.
 template <int MODE, typename TI>
 __global__ void __launch_bounds__(256) k_split_rows(const TI *__restrict__ C, uint16_t *__restrict__ hi,
                                                     uint16_t *__restrict__ lo, float *__restrict__ t32, long long NA,
-                                                    long long NB, long long NBp, unsigned *__restrict__ cmax_bits) {
+                                                    long long NB, long long NBp, unsigned *__restrict__ cmax_bits,
+                                                    const int *__restrict__ strOf, long long NBpos,
+                                                    uint16_t *__restrict__ phi, uint16_t *__restrict__ plo,
+                                                    float *__restrict__ pt32) {
   __shared__ unsigned red[8];
   const long long v = blockIdx.z, row = blockIdx.y;
   const long long b = (long long)blockIdx.x * 256 + threadIdx.x;
   unsigned mx = 0u;
-  if (b < NBp) {
+  if (b < NBp && (hi || t32)) {
     const TI x = b < NB ? C[(v * NA + row) * NB + b] : TI(0);
     mx = __float_as_uint(fabsf((float)x));
     const long long o = (v * NA + row) * NBp + b;
@@ -128,6 +151,15 @@ __global__ void __launch_bounds__(256) k_split_rows(const TI *__restrict__ C, ui
       split_bf16(x, hi[o], lo[o]);
     else
       t32[o] = tf32_rne(x);
+  }
+  if (strOf && b < NBpos) {
+    const int J = strOf[b];
+    const TI x = J >= 0 ? C[(v * NA + row) * NB + J] : TI(0);
+    const long long o = (v * NA + row) * NBpos + b;
+    if (MODE == FORTE_BF16X2)
+      split_bf16(x, phi[o], plo[o]);
+    else
+      pt32[o] = tf32_rne(x);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -151,6 +183,17 @@ __global__ void k_split_g(const double *__restrict__ gpair, int npair, uint16_t 
     hi[i] = bf16_bits(h);
     lo[i] = bf16_bits(rne_drop(x - h, 45));
     t32[i] = (float)rne_drop(x, 42);
+  }
+}
+
+// gTT[pair][rs] = gT[rs][pair] (pair-major copy: the rs values of one pair are contiguous)
+__global__ void k_pair_major(const uint16_t *__restrict__ hi, const uint16_t *__restrict__ lo, int npair,
+                             uint16_t *__restrict__ thi, uint16_t *__restrict__ tlo) {
+  const int total = 128 * npair;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int pr = i / 128, rs = i % 128;
+    thi[i] = hi[rs * npair + pr];
+    tlo[i] = lo[rs * npair + pr];
   }
 }
 
@@ -186,10 +229,35 @@ constexpr int WS_OFF_ACC = WS_OFF_B + WS_STAGES * MX_STAGE;
 // build A[i&1] and the gather rows of item i (`aFull`).  The producers, the MMA
 // thread and the epilogue run their tile rings across item boundaries, so the
 // set-up and the drain of one item overlap the tiles of its neighbours.
+// Shared-memory integer reduction at byte address addr unless en == 0xFFFF (the
+// "no target" marker of the scatter table), without a branch.
+__device__ __forceinline__ void red_add_if(uint32_t addr, int v, uint32_t en) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %2, 65535;\n @p red.shared.add.s32 [%0], %1;\n}\n" ::"r"(addr), "r"(v),
+      "r"(en)
+      : "memory");
+}
+
+// Beta strings enter in positions (see the top of the file).  tabL holds the
+// scatter targets lane-contiguously: entry e of chunk c (8 pairs) of the string at
+// position pos = 128 t + 32 g + lane sits at tabL[(((t * 4 + g) * 16 + c) * 32 + lane) * 8 + e]
+// as (target position) | sign << 14, 0xFFFF when E_rs does not act; posOf[Jb] is
+// the position of string Jb.
+//
+// FORTE_BF16X2: the gathered C tile is staged MN-major (positions contiguous):
+//   stage = [part hi/lo: 16 KB][position half: 8 KB][K row k: 128 B of 64 positions],
+// 128-byte swizzled, so each gathered C row is copied as it is (coalesced loads,
+// conflict-free stores) and the tile is the MMA's A operand in MN-major form.  The
+// integral block is built from the pair-major copy gTT[pair][rs] with coalesced
+// loads.  FORTE_TF32 gathers and transposes the FP32 copy Ct32 into a K-major stage.
+// Chi / Clo / Ct32: the C copies in positions, rows of NBpos.
+// Warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 5-7 item set-up and
+// write-out, 8 .. 8 + MX_EPI - 1 epilogue (MX_EPI / 4 warps per TMEM lane quarter).
 template <int MODE, typename TO>
 __global__ void __launch_bounds__(MX_THREADS, 1)
-    k_ab_mma(const Repl *__restrict__ listA, int nkA, const uint16_t *__restrict__ tabJ, int nN, long long NA,
-             long long NB, long long NBp, const uint16_t *__restrict__ gT_hi, const uint16_t *__restrict__ gT_lo,
+    k_ab_mma(const Repl *__restrict__ listA, int nkA,
+             const uint16_t *__restrict__ tabL, const uint16_t *__restrict__ posOf, int nN, long long NA,
+             long long NB, long long NBpos, const uint16_t *__restrict__ gTT_hi, const uint16_t *__restrict__ gTT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
              const float *__restrict__ Sss, TO *__restrict__ S, long long nitems, int *__restrict__ err) {
@@ -197,9 +265,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   // the swizzle pattern is a function of the shared-space address: align there
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sB = sm + WS_OFF_B;
-  const long long NB4 = (NB + 3) & ~3LL;
-  int *accb = (int *)(sm + WS_OFF_ACC);          // acc[2][NB4]
-  int *sJb = accb + 2 * NB4;                     // gather rows [2][64]
+  const long long NB4 = NBpos;                   // a multiple of 32
+  int *accb = (int *)(sm + WS_OFF_ACC);          // acc[2][NBpos], indexed by position
+  int *sJb = accb + 2 * NB4;                     // gathered strings J_k [2][64]
   uint64_t *bar = (uint64_t *)(((uintptr_t)(sJb + 128) + 15) & ~(uintptr_t)15);
   uint64_t *full = bar, *empty = bar + WS_STAGES, *tfull = bar + 2 * WS_STAGES, *tempty = tfull + WS_ACC;
   uint64_t *aFull = tempty + WS_ACC, *aEmpty = aFull + 2, *accReady = aEmpty + 2, *accDone = accReady + 2;
@@ -209,8 +277,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long nloc = nitems > blockIdx.x ? (nitems - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long vpad = NA * NBp, v64 = NA * NB;
-  const int ntiles = (int)((NB + MX_TILE_N - 1) / MX_TILE_N);
+  const long long vpad = NA * NBpos, v64 = NA * NB;
+  const int ntiles = (int)((NBpos + MX_TILE_N - 1) / MX_TILE_N);
   // fixed-point exponent of vector v (bound |f| <= 1.02 n_kl max|g| max|C|)
   auto sx_of = [&](long long v) -> int {
     const float bound = 1.02f * (float)nkA * gmax * __uint_as_float(cmax_bits[v]);
@@ -219,6 +287,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     return (bound > 0.f) ? min(100, 22 - eb) : 0;
   };
 
+  // K rows k >= n_kl are never written and must read as zero
+  for (int i = tid; i < WS_STAGES * MX_STAGE / 16; i += MX_THREADS) ((uint4 *)sB)[i] = make_uint4(0, 0, 0, 0);
+  fence_proxy_async();
   if (warp == 4) tmem_alloc(sTmem, WS_ACC * MX_TILE_N);
   if (tid == 0) {
     for (int i = 0; i < WS_STAGES; ++i) {
@@ -227,16 +298,16 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     }
     for (int i = 0; i < WS_ACC; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 8);
+      mbar_init(&tempty[i], MX_EPI);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&aFull[i], 3);
       mbar_init(&aEmpty[i], 1);
       mbar_init(&accReady[i], 3);
-      mbar_init(&accDone[i], 8);
+      mbar_init(&accDone[i], MX_EPI);
     }
     mbar_init(drain, 1);
-    *sAbort = 0;
+    abort_word_init(sAbort, err);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -245,7 +316,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   const uint32_t tmem = *sTmem;
   auto fail = [&]() {
     *sAbort = 1;
-    atomicExch(err, 1);
+    atomicOr(err, 1);
   };
 
   if (warp >= 5 && warp < 8) {
@@ -264,9 +335,11 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const int Sx = sx_of(v);
         const float *ss = Sss + v * v64 + Ia * NB;
         TO *out = S + v * v64 + Ia * NB;
+        // padding positions never receive a contribution and stay zero
         for (long long x = st; x < NB; x += 96) {
-          out[x] = (TO)((double)ss[x] + ldexp((double)acc[x], -Sx));
-          acc[x] = 0;
+          const int ps = __ldg(posOf + x);
+          out[x] = (TO)((double)ss[x] + ldexp((double)acc[ps], -Sx));
+          acc[ps] = 0;
         }
       } else {
         for (long long x = st; x < NB4; x += 96) acc[x] = 0;
@@ -274,12 +347,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       if (i >= nloc) continue;
       __syncwarp();
       if (lane == 0) mbar_arrive(&accReady[buf]);
-      // A operand and gather rows of item i, once the MMAs of item i-2 are done
+      // integral operand and gather rows of item i, once the MMAs of item i-2 are done
       if (i >= 2 && !__all_sync(0xffffffffu, mbar_wait_ab(&aEmpty[buf], (uint32_t)(((i - 2) >> 1) & 1), sAbort))) {
         fail();
         break;
       }
-      const long long w = blockIdx.x + i * gridDim.x, Ia = w % NA;
+      const long long Ia = (blockIdx.x + i * gridDim.x) % NA;
       const Repl *la = listA + Ia * nkA;
       uint8_t *sA = sm + buf * MX_A_BYTES;
       if (warp == 5) {
@@ -291,28 +364,27 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       }
       // A[rs][k] = s_k (pq_k|rs), K-major swizzled
       if (MODE == FORTE_BF16X2) {
-        const int k0 = 2 * lane, k1 = 2 * lane + 1;  // k pair of this lane
-        Repl r0{}, r1{};
-        if (k0 < nkA) r0 = la[k0];
-        if (k1 < nkA) r1 = la[k1];
-        for (int rs = warp - 5; rs < 128; rs += 3) {
-          uint32_t wh = 0, wl = 0;
-          if (rs < npair) {
-            if (k0 < nkA) {
-              uint16_t h = gT_hi[rs * npair + r0.pair], l = gT_lo[rs * npair + r0.pair];
-              if (r0.sgn < 0) { h ^= 0x8000u; l ^= 0x8000u; }
-              wh |= h;
-              wl |= l;
-            }
-            if (k1 < nkA) {
-              uint16_t h = gT_hi[rs * npair + r1.pair], l = gT_lo[rs * npair + r1.pair];
-              if (r1.sgn < 0) { h ^= 0x8000u; l ^= 0x8000u; }
-              wh |= (uint32_t)h << 16;
-              wl |= (uint32_t)l << 16;
-            }
+        // lanes over rs (coalesced rows of the pair-major copy), warps over k
+        for (int k = warp - 5; k < 64; k += 3) {
+          int pr = 0;
+          bool neg = false;
+          if (k < nkA) {
+            const Repl r = la[k];
+            pr = r.pair;
+            neg = r.sgn < 0;
           }
-          *(uint32_t *)(sA + swz(rs, 4 * lane)) = wh;
-          *(uint32_t *)(sA + 16384 + swz(rs, 4 * lane)) = wl;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int rs = lane + 32 * q;
+            uint16_t h = 0, l = 0;
+            if (k < nkA && rs < npair) {
+              h = gTT_hi[pr * 128 + rs];
+              l = gTT_lo[pr * 128 + rs];
+              if (neg) { h ^= 0x8000u; l ^= 0x8000u; }
+            }
+            *(uint16_t *)(sA + swz(rs, 2 * k)) = h;
+            *(uint16_t *)(sA + 16384 + swz(rs, 2 * k)) = l;
+          }
         }
       } else {
         for (int idx = st; idx < 128 * 64; idx += 96) {
@@ -331,74 +403,101 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
       if (lane == 0) mbar_arrive(&aFull[buf]);
     }
   } else if (warp < 4) {
-    // ================= producers: B[j][k] = C[J_k][j0 + j], warp p owns columns 32p..32p+31
-    bool ok = true;
-    for (long long i = 0; i < nloc && ok; ++i) {
-      const int buf = (int)(i & 1);
-      if (!mbar_wait_ab(&aFull[buf], (uint32_t)((i >> 1) & 1), sAbort)) {
-        fail();
-        break;
+    if (MODE == FORTE_BF16X2) {
+      // ================= producers: C rows J_k of each tile, copied as they are into the
+      // MN-major stage (K row k = 128 bytes of 64 positions per half) with asynchronous
+      // 16-byte copies: warp w copies rows k = w, w + 4, ...; lanes 0-15 one row and
+      // lanes 16-31 the next, lane c moving positions 8c..8c+7 (chunk c & 7 of half c >> 3),
+      // so the reads are whole row segments and every 128-byte stage row is written in
+      // one go.  Two tiles are in flight per warp: the stage of a tile is announced
+      // (copies complete, proxy fence, arrive) after the next tile's copies are issued.
+      bool ok = true;
+      const int cpos = 8 * (lane & 15);
+      const uint32_t hoff = (uint32_t)(cpos >> 6) * 8192u, cbyte = (uint32_t)(cpos & 63) * 2u;
+      int pending = -1;  // stage whose copies are issued but not yet announced
+      auto announce = [&](int n_in_flight) {
+        if (n_in_flight)
+          asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[pending]);
+      };
+      for (long long i = 0; i < nloc && ok; ++i) {
+        const int buf = (int)(i & 1);
+        if (!__all_sync(0xffffffffu, mbar_wait_ab(&aFull[buf], (uint32_t)((i >> 1) & 1), sAbort))) {
+          fail();
+          break;
+        }
+        const long long v = (blockIdx.x + i * gridDim.x) / NA;
+        const int *sJ = sJb + buf * 64;
+        for (int t = 0; t < ntiles; ++t) {
+          const long long gt = i * ntiles + t;
+          const int s = (int)(gt % WS_STAGES);
+          const long long u = gt / WS_STAGES;
+          if (gt >= WS_STAGES && !__all_sync(0xffffffffu, mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort))) {
+            fail();
+            ok = false;
+            break;
+          }
+          const long long col = (long long)t * MX_TILE_N + cpos;
+          const uint32_t nbytes = col < NBpos ? 16u : 0u;  // zero fill beyond the last position
+          const uint32_t stg = smem_u32(sB + s * MX_STAGE);
+          for (int k = warp + 4 * (lane >> 4); k < nkA; k += 8) {
+            const long long o = (v * NA + sJ[k]) * NBpos + (nbytes ? col : 0);
+            const uint32_t d = stg + hoff + swz((uint32_t)k, cbyte);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(Chi + o), "r"(nbytes)
+                         : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d + 16384u), "l"(Clo + o), "r"(nbytes)
+                         : "memory");
+          }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          if (pending >= 0) announce(1);
+          pending = s;
+        }
+        // the item's last stage before the next item's rows are awaited
+        if (pending >= 0) {
+          announce(0);
+          pending = -1;
+        }
       }
-      const long long v = (blockIdx.x + i * gridDim.x) / NA;
-      const int *sJ = sJb + buf * 64;
-      for (int t = 0; t < ntiles; ++t) {
-        const long long gt = i * ntiles + t;
-        const int s = (int)(gt % WS_STAGES);
-        const long long u = gt / WS_STAGES;
-        const long long col0 = (long long)t * MX_TILE_N + 32 * warp;
-        uint4 g[16];
+      if (pending >= 0) announce(0);  // (an abort between issue and announce)
+    } else {
+      // ================= producers: B[j][k] = C[J_k][j0 + j], warp p owns columns 32p..32p+31
+      bool ok = true;
+      for (long long i = 0; i < nloc && ok; ++i) {
+        const int buf = (int)(i & 1);
+        if (!__all_sync(0xffffffffu, mbar_wait_ab(&aFull[buf], (uint32_t)((i >> 1) & 1), sAbort))) {
+          fail();
+          break;
+        }
+        const long long v = (blockIdx.x + i * gridDim.x) / NA;
+        const int *sJ = sJb + buf * 64;
+        for (int t = 0; t < ntiles; ++t) {
+          const long long gt = i * ntiles + t;
+          const int s = (int)(gt % WS_STAGES);
+          const long long u = gt / WS_STAGES;
+          const long long col0 = (long long)t * MX_TILE_N + 32 * warp;
+          uint4 g[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) g[q] = make_uint4(0, 0, 0, 0);
-        if (MODE == FORTE_BF16X2) {
-#pragma unroll
-          for (int part = 0; part < 2; ++part)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-              const int k = 2 * lane + r;
-              if (k < nkA) {
-                // 32-byte loads (the row base and col0 are 64-byte aligned): half the
-                // L1TEX sector requests of 16-byte ones, each lane reading its own row
-                const uint16_t *src = (part ? Clo : Chi) + v * vpad + (long long)sJ[k] * NBp;
-#pragma unroll
-                for (int c = 0; c < 4; c += 2)
-                  if (col0 + 8 * c < NBp) ldg256(src + col0 + 8 * c, g[part * 8 + r * 4 + c], g[part * 8 + r * 4 + c + 1]);
-              }
-            }
-        } else {
+          for (int q = 0; q < 16; ++q) g[q] = make_uint4(0, 0, 0, 0);
 #pragma unroll
           for (int atom = 0; atom < 2; ++atom) {
             const int k = 32 * atom + lane;
             if (k < nkA) {
-              const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBp;
+              const float *src = Ct32 + v * vpad + (long long)sJ[k] * NBpos;
 #pragma unroll
               for (int c = 0; c < 8; c += 2)
-                if (col0 + 4 * c < NBp) ldg256(src + col0 + 4 * c, g[atom * 8 + c], g[atom * 8 + c + 1]);
+                if (col0 + 4 * c < NBpos) ldg256(src + col0 + 4 * c, g[atom * 8 + c], g[atom * 8 + c + 1]);
             }
           }
-        }
-        if (gt >= WS_STAGES && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
-          fail();
-          ok = false;
-          break;
-        }
-        uint8_t *stg = sB + s * MX_STAGE;
-        if (MODE == FORTE_BF16X2) {
-#pragma unroll
-          for (int part = 0; part < 2; ++part) {
-            uint8_t *dst = stg + part * 16384;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const uint4 qa = g[part * 8 + c], qb = g[part * 8 + 4 + c];
-              const uint32_t ea[4] = {qa.x, qa.y, qa.z, qa.w}, ebb[4] = {qb.x, qb.y, qb.z, qb.w};
-#pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const uint32_t lo16 = (q & 1) ? (ea[q >> 1] >> 16) : (ea[q >> 1] & 0xFFFFu);
-                const uint32_t hi16 = (q & 1) ? (ebb[q >> 1] >> 16) : (ebb[q >> 1] & 0xFFFFu);
-                *(uint32_t *)(dst + swz(32 * warp + 8 * c + q, 4 * lane)) = lo16 | (hi16 << 16);
-              }
-            }
+          if (gt >= WS_STAGES && !__all_sync(0xffffffffu, mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort))) {
+            fail();
+            ok = false;
+            break;
           }
-        } else {
+          uint8_t *stg = sB + s * MX_STAGE;
 #pragma unroll
           for (int atom = 0; atom < 2; ++atom) {
             uint8_t *dst = stg + atom * 16384;
@@ -411,19 +510,21 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
               *(uint32_t *)(dst + swz(32 * warp + 4 * c + 3, 4 * lane)) = q.w;
             }
           }
+          fence_proxy_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&full[s]);
         }
-        fence_proxy_async();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[s]);
       }
     }
   } else if (warp == 4) {
     // ================= MMA issuer
     if (lane == 0) {
       // D[j][rs] = sum_k B[j][k] A[rs][k]: the gathered C tile is the M=128 operand,
-      // the integral block the N=nN operand, so TMEM lanes are beta strings
+      // the integral block the N=nN operand, so TMEM lanes are beta positions.
+      // BF16X2: the C tile is MN-major (transpose bit 15 of the instruction descriptor)
       const uint32_t idesc = (MODE == FORTE_BF16X2)
-                                 ? ((1u << 4) | (1u << 7) | (1u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24))
+                                 ? ((1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (((uint32_t)nN >> 3) << 17) |
+                                    ((128u >> 4) << 24))
                                  : ((1u << 4) | (2u << 7) | (2u << 10) | (((uint32_t)nN >> 3) << 17) | ((128u >> 4) << 24));
       bool ok = true;
       for (long long i = 0; i < nloc && ok; ++i) {
@@ -445,17 +546,20 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           }
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(b * MX_TILE_N);
-          // descriptors of the operand bases; offsets in 16-byte units
-          const uint64_t bd = desc_kmajor_sw128(smem_u32(sB + s * MX_STAGE)), ad = desc_kmajor_sw128(a0);
+          const uint64_t ad = desc_kmajor_sw128(a0);
           if (MODE == FORTE_BF16X2) {
-            // hi*hi + lo*hi + hi*lo  (C part first, integral part second)
+            // hi*hi + lo*hi + hi*lo  (C part first, integral part second); offsets in
+            // 16-byte units: C part 16 KB, integral part 16 KB; a K step of 16 is
+            // 16 C rows (2048 bytes) and 32 bytes of each integral row
+            const uint64_t cd = desc_mnmajor_sw128(smem_u32(sB + s * MX_STAGE), 8192u);
             constexpr uint32_t coff[3] = {0u, 1024u, 0u}, goff[3] = {0u, 0u, 1024u};
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
               for (int ks = 0; ks < 4; ++ks)
-                mma_issue<MODE>(d, bd + (coff[p] + 2u * ks), ad + (goff[p] + 2u * ks), idesc, (p | ks) != 0);
+                mma_issue<MODE>(d, cd + (coff[p] + 128u * ks), ad + (goff[p] + 2u * ks), idesc, (p | ks) != 0);
           } else {
+            const uint64_t bd = desc_kmajor_sw128(smem_u32(sB + s * MX_STAGE));
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
               const uint32_t off = (uint32_t)(ks >> 2) * 1024u + 2u * (ks & 3);
@@ -471,16 +575,19 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ================= epilogue: thread = beta string j0 + j (accumulator lane),
-    //                   nN/2 pairs rs per warp half (accumulator columns)
-    const int e = warp - 8, lg = e & 3, half = e >> 2;
-    const int j = lg * 32 + lane;
-    const int hc = nN >> 1, nq = hc >> 3;
+    // ================= epilogue: thread = beta position 128 t + 32 lg + lane (accumulator
+    //                   lane); the MX_EPI / 4 warps of a lane quarter split the chunks of 8
+    //                   pairs rs (accumulator columns) c0 .. c1-1
+    constexpr int PER_Q = MX_EPI / 4;                       // warps per lane quarter
+    constexpr int MAXQ = (16 + PER_Q - 1) / PER_Q;          // chunks per warp, at most
+    const int e = warp - 8, lg = warp & 3, part = e >> 2;
+    const int nch = nN >> 3, c0 = part * nch / PER_Q, c1 = (part + 1) * nch / PER_Q, nq = c1 - c0;
     bool ok = true;
     for (long long i = 0; i < nloc && ok; ++i) {
       const int buf = (int)(i & 1);
       int *acc = accb + buf * NB4;
       const float fscale = ldexpf(1.f, sx_of((blockIdx.x + i * gridDim.x) / NA));
+      const uint32_t acc_s = smem_u32(acc);
       if (!__all_sync(0xffffffffu, mbar_wait_ab(&accReady[buf], (uint32_t)((i >> 1) & 1), sAbort))) {
         fail();
         break;
@@ -489,15 +596,20 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const long long gt = i * ntiles + t;
         const int b = (int)(gt % WS_ACC);
         const long long ub = gt / WS_ACC;
-        const long long Jb = (long long)t * MX_TILE_N + j;
-        uint4 tg[8];
+        uint4 tg[MAXQ];
+        {
+          // this warp's chunks of 8 pairs: 32 lanes read 512 contiguous bytes each
+          const uint4 *rowq = (const uint4 *)tabL + ((long long)(t * 4 + lg) * 16 + c0) * 32 + lane;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) tg[q] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-        if (Jb < NB) {
-          const uint4 *row = (const uint4 *)(tabJ + Jb * 128 + half * hc);
+          for (int q = 0; q < MAXQ; ++q)
+            tg[q] = (q < nq) ? __ldg(rowq + q * 32) : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+          // the next tile's entries into L1 now: they are L2 hits (the table depends
+          // on the tile only), and an L2 round trip per tile stalled the scatter
+          const int tn = (t + 1 < ntiles) ? t + 1 : 0;
+          const uint4 *nxt = (const uint4 *)tabL + ((long long)(tn * 4 + lg) * 16 + c0) * 32 + lane;
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (q < nq) tg[q] = __ldg(row + q);
+          for (int q = 0; q < MAXQ; ++q)
+            if (q < nq) asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt + q * 32));
         }
         if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
           fail();
@@ -505,40 +617,34 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + half * hc);
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * MX_TILE_N + 8 * c0);
         // all of this warp's columns in one round trip, then the accumulator is released
         // before the scatter (a load / wait per 8-column block left the warps waiting on
         // tensor-memory latency and the MMA thread waiting on them)
-        uint32_t ra[32], rb[32];
-        tmem_ld32(taddr, ra);
-        if (hc == 64) {
-          tmem_ld32(taddr + 32, rb);
-        } else {
-          tmem_ld16(taddr + 32, rb);
-          tmem_ld8(taddr + 48, rb + 16);
-        }
+        uint32_t ra[8 * MAXQ];
+#pragma unroll
+        for (int q = 0; q < MAXQ; ++q)
+          if (q < nq) tmem_ld8(taddr + 8 * q, ra + 8 * q);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[b]);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < MAXQ; ++q) {
           if (q >= nq) break;
           const uint4 tq = tg[q];
           const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const uint32_t en = (c & 1) ? (wv[c >> 1] >> 16) : (wv[c >> 1] & 0xFFFFu);
-            const uint32_t rv = q < 4 ? ra[8 * q + c] : rb[8 * (q - 4) + c];
+            const uint32_t rv = ra[8 * q + c];
             // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
             // conversion instruction, which would run on the narrow FP64 /
-            // conversion pipe.  The reduction is skipped (not predicated) for
-            // invalid entries: issued reductions, even predicated off, are what
-            // limits this loop.
-            if (en != 0xFFFFu) {
-              const float tv = fmaf(__uint_as_float(rv), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
-              atomicAdd(&acc[en & 0x3FFFu], __float_as_int(tv) - 0x4B400000);
-            }
+            // conversion pipe.  The reduction is predicated, not branched: with the
+            // conflict-free positions a reduction costs one wavefront whatever its
+            // lane mask, and a divergent branch per column stalled the warps.
+            const float tv = fmaf(__uint_as_float(rv), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
+            red_add_if(acc_s + ((en & 0x3FFFu) << 2), __float_as_int(tv) - 0x4B400000, en);
           }
         }
       }
@@ -559,9 +665,88 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 
 // ------------------------------------------------------------ host side
 
-static size_t mx_smem_bytes(long long NB) {
-  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)((NB + 3) & ~3LL) + 2 * 64 * 4 + 16 +
+static size_t mx_smem_bytes(long long NBpos) {
+  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)NBpos + 2 * 64 * 4 + 16 +
          8 * (2 * WS_STAGES + 2 * WS_ACC + 9) + 16 + 64;
+}
+
+static uint64_t splitmix64_next(uint64_t &state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Beta-string positions of the alpha-beta kernel (see the top of the file).  The
+// per-orbital 5-bit codes are drawn from a fixed-seed generator; of 1024 draws the
+// one whose largest hash class is smallest is kept (fewest padding positions; at
+// CAS(14,14) 3584 positions for 3432 strings).
+static int ab_positions(forte_ctx *ctx) {
+  if (ctx->d_abTab) return FORTE_OK;
+  const SpinHost &B = ctx->sh[ctx->same_strings ? 0 : 1];
+  const int n = ctx->n;
+  const long long NB = B.N;
+  std::vector<unsigned> hs((size_t)NB);
+  unsigned best[32] = {0};
+  long long bestG = -1;
+  uint64_t state = 0x2405101970000000ull;
+  for (int trial = 0; trial < 1024; ++trial) {
+    unsigned code[32];
+    for (int p = 0; p < n; ++p) code[p] = (unsigned)(splitmix64_next(state) >> 59);
+    long long cnt[32] = {0}, G = 0;
+    for (long long J = 0; J < NB; ++J) {
+      unsigned h = 0;
+      for (uint32_t m = B.str[J]; m; m &= m - 1) h ^= code[__builtin_ctz(m)];
+      G = std::max(G, ++cnt[h]);
+    }
+    if (bestG < 0 || G < bestG) {
+      bestG = G;
+      std::copy(code, code + 32, best);
+    }
+  }
+  const long long NBpos = 32 * bestG;
+  if (NBpos > 0x3FFF) {
+    set_error("alpha-beta MMA kernel: %lld beta positions exceed the 14-bit scatter table", NBpos);
+    return FORTE_ERR_ARG;
+  }
+  std::vector<uint16_t> posOf((size_t)NB);
+  std::vector<int> strOf((size_t)NBpos, -1);
+  long long next[32] = {0};
+  for (long long J = 0; J < NB; ++J) {
+    unsigned h = 0;
+    for (uint32_t m = B.str[J]; m; m &= m - 1) h ^= best[__builtin_ctz(m)];
+    const long long pos = 32 * next[h]++ + h;
+    posOf[J] = (uint16_t)pos;
+    strOf[pos] = (int)J;
+  }
+  const long long rows = (NBpos + MX_TILE_N - 1) / MX_TILE_N * MX_TILE_N;
+  std::vector<uint16_t> tab((size_t)rows * 128, 0xFFFFu);
+  for (long long pos = 0; pos < NBpos; ++pos) {
+    const int J = strOf[pos];
+    if (J < 0) continue;
+    for (int e = 0; e < B.nk; ++e) {
+      const Repl &r = B.list[(size_t)J * B.nk + e];
+      tab[(size_t)pos * 128 + r.pair] = (uint16_t)(posOf[r.J] | (r.sgn < 0 ? 0x4000 : 0));
+    }
+  }
+  // the same entries lane-contiguous for the epilogue's coalesced loads
+  std::vector<uint16_t> tabL(tab.size(), 0xFFFFu);
+  for (long long pos = 0; pos < rows; ++pos) {
+    const long long t = pos / 128, g = (pos % 128) / 32, ln = pos % 32;
+    for (int c = 0; c < 16; ++c)
+      for (int e = 0; e < 8; ++e)
+        tabL[(size_t)((((t * 4 + g) * 16 + c) * 32 + ln) * 8 + e)] = tab[(size_t)pos * 128 + c * 8 + e];
+  }
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abTabL, sizeof(uint16_t) * tabL.size()));
+  FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abTabL, tabL.data(), sizeof(uint16_t) * tabL.size(), cudaMemcpyHostToDevice));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abPosOf, sizeof(uint16_t) * posOf.size()));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abStrOf, sizeof(int) * strOf.size()));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abTab, sizeof(uint16_t) * tab.size()));
+  FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abPosOf, posOf.data(), sizeof(uint16_t) * posOf.size(), cudaMemcpyHostToDevice));
+  FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abStrOf, strOf.data(), sizeof(int) * strOf.size(), cudaMemcpyHostToDevice));
+  FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abTab, tab.data(), sizeof(uint16_t) * tab.size(), cudaMemcpyHostToDevice));
+  ctx->ab_NBpos = NBpos;
+  return FORTE_OK;
 }
 
 int mixed_setup(forte_ctx *ctx) {
@@ -575,12 +760,18 @@ int mixed_setup(forte_ctx *ctx) {
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_lo, cnt * sizeof(uint16_t)));
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gT_t32, cnt * sizeof(float)));
   if (!ctx->d_err) {
-    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_err, sizeof(int)));
-    FORTE_CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    const int rc_err = err_word_setup(ctx);
+    if (rc_err) return rc_err;
   }
   k_split_g<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_gpair, np, ctx->d_gT_hi, ctx->d_gT_lo,
                                                                     ctx->d_gT_t32);
   FORTE_LAUNCH_CHECK();
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gTT_hi, cnt * sizeof(uint16_t)));
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_gTT_lo, cnt * sizeof(uint16_t)));
+  k_pair_major<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ctx->d_gT_hi, ctx->d_gT_lo, np, ctx->d_gTT_hi,
+                                                                       ctx->d_gTT_lo);
+  FORTE_LAUNCH_CHECK();
+  if (ctx->sh[0].nk > 0 && ctx->sh[ctx->same_strings ? 0 : 1].nk > 0) return ab_positions(ctx);
   return FORTE_OK;
 }
 
@@ -607,7 +798,11 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   // + the transposed copies of the tensor-core same-spin GEMM (4 bytes per element)
   const bool ssm = ss_mma_supported(ctx);
   const size_t ntw = ssm ? (size_t)nvec * NB * ((NA + 15) & ~15LL) * 4 : 0;
-  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + ntw + 1024 + 512 + sizeof(unsigned) * nvec;
+  // the C copy in beta positions for the alpha-beta kernel (4 bytes per element)
+  const long long NBpos = ctx->ab_NBpos;
+  const bool ab = nkA > 0 && nkB > 0;
+  const size_t npos = ab ? (size_t)nvec * NA * NBpos : 0;
+  const size_t bytes = 4 * nf * sizeof(float) + np * 4 + ntw + npos * 4 + 1536 + 512 + sizeof(unsigned) * nvec;
   if ((rc = ctx->sc_mixed.ensure(bytes))) return rc;
   float *C32 = (float *)ctx->sc_mixed.ptr;
   // the FP32 copy of C feeds only the CSR fallback of the same-spin term
@@ -618,22 +813,39 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   uint16_t *Chi = (uint16_t *)tc, *Clo = Chi + np;
   float *Ct32 = (float *)tc;
   uint8_t *tw = (uint8_t *)(((uintptr_t)(tc + np * 4) + 255) & ~(uintptr_t)255);
-  unsigned *cmax = (unsigned *)(((uintptr_t)(tw + ntw) + 255) & ~(uintptr_t)255);
+  uint8_t *tp = (uint8_t *)(((uintptr_t)(tw + ntw) + 255) & ~(uintptr_t)255);
+  uint16_t *Phi = ab ? (uint16_t *)tp : nullptr, *Plo = ab ? Phi + npos : nullptr;
+  float *Pt32 = ab ? (float *)tp : nullptr;
+  const int *strOf = ab ? ctx->d_abStrOf : nullptr;
+  unsigned *cmax = (unsigned *)(((uintptr_t)(tp + npos * 4) + 255) & ~(uintptr_t)255);
   FORTE_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(unsigned) * nvec, st));
   {
     const long long per = NA * NBp;
     dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
-    if (!C32w) {  // no FP32 copy wanted: the row kernel
-      dim3 g2((unsigned)((NBp + 255) / 256), (unsigned)NA, (unsigned)nvec);
+    const long long wcols = std::max(NBp, ab ? NBpos : 0LL);
+    dim3 g2((unsigned)((wcols + 255) / 256), (unsigned)NA, (unsigned)nvec);
+    if (!C32w) {  // no FP32 copy wanted: the row kernel writes both copies
       if (mode == FORTE_BF16X2)
-        k_split_rows<FORTE_BF16X2, T><<<g2, 256, 0, st>>>(C, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+        k_split_rows<FORTE_BF16X2, T><<<g2, 256, 0, st>>>(C, Chi, Clo, nullptr, NA, NB, NBp, cmax, strOf, NBpos, Phi,
+                                                          Plo, nullptr);
       else
-        k_split_rows<FORTE_TF32, T><<<g2, 256, 0, st>>>(C, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
-    } else if (mode == FORTE_BF16X2) {
-      k_split<FORTE_BF16X2, T><<<grid, 256, 0, st>>>(C, C32w, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+        k_split_rows<FORTE_TF32, T><<<g2, 256, 0, st>>>(C, nullptr, nullptr, Ct32, NA, NB, NBp, cmax, strOf, NBpos,
+                                                        nullptr, nullptr, Pt32);
     } else {
-      k_split<FORTE_TF32, T><<<grid, 256, 0, st>>>(C, C32w, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+      if (mode == FORTE_BF16X2)
+        k_split<FORTE_BF16X2, T><<<grid, 256, 0, st>>>(C, C32w, Chi, Clo, nullptr, NA, NB, NBp, cmax);
+      else
+        k_split<FORTE_TF32, T><<<grid, 256, 0, st>>>(C, C32w, nullptr, nullptr, Ct32, NA, NB, NBp, cmax);
+      FORTE_LAUNCH_CHECK();
+      if (ab) {  // positional copy only (the row copy is written above)
+        if (mode == FORTE_BF16X2)
+          k_split_rows<FORTE_BF16X2, T><<<g2, 256, 0, st>>>(C, nullptr, nullptr, nullptr, NA, NB, NBp, cmax, strOf,
+                                                            NBpos, Phi, Plo, nullptr);
+        else
+          k_split_rows<FORTE_TF32, T><<<g2, 256, 0, st>>>(C, nullptr, nullptr, nullptr, NA, NB, NBp, cmax, strOf,
+                                                          NBpos, nullptr, nullptr, Pt32);
+      }
     }
     FORTE_LAUNCH_CHECK();
   }
@@ -642,9 +854,9 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   else
     rc = same_spin_f32(ctx, C32r, S32, T1, T2, nvec);
   if (rc) return rc;
-  if (nkA > 0 && nkB > 0) {
+  if (ab) {
     const int nN = ctx->npair <= 112 ? 112 : 128;
-    const size_t smem = mx_smem_bytes(NB);
+    const size_t smem = mx_smem_bytes(NBpos);
     if (smem > 232448) {
       set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;
@@ -656,16 +868,16 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
     if (mode == FORTE_BF16X2) {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2, T>));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
-      k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
-                                                             ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                             ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, nitems, ctx->d_err);
+      k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(
+          ctx->sd[0].list, nkA, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
+          ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, Phi, Plo, nullptr, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32, T>));
       FORTE_PROF(ctx, "ab_mma_tf32");
-      k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, ctx->sd[1].tabJ, nN, NA, NB, NBp,
-                                                           ctx->d_gT_hi, ctx->d_gT_lo, ctx->d_gT_t32, ctx->npair,
-                                                           ctx->gmax, cmax, Chi, Clo, Ct32, S32, S, nitems, ctx->d_err);
+      k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(
+          ctx->sd[0].list, nkA, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
+          ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, nullptr, nullptr, Pt32, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     }
   } else if (sizeof(T) == 8) {
@@ -694,7 +906,12 @@ int mixed_status(forte_ctx *ctx) {
   FORTE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   if (h) {
     cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream);
-    set_error("a bounded device wait in the alpha-beta MMA kernel expired");
+    // one bit per kernel (the value each kernel ORs into the flag)
+    std::string who;
+    const char *names[4] = {"alpha-beta MMA", "same-spin MMA", "digit-slice alpha-beta", "digit-slice 2-RDM Gram"};
+    for (int b = 0; b < 4; ++b)
+      if (h & (1 << b)) who += (who.empty() ? "" : ", ") + std::string(names[b]);
+    set_error("a bounded device wait expired in: %s", who.c_str());
     return FORTE_ERR_TIMEOUT;
   }
   return FORTE_OK;

@@ -64,7 +64,7 @@ static_assert(ZB_ACOL + OZ_DIGITS * 32 <= 512, "tensor memory budget");
 
 static size_t zb_smem_bytes(long long NB) {
   return 1024 + (size_t)ZB_OFF_ROW + 3 * sizeof(uint32_t) * (size_t)NB + 16 + 8 * (2 * ZB_NSTAGE + 2 * ZB_SLOTS + 5) +
-         16;
+         32;
 }
 
 // ------------------------------------------------------------ C digits
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(ZB_THREADS, 1)
     mbar_init(accReady, 3);
     mbar_init(accDone, 16);
     mbar_init(drain, 1);
-    *sAbort = 0;
+    abort_word_init(sAbort, err);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(ZB_THREADS, 1)
   const uint32_t a_t = tmem + ZB_ACOL;  // A (integral digits) columns
   auto fail = [&]() {
     *sAbort = 1;
-    atomicExch(err, 1);
+    atomicOr(err, 4);
   };
 
   if (warp >= 5 && warp < 8) {
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(ZB_THREADS, 1)
         const long long gt = i * ntiles + t;
         const int s = (int)(gt % ZB_NSTAGE);
         const long long u = gt / ZB_NSTAGE;
-        if (gt >= ZB_NSTAGE && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
+        if (gt >= ZB_NSTAGE && !__all_sync(0xffffffffu, mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort))) {
           fail();
           ok = false;
           break;
@@ -535,8 +535,8 @@ static int oz_ab_setup(forte_ctx *ctx) {
   FORTE_CUDA_TRY(cudaMemcpy(ctx->d_ozG, gd.data(), sizeof(uint16_t) * gd.size(), cudaMemcpyHostToDevice));
   FORTE_CUDA_TRY(cudaMemcpy(ctx->d_ozGa, ga.data(), sizeof(int) * 128, cudaMemcpyHostToDevice));
   if (!ctx->d_err) {
-    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_err, sizeof(int)));
-    FORTE_CUDA_TRY(cudaMemset(ctx->d_err, 0, sizeof(int)));
+    const int rc_err = err_word_setup(ctx);
+    if (rc_err) return rc_err;
   }
   return FORTE_OK;
 }

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(SSM_THREADS, 1)
       mbar_init(&tempty[i], 4);
     }
     mbar_init(drain, 1);
-    *sAbort = 0;
+    abort_word_init(sAbort, err);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(SSM_THREADS, 1)
           const long long u = it / Cf::NSTAGE;
           if (it >= Cf::NSTAGE && !mbar_wait_ab(&empty[s], (uint32_t)((u - 1) & 1), sAbort)) {
             *sAbort = 1;
-            atomicExch(err, 1);
+            atomicOr(err, 2);
             ok = false;
             break;
           }
@@ -131,6 +131,12 @@ __global__ void __launch_bounds__(SSM_THREADS, 1)
             }
           }
         }
+      }
+      if (!ok) {
+        // let the copies already issued land before the CTA can exit (stages not
+        // yet reused, so the parity of their last phase is still current)
+        for (long long g = it > Cf::NSTAGE ? it - Cf::NSTAGE : 0; g < it; ++g)
+          mbar_wait(&full[g % Cf::NSTAGE], (uint32_t)((g / Cf::NSTAGE) & 1));
       }
     }
     __syncwarp();
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(SSM_THREADS, 1)
       }
       if (!ok) {
         *sAbort = 1;
-        atomicExch(err, 1);
+        atomicOr(err, 2);
       }
     }
     __syncwarp();
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(SSM_THREADS, 1)
       const int b = lt & 1, ub = lt >> 1;
       if (!__all_sync(0xffffffffu, mbar_wait_ab(&tfull[b], (uint32_t)(ub & 1), sAbort))) {
         *sAbort = 1;
-        atomicExch(err, 1);
+        atomicOr(err, 2);
         break;
       }
       tc_fence_after();

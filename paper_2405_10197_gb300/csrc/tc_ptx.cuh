@@ -11,7 +11,9 @@
 
 namespace forte {
 
-// Clock budget of one bounded mbarrier wait (about two seconds at 2 GHz).
+// Clock budget of one bounded mbarrier wait (about two seconds at 2 GHz): the
+// default of the pipeline waits and the fixed budget of the waits that drain a
+// CTA's own MMAs and copies before it exits.
 constexpr unsigned long long MX_WAIT_CYCLES = 4000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -154,6 +156,20 @@ __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor: MN-major operand, 128-byte swizzle.  Rows of
+// 128 bytes hold 64 consecutive M (or N) elements of one K index; 8 consecutive
+// K rows form a 1024-byte swizzle atom (SBO = 1024 to the next 8 K rows) and the
+// next 64 M elements start LBO bytes further.
+__device__ __forceinline__ uint64_t desc_mnmajor_sw128(uint32_t saddr, uint32_t lbo_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;  // LBO: next 64 M elements
+  d |= (uint64_t)(1024 >> 4) << 32;                    // SBO: next 8 K rows
+  d |= (uint64_t)1 << 46;                              // version
+  d |= (uint64_t)2 << 61;                              // SWIZZLE_128B
+  return d;
+}
+
 // Byte offset of (row, byte-in-row) inside a K-major 128B-swizzled block of rows.
 __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t b) {
   return (row >> 3) * 1024u + (row & 7u) * 128u + ((((b >> 4) ^ (row & 7u)) & 7u) << 4) + (b & 15u);
@@ -162,12 +178,23 @@ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t b) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
-// Bounded wait that also gives up once another warp raised the abort flag.
+// Per-CTA abort word in shared memory: [0] the abort flag, [1], [2] the clock budget
+// of one pipeline wait (low, high 32 bits), copied at kernel start from words 2 and 3
+// of the context's device status array (word 0 there is the status flag).
+__device__ __forceinline__ void abort_word_init(volatile int *abort_word, const int *err) {
+  abort_word[0] = 0;
+  abort_word[1] = err[2];
+  abort_word[2] = err[3];
+}
+// Bounded pipeline wait: gives up when another warp raised the abort flag or when
+// the budget of the abort word runs out.
 __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  const unsigned long long budget =
+      ((unsigned long long)(unsigned)abort_flag[2] << 32) | (unsigned long long)(unsigned)abort_flag[1];
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if ((unsigned long long)(clock64() - t0) > MX_WAIT_CYCLES) return false;
+    if ((unsigned long long)(clock64() - t0) > budget) return false;
   }
   return true;
 }
