@@ -387,7 +387,10 @@ def run_ours(args):
         it = {args.precision: dav[-1]["iterations"]}
         for name, c in ttl["cmp"].items():
             ms[name], err[name], it[name] = _sig(c["ms"]), _sig(c["err"], 2), c["it"]
-        ttl_line = {"ref": ttl["ref"], "gap": ttl["gap"], "ms": ms, "err": err, "it": it}
+        # DL: Davidson-Liu with the mode's sigma; DL+JD: Davidson-Liu with the reduced sigma,
+        # then Jacobi-Davidson with the FP64-class sigma (details: "solvers")
+        ttl_line = {"ref": ttl["ref"], "gap": ttl["gap"], "ms": ms, "err": err, "it": it,
+                    "solver": {k: ("DL" if k in ("fp64", "df32", "oz64") else "DL+JD") for k in ms}}
     out = {
         "metric": METRIC, "value": value, "unit": "det/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -709,8 +712,11 @@ def run_configs(args):
         cfg = si.CAS88
         h, eri = si.integrals(8, cfg["n_l"], cfg["seed"])
         t0 = time.perf_counter()
-        oracle.davidson(8, 4, 4, h, eri, nroots=1, tol=1e-10)
+        _, _, _, it_or = oracle.davidson(8, 4, 4, h, eri, nroots=1, tol=1e-10)
         orc["C0_davidson_1e-10_s"] = time.perf_counter() - t0
+        # the same textbook Davidson-Liu (reading 6) on the same input: iteration counts
+        orc["C0_davidson_1e-10_iterations"] = {"oracle": int(it_or),
+                                               "gpu_fp64": int(c0["davidson_1e-10"]["fp64"]["iterations"])}
         lines.append(orc)
     for ln in lines:
         print(json.dumps(ln))
