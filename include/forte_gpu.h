@@ -127,8 +127,11 @@ int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
  * kept determinants: entries of C outside count as zero, those of S are zero),
  * forte_davidson solves P H P in the kept space, and stored guesses are
  * projected.  Vectors keep the full [N_alpha][N_beta] layout, zero outside.
- * The RDM calls act on whatever vectors they are given.  nspace = 0 removes
- * the restriction.  ndet_out (host, may be NULL) receives the number of kept
+ * The RDM calls act on whatever vectors they are given.  When at most a quarter
+ * of the determinants is kept, every sigma of the context (any precision mode) is
+ * formed over the kept determinants only, in FP64 (FP32 for the FP32 vectors of
+ * the reduced-precision Davidson phase), so its cost follows the kept space.
+ * nspace = 0 removes the restriction.  ndet_out (host, may be NULL) receives the number of kept
  * determinants.  FORTE_ERR_ARG for inconsistent sizes or limits, or when no
  * determinant is kept (the previous restriction then stays in force).  Not
  * applied by forte_sigma_fp64_noalloc or forte_batch_solve.  Synchronises the
@@ -286,9 +289,11 @@ int forte_rdm3(forte_ctx *ctx, const double *C, double *g3);
  *              subspace and eigenproblem are FP64 in every mode.
  *   tol        max residual 2-norm per root; max_iter the iteration cap (<= 0: 400)
  * Davidson as forte_davidson (guess, preconditioner, 12 vectors per root,
- * collapse to 2 per root).  Problems with more than 4,000,000 determinants or
- * more than 3 roots take the single-problem path (forte_cas_create /
- * forte_davidson, one after another).  status_out (host [nprob], may be NULL)
+ * collapse to 2 per root).  Problems with more than 100,000 determinants (they
+ * fill the GPU on their own) or more than 3 roots take the single-problem path
+ * (forte_cas_create / forte_davidson with the tensor-core sigma of the chosen
+ * mode), four at a time on worker threads with their own streams, before the
+ * class launches.  status_out (host [nprob], may be NULL)
  * gets each problem's status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED
  * keeps energies); FORTE_ERR_ALLOC when the pooled workspace (about
  * (2 * 12 * nroots + 2 * nroots + 4) * N_det doubles per problem) cannot be

@@ -116,6 +116,10 @@ int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec) {
 static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
   int rc;
+  if (gas_sparse(ctx)) {  // small restricted space: FP64 sigma over the kept determinants
+    ctx->n_sigma_fp64 += nvec;
+    return gas_sigma(ctx, C, S, nvec);
+  }
   if (mode == FORTE_FP64) {
     ctx->n_sigma_fp64 += nvec;
     rc = sigma_fp64(ctx, C, S, nvec);
@@ -140,6 +144,7 @@ static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, in
     return FORTE_ERR_ARG;
   }
   ctx->n_sigma_mixed += nvec;
+  if (gas_sparse(ctx)) return gas_sigma(ctx, C, S, nvec);  // FP32 over the kept determinants
   int rc = sigma_mixed(ctx, C, S, nvec, mode);
   if (rc) return rc;
   return gas_mask(ctx, S, nvec);
@@ -430,15 +435,17 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       std::vector<double> h0(65);
       FORTE_CUDA_TRY(cudaMemcpyAsync(h0.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
       FORTE_CUDA_TRY(cudaStreamSynchronize(st));
-      if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N))) return rc;    // CGS pass 1
-      // second pass only when the first removed more than half of |t|^2 (the
+      // second pass only when the first removes more than half of |t|^2 (the
       // criterion of Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30 (1976) 772:
-      // ||t1|| >= ||t0|| / sqrt(2), with ||t1||^2 = ||t0||^2 - ||B^T t0||^2)
+      // ||t1|| >= ||t0|| / sqrt(2), with ||t1||^2 = ||t0||^2 - ||B^T t0||^2), which is
+      // known before pass 1: pass 1 forms B^T t1 only when pass 2 will use it
       double proj = 0.0;
       for (int i = 0; i < k; ++i) proj += h0[i] * h0[i];
+      const bool second = !(h0[k] - proj >= 0.5 * h0[k]);
+      if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N, second))) return rc;  // CGS pass 1
       const double *dfin = d_d1;
-      if (!(h0[k] - proj >= 0.5 * h0[k])) {
-        if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N))) return rc;  // CGS pass 2
+      if (second) {
+        if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N, false))) return rc;  // CGS pass 2
         dfin = d_d2;
       }
       FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), dfin, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));

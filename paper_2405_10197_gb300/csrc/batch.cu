@@ -28,15 +28,20 @@
 // in shared memory; the fastest candidate (CUDA events) is used for the solve
 // and reported by forte_batch_tuning.
 //
-// Problems with more than BT_MAX_DET determinants are solved one after another
-// with the single-problem path (forte_cas_create / forte_davidson).
+// Problems with more than BT_MAX_DET determinants are large enough to occupy the
+// whole GPU on their own: they take the single-problem path (forte_cas_create /
+// forte_davidson, with the tensor-core sigma in the reduced-precision modes), four
+// at a time on their own streams, before the class launches of the small problems.
+// (One CTA per such problem would spend minutes per FP64 solve on one SM.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -51,7 +56,7 @@ namespace {
 constexpr int BT_MAXK = 36;               // subspace vectors per problem (12 per root, 3 roots)
 constexpr int BT_LD = 37;                 // leading dimension of the small matrices in shared memory
 constexpr int BT_SEG = 512;               // CSR entries staged per pass
-constexpr long long BT_MAX_DET = 4000000; // larger problems take the single-problem path
+constexpr long long BT_MAX_DET = 100000;  // larger problems take the single-problem path
 constexpr int BT_MAX_ROOTS = 3;
 
 enum { AR_F64 = 0, AR_F32 = 1, AR_DF = 2 };
@@ -1015,6 +1020,47 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
   const size_t table_bytes = pool.used;
   const size_t total_bytes = ((table_bytes + 255) & ~(size_t)255) + sizeof(double) * (size_t)work_total;
 
+  // ---- problems beyond the in-CTA limit: the single-problem path, on four worker
+  // threads with their own streams
+  std::mutex mu;
+  std::atomic<int> next_single(0);
+  auto single_worker = [&]() {
+    cudaSetDevice(dev);
+    cudaStream_t sx = nullptr;
+    if (cudaStreamCreateWithFlags(&sx, cudaStreamNonBlocking) != cudaSuccess) sx = nullptr;
+    for (;;) {
+      const int kk = next_single.fetch_add(1);
+      if (kk >= (int)singles.size()) break;
+      const int i = singles[kk];
+      int rc = FORTE_OK;
+      std::string msg;
+      forte_ctx *ctx = forte_cas_create(norb[i], nalpha[i], nbeta[i], h[i], eri[i]);
+      if (!ctx) rc = FORTE_ERR_ARG;
+      if (!rc && sx) rc = forte_set_stream(ctx, sx);
+      if (!rc) rc = forte_set_precision(ctx, precision);
+      if (!rc) rc = forte_set_davidson_params(ctx, 12, 2, max_iter, 1e-8);
+      if (!rc) rc = forte_davidson(ctx, nroots[i], tol);
+      if (rc == FORTE_OK || rc == FORTE_ERR_NOT_CONVERGED) {
+        const int rc2 = forte_get_roots(ctx, E_out + eoff[i], nullptr, nullptr, nullptr);
+        if (rc2) rc = rc2;
+      }
+      if (rc) msg = forte_last_error();
+      forte_destroy(ctx);
+      std::lock_guard<std::mutex> lock(mu);
+      note(i, rc, msg.c_str());
+    }
+    if (sx) {
+      cudaStreamSynchronize(sx);
+      cudaStreamDestroy(sx);
+    }
+  };
+  // (before the class launches: a context's cudaFree would wait for them anyway)
+  {
+    std::vector<std::thread> workers;
+    for (int w = 0; w < std::min<int>(4, (int)singles.size()); ++w) workers.emplace_back(single_worker);
+    for (auto &x : workers) x.join();
+  }
+
   // ---- one pooled device allocation for the batch
   char *dbuf = nullptr;
   if (!classes.empty()) {
@@ -1175,6 +1221,7 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     std::vector<int> sth(nprob, FORTE_OK);
     FORTE_CUDA_TRY(cudaMemcpy(Eh.data(), dbuf + off_E, sizeof(double) * nE, cudaMemcpyDeviceToHost));
     FORTE_CUDA_TRY(cudaMemcpy(sth.data(), dbuf + off_st, sizeof(int) * nprob, cudaMemcpyDeviceToHost));
+    std::lock_guard<std::mutex> lock(mu);
     for (const ClassHost &ch : classes)
       for (int i : ch.probs) {
         for (int r = 0; r < nroots[i]; ++r) E_out[eoff[i] + r] = Eh[eoff[i] + r];
@@ -1183,21 +1230,6 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
       }
   }
 
-  // ---- problems beyond the in-CTA limits: the single-problem path
-  for (int i : singles) {
-    int rc = FORTE_OK;
-    forte_ctx *ctx = forte_cas_create(norb[i], nalpha[i], nbeta[i], h[i], eri[i]);
-    if (!ctx) rc = FORTE_ERR_ARG;
-    if (!rc) rc = forte_set_precision(ctx, precision);
-    if (!rc) rc = forte_set_davidson_params(ctx, 12, 2, max_iter, 1e-8);
-    if (!rc) rc = forte_davidson(ctx, nroots[i], tol);
-    if (rc == FORTE_OK || rc == FORTE_ERR_NOT_CONVERGED) {
-      const int rc2 = forte_get_roots(ctx, E_out + eoff[i], nullptr, nullptr, nullptr);
-      if (rc2) rc = rc2;
-    }
-    note(i, rc, forte_last_error());
-    forte_destroy(ctx);
-  }
   if (worst) set_error("%s", first_msg.c_str());
   return worst;
 }

@@ -169,6 +169,12 @@ struct forte_ctx {
   int *d_gas_cls[2] = {nullptr, nullptr};  // [N_alpha], [N_beta]
   int gas_nc[2] = {0, 0};
   uint8_t *d_gas_ok = nullptr;             // [gas_nc[0]][gas_nc[1]]
+  // the restricted sigma over the kept determinants only: kept alpha rows, and per
+  // alpha class the beta strings of its allowed classes (offsets [nc_alpha + 1])
+  int *d_gas_rows = nullptr;               // [gas_nrows]
+  long long gas_nrows = 0;
+  int *d_gas_boff = nullptr, *d_gas_blist = nullptr;
+  int gas_maxnnz = 0;                      // longest same-spin CSR row (alpha)
   long long gas_ndiag = 0;                 // kept determinants with I_alpha == I_beta (n_alpha == n_beta)
   // spin-parity sector (Ms = 0): 0 off, +1 even S, -1 odd S
   int spin_parity = 0;
@@ -253,10 +259,11 @@ int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k,
                         double theta, double guard, double *t, double *rnorm2, long long n);
 int vk_residual_precond(forte_ctx *ctx, const float *B, const float *S, int k, long long ld, const double *u,
                         double theta, double guard, float *t, double *rnorm2, long long n);
+// t_out = t_in - B c, dots_out = [B^T t_out (zeros unless dots), |t_out|^2]
 int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c, const double *t_in,
-                   double *t_out, double *dots_out, long long n);
+                   double *t_out, double *dots_out, long long n, bool dots = true);
 int vk_orth_update(forte_ctx *ctx, const float *B, int k, long long ld, const double *c, const float *t_in,
-                   float *t_out, double *dots_out, long long n);
+                   float *t_out, double *dots_out, long long n, bool dots = true);
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n);
 int vk_scale(forte_ctx *ctx, float *x, const float *src, double alpha, long long n);
 int vk_convert(forte_ctx *ctx, const double *x, float *y, long long n);
@@ -272,6 +279,12 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
 void gas_free(forte_ctx *ctx);
 int gas_mask(forte_ctx *ctx, double *x, int nvec);  // zero the excluded entries of nvec vectors
 int gas_mask(forte_ctx *ctx, float *x, int nvec);
+// sigma = P H P C over the kept determinants only (C zero outside them; S written
+// everywhere), in the precision of the vectors; gas_sparse() tells whether the
+// restriction is small enough for it
+bool gas_sparse(const forte_ctx *ctx);
+int gas_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
+int gas_sigma(forte_ctx *ctx, const float *C, float *S, int nvec);
 long long space_dim(const forte_ctx *ctx);           // dimension of the space Davidson works in
 int det_mask_fill(forte_ctx *ctx, double *x, int nvec, double value);  // value at the masked-out entries
 int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec);  // api.cu: unrestricted FP64-class sigma

@@ -6,12 +6,16 @@
 // of string classes (a small table ok[class_a][class_b]).
 //
 // The restricted Hamiltonian is P H P.  Vectors keep the [N_alpha][N_beta]
-// layout of the full space, zero outside the kept determinants: every sigma is
-// followed by a pass that zeroes the excluded entries (write-only: it reads the
-// class table and stores a zero where a determinant is excluded), and the
-// diagonal is +inf there, so that guesses and preconditioned corrections stay
-// inside the restricted space.  The sigma kernels still sweep the full product
-// space.
+// layout of the full space, zero outside the kept determinants, and the diagonal
+// is +inf there, so that guesses and preconditioned corrections stay inside the
+// restricted space.  When at most a quarter of the determinants is kept, sigma is
+// formed over the kept determinants only (k_gas_sigma: each output from its
+// same-spin Hamiltonian rows and its alpha-beta replacement pairs, skipping the
+// source determinants of excluded class pairs), so its cost follows the kept
+// space; otherwise the full-grid kernels run and a pass zeroes the excluded
+// entries (write-only: it reads the class table and stores a zero where a
+// determinant is excluded).
+#include <algorithm>
 #include <map>
 #include <vector>
 
@@ -41,6 +45,102 @@ __global__ void k_det_fill(T *__restrict__ x, long long total, long long nd, con
        i += (long long)gridDim.x * blockDim.x)
     if (!mask[i % nd]) x[i] = value;
 }
+
+// sigma[Ia][Ib] for the kept determinants of the kept alpha row rows[blockIdx.x]
+// (vector blockIdx.y); threads over the allowed beta strings of the row's class:
+//   sum_Ja H_aa[Ia][Ja] C[Ja][Ib] + sum_Jb H_bb[Ib][Jb] C[Ia][Jb]
+//   + sum_{m in L(Ib)} s_m sum_{k in L(Ia)} s_k (pq_k|rs_m) C[J_k][J_m]
+// (the last sum only over source determinants of allowed class pairs; C is zero
+// elsewhere).  T: FP64, or FP32 for the FP32 vectors of the reduced-precision phase.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gas_sigma(
+    const T *__restrict__ C, T *__restrict__ S, long long NA, long long NB, long long vstride,
+    const Repl *__restrict__ listA, int nkA, const Repl *__restrict__ listB, int nkB,
+    const int *__restrict__ ptrA, const int *__restrict__ colA, const T *__restrict__ valA,
+    const int *__restrict__ ptrB, const int *__restrict__ colB, const T *__restrict__ valB,
+    const T *__restrict__ gpair, int npair, const int *__restrict__ clsA, const int *__restrict__ clsB,
+    const uint8_t *__restrict__ ok, int ncA, int ncB, const int *__restrict__ rows, const int *__restrict__ boff,
+    const int *__restrict__ blist) {
+  extern __shared__ __align__(16) uint8_t gsm[];
+  T *Gs = (T *)gsm;                                   // [nkA][npair]
+  T *sval = Gs + (size_t)nkA * npair;                 // [nnz of CSR row Ia]
+  const int Ia = rows[blockIdx.x];
+  const int rb = ptrA[Ia], re = ptrA[Ia + 1], nnz = re - rb;
+  int *scol = (int *)(sval + nnz);                    // [nnz]
+  int *sJ = scol + nnz;                               // [nkA]
+  int *sJc = sJ + nkA;                                // [nkA]: classes of the J_k
+  uint8_t *sok = (uint8_t *)(sJc + nkA);              // [ncA][ncB]
+  const Repl *la = listA + (long long)Ia * nkA;
+  for (int i = threadIdx.x; i < nkA * npair; i += blockDim.x) {
+    const int e = i / npair, rs = i % npair;
+    const Repl r = la[e];
+    const T g = gpair[(size_t)r.pair * npair + rs];
+    Gs[i] = r.sgn < 0 ? -g : g;
+  }
+  for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
+    sval[i] = valA[rb + i];
+    scol[i] = colA[rb + i];
+  }
+  for (int e = threadIdx.x; e < nkA; e += blockDim.x) {
+    sJ[e] = la[e].J;
+    sJc[e] = clsA[la[e].J];
+  }
+  for (int i = threadIdx.x; i < ncA * ncB; i += blockDim.x) sok[i] = ok[i];
+  __syncthreads();
+  const T *Cv = C + (long long)blockIdx.y * vstride;
+  T *Sv = S + (long long)blockIdx.y * vstride;
+  const int ca = clsA[Ia];
+  for (int b = boff[ca] + threadIdx.x; b < boff[ca + 1]; b += blockDim.x) {
+    const long long Ib = blist[b];
+    T acc = T(0);
+    for (int e = 0; e < nnz; ++e) acc += sval[e] * Cv[(long long)scol[e] * NB + Ib];
+    for (int f = ptrB[Ib]; f < ptrB[Ib + 1]; ++f) acc += valB[f] * Cv[(long long)Ia * NB + colB[f]];
+    const Repl *lb = listB + Ib * nkB;
+    for (int m = 0; m < nkB; ++m) {
+      const Repl r = lb[m];
+      const uint8_t *okb = sok + clsB[r.J];
+      T in = T(0);
+      for (int k = 0; k < nkA; ++k)
+        if (okb[sJc[k] * ncB]) in += Gs[k * npair + r.pair] * Cv[(long long)sJ[k] * NB + r.J];
+      acc += r.sgn < 0 ? -in : in;
+    }
+    Sv[(long long)Ia * NB + Ib] = acc;
+  }
+}
+
+bool gas_sparse(const forte_ctx *ctx) {
+  return ctx->gas_on && !ctx->detmask_on && ctx->d_gas_rows && 4 * ctx->gas_ndet <= ctx->Ndet;
+}
+
+template <typename T>
+static int gas_sigma_t(forte_ctx *ctx, const T *C, T *S, int nvec) {
+  if (nvec <= 0) return FORTE_OK;
+  cudaStream_t st = ctx->stream;
+  FORTE_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(T) * ctx->Ndet * nvec, st));
+  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[1].nk, np = ctx->npair;
+  const size_t smem = sizeof(T) * ((size_t)nkA * np + ctx->gas_maxnnz) + sizeof(int) * ((size_t)ctx->gas_maxnnz + 2 * nkA) +
+                      (size_t)ctx->gas_nc[0] * ctx->gas_nc[1] + 64;
+  if (smem > 200 * 1024) {
+    set_error("restricted sigma needs %zu bytes of shared memory", smem);
+    return FORTE_ERR_ARG;
+  }
+  FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_gas_sigma<T>));
+  const bool f32 = sizeof(T) == 4;
+  const T *valA = f32 ? (const T *)(const void *)ctx->sd[0].csr_val32 : (const T *)(const void *)ctx->sd[0].csr_val;
+  const T *valB = f32 ? (const T *)(const void *)ctx->sd[1].csr_val32 : (const T *)(const void *)ctx->sd[1].csr_val;
+  const T *gp = f32 ? (const T *)(const void *)ctx->d_gpair32 : (const T *)(const void *)ctx->d_gpair;
+  dim3 grid((unsigned)ctx->gas_nrows, (unsigned)nvec);
+  FORTE_PROF(ctx, f32 ? "gas_sigma_f32" : "gas_sigma");
+  k_gas_sigma<T><<<grid, 256, smem, st>>>(C, S, ctx->Na, ctx->Nb, ctx->Ndet, ctx->sd[0].list, nkA, ctx->sd[1].list,
+                                          nkB, ctx->sd[0].csr_ptr, ctx->sd[0].csr_col, valA, ctx->sd[1].csr_ptr,
+                                          ctx->sd[1].csr_col, valB, gp, np, ctx->d_gas_cls[0], ctx->d_gas_cls[1],
+                                          ctx->d_gas_ok, ctx->gas_nc[0], ctx->gas_nc[1], ctx->d_gas_rows,
+                                          ctx->d_gas_boff, ctx->d_gas_blist);
+  FORTE_LAUNCH_CHECK();
+  return FORTE_OK;
+}
+int gas_sigma(forte_ctx *ctx, const double *C, double *S, int nvec) { return gas_sigma_t(ctx, C, S, nvec); }
+int gas_sigma(forte_ctx *ctx, const float *C, float *S, int nvec) { return gas_sigma_t(ctx, C, S, nvec); }
 
 template <typename T>
 static int gas_fill(forte_ctx *ctx, T *x, int nvec, T value) {
@@ -89,6 +189,11 @@ static void gas_release(forte_ctx *ctx) {
   }
   cudaFree(ctx->d_gas_ok);
   ctx->d_gas_ok = nullptr;
+  cudaFree(ctx->d_gas_rows);
+  cudaFree(ctx->d_gas_boff);
+  cudaFree(ctx->d_gas_blist);
+  ctx->d_gas_rows = ctx->d_gas_boff = ctx->d_gas_blist = nullptr;
+  ctx->gas_nrows = 0;
   ctx->gas_on = false;
   ctx->gas_ndet = 0;
   ctx->gas_ndiag = 0;
@@ -171,6 +276,35 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
     return FORTE_ERR_ALLOC;
   }
   FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_ok, ok.data(), ok.size(), cudaMemcpyHostToDevice));
+  // lists of the restricted sigma: kept alpha rows; per alpha class the beta strings
+  // of its allowed classes (ascending)
+  {
+    std::vector<int> rowsv, boff(ncA + 1, 0), blist;
+    for (int a = 0; a < ncA; ++a) {
+      for (long long j = 0; j < ctx->sh[1].N; ++j)
+        if (ok[(size_t)a * ncB + cls[1][j]]) blist.push_back((int)j);
+      boff[a + 1] = (int)blist.size();
+    }
+    for (long long i = 0; i < ctx->sh[0].N; ++i)
+      if (boff[cls[0][i] + 1] > boff[cls[0][i]]) rowsv.push_back((int)i);
+    int maxnnz = 0;
+    for (long long i = 0; i < ctx->sh[0].N; ++i)
+      maxnnz = std::max(maxnnz, ctx->sh[0].csr_ptr[i + 1] - ctx->sh[0].csr_ptr[i]);
+    if (blist.empty()) blist.push_back(0);
+    if (cudaMalloc(&ctx->d_gas_rows, sizeof(int) * std::max<size_t>(1, rowsv.size())) != cudaSuccess ||
+        cudaMalloc(&ctx->d_gas_boff, sizeof(int) * boff.size()) != cudaSuccess ||
+        cudaMalloc(&ctx->d_gas_blist, sizeof(int) * blist.size()) != cudaSuccess) {
+      gas_release(ctx);
+      set_error("cudaMalloc of the restricted-sigma lists failed");
+      return FORTE_ERR_ALLOC;
+    }
+    if (!rowsv.empty())
+      FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_rows, rowsv.data(), sizeof(int) * rowsv.size(), cudaMemcpyHostToDevice));
+    FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_boff, boff.data(), sizeof(int) * boff.size(), cudaMemcpyHostToDevice));
+    FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_blist, blist.data(), sizeof(int) * blist.size(), cudaMemcpyHostToDevice));
+    ctx->gas_nrows = (long long)rowsv.size();
+    ctx->gas_maxnnz = maxnnz;
+  }
   ctx->gas_nc[0] = ncA;
   ctx->gas_nc[1] = ncB;
   ctx->gas_ndet = ndet;

@@ -229,19 +229,19 @@ constexpr int WS_OFF_ACC = WS_OFF_B + WS_STAGES * MX_STAGE;
 // build A[i&1] and the gather rows of item i (`aFull`).  The producers, the MMA
 // thread and the epilogue run their tile rings across item boundaries, so the
 // set-up and the drain of one item overlap the tiles of its neighbours.
-// Shared-memory integer reduction at byte address addr unless en == 0xFFFF (the
-// "no target" marker of the scatter table), without a branch.
+// Shared-memory integer reduction at byte address addr unless bit 1 of en is set (the
+// "no target" marker 0xFFFF of the scatter table), without a branch.
 __device__ __forceinline__ void red_add_if(uint32_t addr, int v, uint32_t en) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.u32 p, %2, 65535;\n @p red.shared.add.s32 [%0], %1;\n}\n" ::"r"(addr), "r"(v),
-      "r"(en)
+      "{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %2, 2;\n setp.eq.u32 p, t, 0;\n"
+      " @p red.shared.add.u32 [%0], %1;\n}\n" ::"r"(addr), "r"(v), "r"(en)
       : "memory");
 }
 
 // Beta strings enter in positions (see the top of the file).  tabL holds the
 // scatter targets lane-contiguously: entry e of chunk c (8 pairs) of the string at
 // position pos = 128 t + 32 g + lane sits at tabL[(((t * 4 + g) * 16 + c) * 32 + lane) * 8 + e]
-// as (target position) | sign << 14, 0xFFFF when E_rs does not act; posOf[Jb] is
+// as 4 x (target position) | (sign < 0), 0xFFFF when E_rs does not act; posOf[Jb] is
 // the position of string Jb.
 //
 // FORTE_BF16X2: the gathered C tile is staged MN-major (positions contiguous):
@@ -255,7 +255,7 @@ __device__ __forceinline__ void red_add_if(uint32_t addr, int v, uint32_t en) {
 // write-out, 8 .. 8 + MX_EPI - 1 epilogue (MX_EPI / 4 warps per TMEM lane quarter).
 template <int MODE, typename TO>
 __global__ void __launch_bounds__(MX_THREADS, 1)
-    k_ab_mma(const Repl *__restrict__ listA, int nkA,
+    k_ab_mma(const Repl *__restrict__ listA, int nkA, int nkB,
              const uint16_t *__restrict__ tabL, const uint16_t *__restrict__ posOf, int nN, long long NA,
              long long NB, long long NBpos, const uint16_t *__restrict__ gTT_hi, const uint16_t *__restrict__ gTT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
@@ -335,10 +335,12 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const int Sx = sx_of(v);
         const float *ss = Sss + v * v64 + Ia * NB;
         TO *out = S + v * v64 + Ia * NB;
+        // every output received n_kl(beta) contributions carrying bits(1.5 2^23) each
+        const uint32_t bias = (uint32_t)nkB * 0x4B400000u;
         // padding positions never receive a contribution and stay zero
         for (long long x = st; x < NB; x += 96) {
           const int ps = __ldg(posOf + x);
-          out[x] = (TO)((double)ss[x] + ldexp((double)acc[ps], -Sx));
+          out[x] = (TO)((double)ss[x] + ldexp((double)(int)((uint32_t)acc[ps] - bias), -Sx));
           acc[ps] = 0;
         }
       } else {
@@ -636,15 +638,17 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            const uint32_t en = (c & 1) ? (wv[c >> 1] >> 16) : (wv[c >> 1] & 0xFFFFu);
-            const uint32_t rv = ra[8 * q + c];
-            // V = rint(f 2^S) by one FMA with 1.5 2^23 (exact for |x| <= 2^22): no
-            // conversion instruction, which would run on the narrow FP64 /
-            // conversion pipe.  The reduction is predicated, not branched: with the
-            // conflict-free positions a reduction costs one wavefront whatever its
-            // lane mask, and a divergent branch per column stalled the warps.
-            const float tv = fmaf(__uint_as_float(rv), (en & 0x4000u) ? -fscale : fscale, 12582912.0f);
-            red_add_if(acc_s + ((en & 0x3FFFu) << 2), __float_as_int(tv) - 0x4B400000, en);
+            // entry in the low half of en (the high half is ignored by the masks below)
+            const uint32_t en = (c & 1) ? (wv[c >> 1] >> 16) : wv[c >> 1];
+            // the sign (bit 0) onto the float's sign bit
+            const uint32_t rv = ra[8 * q + c] ^ (en << 31);
+            // bits(f 2^S + 1.5 2^23) = bits(1.5 2^23) + rint(f 2^S) for |f 2^S| <= 2^22: one
+            // FMA, no conversion instruction (those run on the narrow FP64 / conversion
+            // pipe).  The constant bits(1.5 2^23) is added n_kl(beta) times to every output
+            // per item (each output has exactly that many replacements) and is removed
+            // once, modulo 2^32, at write-out.  The reduction is predicated, not branched.
+            const float tv = fmaf(__uint_as_float(rv), fscale, 12582912.0f);
+            red_add_if(acc_s + (en & 0xFFFCu), __float_as_int(tv), en);
           }
         }
       }
@@ -729,13 +733,19 @@ static int ab_positions(forte_ctx *ctx) {
       tab[(size_t)pos * 128 + r.pair] = (uint16_t)(posOf[r.J] | (r.sgn < 0 ? 0x4000 : 0));
     }
   }
-  // the same entries lane-contiguous for the epilogue's coalesced loads
+  // the same entries lane-contiguous for the epilogue's coalesced loads, each as the
+  // byte offset of the target in the accumulator row with the sign in bit 0
+  // (positions < 16384, so offsets fit 16 bits with bits 0-1 free; 0xFFFF, bit 1 set,
+  // marks "no target")
   std::vector<uint16_t> tabL(tab.size(), 0xFFFFu);
   for (long long pos = 0; pos < rows; ++pos) {
     const long long t = pos / 128, g = (pos % 128) / 32, ln = pos % 32;
     for (int c = 0; c < 16; ++c)
-      for (int e = 0; e < 8; ++e)
-        tabL[(size_t)((((t * 4 + g) * 16 + c) * 32 + ln) * 8 + e)] = tab[(size_t)pos * 128 + c * 8 + e];
+      for (int e = 0; e < 8; ++e) {
+        const uint16_t en = tab[(size_t)pos * 128 + c * 8 + e];
+        tabL[(size_t)((((t * 4 + g) * 16 + c) * 32 + ln) * 8 + e)] =
+            en == 0xFFFFu ? (uint16_t)0xFFFFu : (uint16_t)(((en & 0x3FFFu) << 2) | ((en >> 14) & 1u));
+      }
   }
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abTabL, sizeof(uint16_t) * tabL.size()));
   FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abTabL, tabL.data(), sizeof(uint16_t) * tabL.size(), cudaMemcpyHostToDevice));
@@ -869,14 +879,14 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2, T>));
       FORTE_PROF(ctx, "ab_mma_bf16x2");
       k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(
-          ctx->sd[0].list, nkA, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
+          ctx->sd[0].list, nkA, nkB, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
           ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, Phi, Plo, nullptr, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     } else {
       FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32, T>));
       FORTE_PROF(ctx, "ab_mma_tf32");
       k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(
-          ctx->sd[0].list, nkA, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
+          ctx->sd[0].list, nkA, nkB, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
           ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, nullptr, nullptr, Pt32, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
     }

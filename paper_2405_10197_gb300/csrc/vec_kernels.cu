@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
   if (threadIdx.x == 0) part[blockIdx.x] = rt;
 }
 
-// t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2
-template <typename T>
+// t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2.
+// Without DOTS the B_i . t_out are not formed (a second read of every B_i) and part
+// holds zeros there.
+template <typename T, bool DOTS>
 __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict__ Bm, int k,
                                                             long long ld, const double *__restrict__ c,
                                                             const T *t_in, T *t_out, long long n,
@@ -179,16 +181,20 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict_
       nn += tr[e] * tr[e];
     }
   }
-  for (int i = 0; i < k; ++i) {
-    const T *b = Bm + (long long)i * ld;
-    T a = 0;
+  if (DOTS) {
+    for (int i = 0; i < k; ++i) {
+      const T *b = Bm + (long long)i * ld;
+      T a = 0;
 #pragma unroll
-    for (int e = 0; e < VK_EPT; ++e) {
-      long long j = base + (long long)e * VK_THREADS;
-      if (j < n) a += b[j] * tr[e];
+      for (int e = 0; e < VK_EPT; ++e) {
+        long long j = base + (long long)e * VK_THREADS;
+        if (j < n) a += b[j] * tr[e];
+      }
+      const double at = block_sum_t<T>(a, red);
+      if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + i] = at;
     }
-    const double at = block_sum_t<T>(a, red);
-    if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + i] = at;
+  } else {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) part[(long long)blockIdx.x * (k + 1) + i] = 0.0;
   }
   const double nt = block_sum_t<T>(nn, red);
   if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nt;
@@ -354,7 +360,7 @@ static int vk_residual_precond_t(forte_ctx *ctx, const T *B, const T *S, int k, 
 
 template <typename T>
 static int vk_orth_update_t(forte_ctx *ctx, const T *B, int k, long long ld, const double *c, const T *t_in,
-                            T *t_out, double *dots_out, long long n) {
+                            T *t_out, double *dots_out, long long n, bool dots) {
   if (k + 1 > VK_MAXV) { set_error("orth: subspace too large (%d)", k); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
@@ -362,7 +368,10 @@ static int vk_orth_update_t(forte_ctx *ctx, const T *B, int k, long long ld, con
   if (rc) return rc;
   {
     FORTE_PROF(ctx, "orth_update");
-    k_orth_update<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+    if (dots)
+      k_orth_update<T, true><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+    else
+      k_orth_update<T, false><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
   FORTE_LAUNCH_CHECK();
   }
   {
@@ -407,12 +416,12 @@ int vk_residual_precond(forte_ctx *ctx, const float *B, const float *S, int k, l
   return vk_residual_precond_t(ctx, B, S, k, ld, u, theta, guard, t, rnorm2, n);
 }
 int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c, const double *t_in,
-                   double *t_out, double *dots_out, long long n) {
-  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n);
+                   double *t_out, double *dots_out, long long n, bool dots) {
+  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n, dots);
 }
 int vk_orth_update(forte_ctx *ctx, const float *B, int k, long long ld, const double *c, const float *t_in,
-                   float *t_out, double *dots_out, long long n) {
-  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n);
+                   float *t_out, double *dots_out, long long n, bool dots) {
+  return vk_orth_update_t(ctx, B, k, ld, c, t_in, t_out, dots_out, n, dots);
 }
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n) {
   return vk_scale_t(ctx, x, src, alpha, n);

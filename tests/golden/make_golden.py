@@ -3,8 +3,9 @@
 Run from the repository root:  python tests/golden/make_golden.py [name ...]
 Each entry is computed by oracle.davidson (direct Slater-Condon sigma) on the
 seeded synthetic inputs of synth_inputs; nothing here touches the CUDA path.
-Residual tolerance 1e-6 bounds each energy error by |r|^2/gap < 1e-10 Eh for
-the gaps of these problems (the gap is recorded)."""
+Residual tolerance 1e-6 (1e-10 where the eigenvectors themselves are used)
+bounds each energy error by |r|^2/gap < 1e-10 Eh for the gaps of these problems
+(the gap is recorded)."""
 import json
 import os
 import sys
@@ -20,10 +21,15 @@ import synth_inputs as si  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
+SA_SAMPLE = 48  # sampled 2-RDM elements of the state-averaged ensemble
+
 JOBS = {
     "cas1212_seed1_4roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=1, nroots=4),
     "hubbard12_t1_U4": dict(kind="hubbard", norb=12, nalpha=6, nbeta=6, t=1.0, U=4.0, nroots=2),
-    "cas1212_seed3_3roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=3, nroots=3),
+    # the differentiation workload: also the equal-weight state-averaged RDMs of its
+    # three roots (Sec. II.B), from eigenvectors converged to a residual of 1e-10
+    "cas1212_seed3_3roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=3, nroots=3,
+                                 tol=1e-10, sa_rdms=True),
     "cas1010_seed5_3roots": dict(kind="integrals", norb=10, nalpha=5, nbeta=5, n_l=20, seed=5, nroots=3),
 }
 
@@ -38,11 +44,22 @@ def run(name):
     t0 = time.time()
     # one extra root so that the gap above the last requested root is known
     E, V, rn, it = oracle.davidson(job["norb"], job["nalpha"], job["nbeta"], h, eri, nroots=nr + 1,
-                                   tol=1e-6, max_iter=400)
+                                   tol=job.get("tol", 1e-6), max_iter=800)
     out = dict(job)
     out.update(energies=[float(e) for e in E[:nr]], next_energy=float(E[nr]),
                residuals=[float(r) for r in rn], iterations=int(it), seconds=time.time() - t0,
                threads=oracle.num_threads(), source="oracle.davidson (tests/golden/make_golden.py)")
+    if job.get("sa_rdms"):
+        n, na, nb = job["norb"], job["nalpha"], job["nbeta"]
+        w = np.full(nr, 1.0 / nr)
+        g1 = sum(w[k] * oracle.rdm12(n, na, nb, V[k], two=False)[0] for k in range(nr))
+        rng = np.random.default_rng(17)
+        idx = np.vstack([rng.integers(0, n, size=(SA_SAMPLE - 8, 4)),
+                         [[p, p, q, q] for p, q in rng.integers(0, n, size=(4, 2))],
+                         [[p, q, q, p] for p, q in rng.integers(0, n, size=(4, 2))]])
+        g2 = sum(w[k] * oracle.rdm2_elements(n, na, nb, V[k], idx) for k in range(nr))
+        out.update(sa_weights=[float(x) for x in w], sa_gamma1=g1.tolist(), sa_gamma2_index=idx.tolist(),
+                   sa_gamma2=[float(x) for x in g2])
     with open(os.path.join(HERE, name + ".json"), "w") as f:
         json.dump(out, f, indent=1)
     print(name, out["energies"], it, out["seconds"])

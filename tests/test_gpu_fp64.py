@@ -165,7 +165,8 @@ def test_rdms_cas1212_sampled_elements_and_invariants():
     n = 12
     h, eri = si.integrals(n, cfg["n_l"], cfg["seed"])
     prob = fg.CASProblem(n, 6, 6, h, eri)
-    C = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=9)[0], device="cuda")
+    Ch = si.random_vectors(1, prob.na, prob.nb, seed=9)[0]
+    C = torch.tensor(Ch, device="cuda")
     g1, g2 = prob.rdms(C)
     g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
     N = 12
@@ -174,7 +175,7 @@ def test_rdms_cas1212_sampled_elements_and_invariants():
     assert np.abs(np.einsum("pqrr->pq", g2) - (N - 1) * g1).max() < 1e-9
     rng = np.random.default_rng(1)
     idx = rng.integers(0, n, size=(24, 4))
-    ref = oracle.rdm2_elements(n, 6, 6, C.cpu().numpy(), idx)
+    ref = oracle.rdm2_elements(n, 6, 6, Ch, idx)
     assert np.abs(g2[tuple(idx.T)] - ref).max() < 1e-9
     # energy expectation from RDMs equals <C|H|C> from sigma
     S = prob.sigma(C.reshape(1, prob.na, prob.nb))
