@@ -550,15 +550,23 @@ def run_batch(args):
             flop = 2.0 * (NA * per_row(na) * NB + NB * per_row(nb) * NA) + 2.0 * NA * NB * nk(na) * nk(nb)
             probed = min(nprob, nsm)
             rate = probed * flop / (t["sigma_ms"] * 1e-3) / 1e12
-            entry = dict(t, problems=nprob, ctas_per_sm=round(nprob / nsm, 3))
+            entry = dict(t, sigma_ms=_sig(t["sigma_ms"], 4), single_iter_ms=_sig(t["single_iter_ms"], 4),
+                         ctas_per_problem_slot=round(nprob / (nsm * t["ctas_per_sm"]), 3))
             if name == "fp64":
                 entry["sigma_fp64_tflops"] = _sig(rate, 3)
                 entry["frac_of_fp64_pipe_1.25"] = _sig(rate / FP64_PEAK_TFLOPS, 3)
             tun.append(entry)
+        big = sum(1 for p in probs if comb(p["norb"], p["nalpha"]) * comb(p["norb"], p["nbeta"]) > 100000)
         out[name] = {"seconds": _sig(dt), "solves_per_s": _sig(len(probs) / dt), "not_converged": int((st != 0).sum()),
-                     "tuning": tun}
+                     "not_converged_instances": [dict(index=int(i), norb=probs[i]["norb"], nroots=probs[i]["nroots"],
+                                                      status=int(st[i])) for i in np.nonzero(st)[0][:16]],
+                     "single_path_above_1e5_det": big, "tuning": tun}
     diffs = [float(np.max(np.abs(np.array(a) - np.array(b)))) for a, b in zip(energies["fp64"], energies[mixed])]
     out["max_energy_diff_mixed_vs_fp64"] = max(diffs)
+    worst = np.argsort(diffs)[::-1][:5]
+    out["largest_diffs"] = [dict(index=int(i), norb=probs[i]["norb"], nroots=probs[i]["nroots"], diff=_sig(diffs[i], 3),
+                                 e_fp64=[float(x) for x in energies["fp64"][i]],
+                                 e_mixed=[float(x) for x in energies[mixed][i]]) for i in worst[:3]]
     import oracle
     errs = []
     for p, e in zip(probs[:64], energies["fp64"][:64]):
@@ -781,20 +789,32 @@ def run_extensions(args):
 
     C1 = torch.tensor(si.random_vectors(1, prob.na, prob.nb, seed=5), device="cuda")
     S1 = torch.empty_like(C1)
-    fg.forte_set_precision(prob.ctx, fg.FORTE_OZ64)
-    sig_full = ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), 5)
+    sig_modes = (("fp64", fg.FORTE_FP64, 2), ("oz64", fg.FORTE_OZ64, 5), ("bf16x2", fg.FORTE_BF16X2, 5))
+    sig = {}
+    for name, m, reps in sig_modes:
+        fg.forte_set_precision(prob.ctx, m)
+        sig[name] = {"unrestricted": _sig(ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), reps))}
     fg.forte_set_precision(prob.ctx, fg.FORTE_BF16X2)
     full = solve("full")
-    # X2: RAS(2h, 2p)
+    # X2: RAS(2h, 2p); both exact routes of the restricted sigma, then the timed choice
     nd = prob.set_gas((4, 6, 4), (6, 0, 0), (8, 12, 2))
-    fg.forte_set_precision(prob.ctx, fg.FORTE_OZ64)
-    sig_gas = ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), 5)
+    for name, m, reps in sig_modes:
+        fg.forte_set_precision(prob.ctx, m)
+        for route, key in ((0, "grid_route"), (1, "kept_route")):
+            fg.forte_set_gas_route(prob.ctx, route)
+            sig[name][key] = _sig(ev_ms(lambda: fg.forte_sigma(prob.ctx, C1, S1, 1), reps))
+        sig[name]["kept_over_unrestricted"] = _sig(sig[name]["kept_route"] / sig[name]["unrestricted"], 3)
+    fg.forte_set_gas_route(prob.ctx, -1)
     fg.forte_set_precision(prob.ctx, fg.FORTE_BF16X2)
     gas = solve("gas")
+    r64, r32, rms = fg.forte_get_gas_route(prob.ctx)
+    names = {-1: "not timed", 0: "full grid", 1: "kept determinants"}
+    gas["routes"] = {"fp64_vectors": names[r64], "fp32_vectors": names[r32],
+                     "timed_ms": {"fp64_grid": _sig(rms[0]), "fp64_kept": _sig(rms[1]), "fp32_grid": _sig(rms[2]),
+                                  "fp32_kept": _sig(rms[3])}}
     lines.append({"config": "X2 CAS(14,14) seed 2 under RAS(2 holes in orbitals 0-3, 2 particles in 10-13), "
                             "BF16x2 Davidson refined to 1e-8", "kept_determinants": nd, "n_det": prob.ndet,
-                  "sigma_oz64_ms": {"unrestricted": sig_full, "restricted": sig_gas},
-                  "davidson": {"unrestricted": full, "restricted": gas}})
+                  "sigma_ms": sig, "davidson": {"unrestricted": full, "restricted": gas}})
     prob.set_gas((), (), ())
     # X3: even-S sector
     prob.set_spin_parity(1)

@@ -128,9 +128,13 @@ int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
  * forte_davidson solves P H P in the kept space, and stored guesses are
  * projected.  Vectors keep the full [N_alpha][N_beta] layout, zero outside.
  * The RDM calls act on whatever vectors they are given.  When at most a quarter
- * of the determinants is kept, every sigma of the context (any precision mode) is
- * formed over the kept determinants only, in FP64 (FP32 for the FP32 vectors of
- * the reduced-precision Davidson phase), so its cost follows the kept space.
+ * of the determinants is kept (and the beta strings fall in at most 64
+ * occupation classes), sigma has a second exact route besides the full-grid
+ * kernels of the precision mode followed by the projection: a kernel over the
+ * kept determinants only, in FP64 (FP32 for the FP32 vectors of the
+ * reduced-precision Davidson phase), whose cost follows the kept space.  By
+ * default the first sigma of each vector type and mode times both routes and
+ * keeps the faster (forte_set_gas_route fixes the route).
  * nspace = 0 removes the restriction.  ndet_out (host, may be NULL) receives the number of kept
  * determinants.  FORTE_ERR_ARG for inconsistent sizes or limits, or when no
  * determinant is kept (the previous restriction then stays in force).  Not
@@ -138,6 +142,18 @@ int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
  * context stream. */
 int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const int *gmax,
                   long long *ndet_out);
+
+/* Route of the restricted sigma (see forte_set_gas): -1 timed choice (default),
+ * 0 full-grid kernels + projection, 1 the kept-determinant kernel (for any
+ * restriction with at most 64 beta occupation classes; otherwise the full grid).
+ * Clears earlier timings.  FORTE_ERR_ARG for other values. */
+int forte_set_gas_route(forte_ctx *ctx, int route);
+
+/* Route the restricted sigma takes for FP64 and FP32 vectors (host outputs, may
+ * be NULL): -1 no restriction or not yet timed, 0 full grid, 1 kept
+ * determinants; ms (host [4], may be NULL): the timings of the choice, FP64 full
+ * grid, FP64 kept, FP32 full grid, FP32 kept (0 when not timed). */
+int forte_get_gas_route(const forte_ctx *ctx, int *route_fp64, int *route_fp32, double *ms);
 
 /* Spin-parity sector of the Davidson solve (Sec. II.A.1: projection on states
  * of well-defined total spin), for n_alpha == n_beta (Ms = 0) only.  Exchanging
@@ -277,38 +293,45 @@ int forte_rdm3(forte_ctx *ctx, const double *C, double *g3);
  * E_out[offset_i .. offset_i + nroots[i]) with offset_i = sum_{j<i} nroots[j] (host).
  * Inputs per problem as for forte_cas_create (host arrays h[i], eri[i]).
  * Problems with equal (norb, nalpha, nbeta) form a size class sharing strings,
- * replacement lists and the same-spin sparsity pattern; each class is one kernel
- * launch with one CTA per problem that runs the whole Davidson-Liu solve on the
- * device, the class launches are captured in one CUDA graph, and the batch makes
- * one device allocation.  Before the solve an autotuner times the per-CTA sigma
- * of every class for each (threads per CTA, beta tile width) candidate and keeps
- * the fastest (forte_batch_tuning reports the choices).
+ * replacement lists and the same-spin sparsity pattern.  A class runs either as
+ * ONE kernel launch with one CTA per problem that runs the whole Davidson-Liu
+ * solve on the device (the class launches are captured in one CUDA graph and use
+ * one pooled device allocation), or on the single-problem path (forte_cas_create /
+ * forte_davidson with the tensor-core sigma of the chosen mode) on 8 worker
+ * threads with their own streams, concurrently with the class launches.  Before
+ * the solve an autotuner times, for every class, the per-CTA sigma for each
+ * (threads per CTA, beta tile width) candidate and keeps the fastest; it then
+ * times one Davidson iteration of the class's first problem on the
+ * single-problem path and sends the class there when
+ *   P x t_single_iteration < t_CTA_sigma x ceil(P / (resident CTAs per SM x SMs)).
+ * Problems with more than 100,000 determinants or more than 3 roots always take
+ * the single-problem path.  forte_batch_tuning reports the choices.
  *   precision  FORTE_FP64: FP64 sigma; FORTE_DF32 / FORTE_OZ64: double-FP32
  *              (FP64-class) sigma; FORTE_TF32 / FORTE_BF16X2: FP32 sigma down to
- *              a residual of max(tol, 3e-4), then the double-FP32 sigma.  Vectors,
- *              subspace and eigenproblem are FP64 in every mode.
+ *              a residual of max(tol, 3e-4), then the double-FP32 sigma (class
+ *              launches; the single-problem path uses that mode's own solver).
+ *              Vectors, subspace and eigenproblem are FP64 in every mode.
  *   tol        max residual 2-norm per root; max_iter the iteration cap (<= 0: 400)
  * Davidson as forte_davidson (guess, preconditioner, 12 vectors per root,
- * collapse to 2 per root).  Problems with more than 100,000 determinants (they
- * fill the GPU on their own) or more than 3 roots take the single-problem path
- * (forte_cas_create / forte_davidson with the tensor-core sigma of the chosen
- * mode), four at a time on worker threads with their own streams, before the
- * class launches.  status_out (host [nprob], may be NULL)
- * gets each problem's status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED
- * keeps energies); FORTE_ERR_ALLOC when the pooled workspace (about
- * (2 * 12 * nroots + 2 * nroots + 4) * N_det doubles per problem) cannot be
- * allocated.  Synchronous. */
+ * collapse to 2 per root).  status_out (host [nprob], may be NULL) gets each
+ * problem's status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED keeps
+ * energies); FORTE_ERR_ALLOC when the pooled workspace (about
+ * (2 * 12 * nroots + 2 * nroots + 4) * N_det doubles per class-launch problem)
+ * cannot be allocated.  Synchronous. */
 int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *nbeta, const int *nroots,
                       const double *const *h, const double *const *eri, int precision, double tol,
                       int max_iter, double *E_out, int *status_out);
 
-/* Autotuner choices of the last forte_batch_solve, one entry per size class
- * (host outputs of length max_classes, any may be NULL; *nclass = number of
- * classes): orbital and electron counts, threads per CTA, beta tile width of the
- * alpha-beta term, and the measured time (ms) of one sigma build of the class's
- * first problems (one CTA each) with the chosen candidate. */
+/* Autotuner choices of the last forte_batch_solve, one entry per size class below
+ * the in-CTA limits (host outputs of length max_classes, any may be NULL;
+ * *nclass = number of classes): orbital and electron counts, threads per CTA,
+ * beta tile width of the alpha-beta term, the measured time (ms) of one sigma
+ * build of the class's first problems (one CTA each) with the chosen candidate,
+ * the chosen path (0: class launch, 1: single-problem path), the measured time
+ * (ms) of one single-problem-path Davidson iteration, the class's problem count
+ * and the resident CTAs per SM of its launch. */
 int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads, int *tile,
-                       double *sigma_ms);
+                       double *sigma_ms, int *path, double *single_iter_ms, int *problems, int *ctas_per_sm);
 
 /* FP64 sigma = H C that allocates no device memory (the paper has no
  * counterpart; this is a service for callers of the library).  It is meant for

@@ -78,6 +78,8 @@ def library():
         "forte_tdm1": [vp, vp, vp, vp],
         "forte_rdm3": [vp, vp, vp],
         "forte_set_gas": [vp, i, vp, vp, vp, vp],
+        "forte_set_gas_route": [vp, i],
+        "forte_get_gas_route": [vp, vp, vp, vp],
         "forte_set_spin_parity": [vp, i],
         "forte_aci": [vp, d, d, i, d, i, vp, vp, vp, vp, vp],
         "forte_sigma_fp64_noalloc": [vp, vp, vp, i],
@@ -86,7 +88,7 @@ def library():
         "forte_get_status": [vp],
         "forte_set_wait_budget": [vp, ctypes.c_ulonglong],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
-        "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp],
+        "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -253,6 +255,19 @@ def forte_set_gas(ctx, spaces, gmin, gmax):
     return nd.value
 
 
+def forte_set_gas_route(ctx, route):
+    """Restricted sigma route: -1 timed choice (default), 0 full grid, 1 kept determinants."""
+    return _check(library().forte_set_gas_route(ctx, int(route)))
+
+
+def forte_get_gas_route(ctx):
+    """(route for FP64 vectors, route for FP32 vectors, timings [4] in ms)."""
+    r64, r32 = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(4)
+    _check(library().forte_get_gas_route(ctx, ctypes.byref(r64), ctypes.byref(r32), ms.ctypes.data))
+    return r64.value, r32.value, ms
+
+
 def forte_set_spin_parity(ctx, parity):
     """Davidson sector C^T = parity C for Ms = 0: +1 even S, -1 odd S, 0 off."""
     return _check(library().forte_set_spin_parity(ctx, int(parity)))
@@ -333,11 +348,18 @@ def forte_batch_tuning():
     nc = ctypes.c_int()
     arrs = [np.zeros(cap, dtype=np.int32) for _ in range(5)]
     ms = np.zeros(cap)
-    _check(library().forte_batch_tuning(cap, ctypes.byref(nc), *[a.ctypes.data for a in arrs], ms.ctypes.data))
+    path = np.zeros(cap, dtype=np.int32)
+    single = np.zeros(cap)
+    nprob = np.zeros(cap, dtype=np.int32)
+    occ = np.zeros(cap, dtype=np.int32)
+    _check(library().forte_batch_tuning(cap, ctypes.byref(nc), *[a.ctypes.data for a in arrs], ms.ctypes.data,
+                                        path.ctypes.data, single.ctypes.data, nprob.ctypes.data, occ.ctypes.data))
     out = []
     for k in range(min(nc.value, cap)):
         out.append(dict(norb=int(arrs[0][k]), nalpha=int(arrs[1][k]), nbeta=int(arrs[2][k]),
-                        threads=int(arrs[3][k]), tile=int(arrs[4][k]), sigma_ms=float(ms[k])))
+                        threads=int(arrs[3][k]), tile=int(arrs[4][k]), sigma_ms=float(ms[k]),
+                        path="class launch" if path[k] == 0 else "single-problem path",
+                        single_iter_ms=float(single[k]), problems=int(nprob[k]), ctas_per_sm=int(occ[k])))
     return out
 
 

@@ -111,30 +111,68 @@ int sigma_grid(forte_ctx *ctx, const double *C, double *S, int nvec) {
   return oz_ab_supported(ctx) ? sigma_oz64(ctx, C, S, nvec) : sigma_df(ctx, C, S, nvec);
 }
 
+// Under a small occupation restriction (gas_sparse) sigma has two exact routes:
+// the kernel over the kept determinants, or the full-grid kernels of the mode
+// followed by the projection.  Unless the caller fixed the route
+// (forte_set_gas_route), the first call for each vector type and mode runs both,
+// timed with events on the context stream, and later calls take the faster; the
+// result always comes from the route kept.
+template <typename T, typename Grid>
+static int gas_timed_route(forte_ctx *ctx, const T *C, T *S, int nvec, int mode, Grid &&grid) {
+  if (ctx->gas_route == 1) return gas_sigma(ctx, C, S, nvec);
+  const int slot = sizeof(T) == 8 ? 0 : 1;
+  if (ctx->gas_pick[slot] >= 0 && ctx->gas_pick_mode[slot] == mode)
+    return ctx->gas_pick[slot] ? gas_sigma(ctx, C, S, nvec) : grid();
+  struct Ev {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Ev() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  for (auto &x : ev.e) FORTE_CUDA_TRY(cudaEventCreate(&x));
+  FORTE_CUDA_TRY(cudaEventRecord(ev.e[0], ctx->stream));
+  int rc = grid();
+  if (rc) return rc;
+  FORTE_CUDA_TRY(cudaEventRecord(ev.e[1], ctx->stream));
+  rc = gas_sigma(ctx, C, S, nvec);
+  if (rc) return rc;
+  FORTE_CUDA_TRY(cudaEventRecord(ev.e[2], ctx->stream));
+  FORTE_CUDA_TRY(cudaEventSynchronize(ev.e[2]));
+  float tg = 0.f, ts = 0.f;
+  FORTE_CUDA_TRY(cudaEventElapsedTime(&tg, ev.e[0], ev.e[1]));
+  FORTE_CUDA_TRY(cudaEventElapsedTime(&ts, ev.e[1], ev.e[2]));
+  ctx->gas_pick_ms[slot][0] = tg;
+  ctx->gas_pick_ms[slot][1] = ts;
+  ctx->gas_pick[slot] = ts <= tg ? 1 : 0;
+  ctx->gas_pick_mode[slot] = mode;
+  return ctx->gas_pick[slot] ? FORTE_OK : grid();
+}
+
 // Under an occupation restriction the input vectors lie in the kept space and
 // the output is projected onto it (sigma = P H P C).
 static int sigma_dispatch(forte_ctx *ctx, const double *C, double *S, int nvec, int mode) {
   if (nvec <= 0) return FORTE_OK;
-  int rc;
-  if (gas_sparse(ctx)) {  // small restricted space: FP64 sigma over the kept determinants
+  auto grid = [&]() -> int {
+    int rc;
+    if (mode == FORTE_FP64)
+      rc = sigma_fp64(ctx, C, S, nvec);
+    else if (mode == FORTE_DF32)
+      rc = sigma_df(ctx, C, S, nvec);
+    else if (mode == FORTE_OZ64)
+      rc = sigma_oz64(ctx, C, S, nvec);
+    else
+      rc = sigma_mixed(ctx, C, S, nvec, mode);
+    if (rc) return rc;
+    return gas_mask(ctx, S, nvec);
+  };
+  // FP64-class modes (DF32 / OZ64) are counted with the FP64 ones
+  if (mode == FORTE_FP64 || mode == FORTE_DF32 || mode == FORTE_OZ64)
     ctx->n_sigma_fp64 += nvec;
-    return gas_sigma(ctx, C, S, nvec);
-  }
-  if (mode == FORTE_FP64) {
-    ctx->n_sigma_fp64 += nvec;
-    rc = sigma_fp64(ctx, C, S, nvec);
-  } else if (mode == FORTE_DF32) {  // FP64-class: counted with the FP64 ones
-    ctx->n_sigma_fp64 += nvec;
-    rc = sigma_df(ctx, C, S, nvec);
-  } else if (mode == FORTE_OZ64) {
-    ctx->n_sigma_fp64 += nvec;
-    rc = sigma_oz64(ctx, C, S, nvec);
-  } else {
+  else
     ctx->n_sigma_mixed += nvec;
-    rc = sigma_mixed(ctx, C, S, nvec, mode);
-  }
-  if (rc) return rc;
-  return gas_mask(ctx, S, nvec);
+  if (gas_sparse(ctx)) return gas_timed_route(ctx, C, S, nvec, mode, grid);
+  return grid();
 }
 
 static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, int mode) {
@@ -144,10 +182,13 @@ static int sigma_dispatch(forte_ctx *ctx, const float *C, float *S, int nvec, in
     return FORTE_ERR_ARG;
   }
   ctx->n_sigma_mixed += nvec;
-  if (gas_sparse(ctx)) return gas_sigma(ctx, C, S, nvec);  // FP32 over the kept determinants
-  int rc = sigma_mixed(ctx, C, S, nvec, mode);
-  if (rc) return rc;
-  return gas_mask(ctx, S, nvec);
+  auto grid = [&]() -> int {
+    int rc = sigma_mixed(ctx, C, S, nvec, mode);
+    if (rc) return rc;
+    return gas_mask(ctx, S, nvec);
+  };
+  if (gas_sparse(ctx)) return gas_timed_route(ctx, C, S, nvec, mode, grid);
+  return grid();
 }
 
 // ----------------------------------------------------------------- Davidson
@@ -485,16 +526,23 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
                      double *out, int max_outer, DvResult &res) {
   cudaStream_t st = ctx->stream;
   const long long N = ctx->Ndet;
-  const int kmax = std::min(63, nroots * (max_outer + 1));
-  // vectors: V[kmax], HV[kmax], W[nroots] (combine target), PCG: x r z p q
-  size_t nvec = (size_t)2 * kmax + nroots + 5;
+  // thick restart: after each Rayleigh-Ritz step the basis keeps nroots extra Ritz
+  // vectors besides the targets, so that a state close above the last target (a
+  // gap comparable to the start vectors' residual) stays resolved instead of being
+  // mixed into the targets at every collapse
+  const int nextra = (int)std::max(0LL, std::min<long long>({(long long)nroots, 63LL - 2 * nroots,
+                                                               space_dim(ctx) - nroots}));
+  const int nkeep = nroots + nextra;
+  const int kmax = std::min(63, std::max(nroots * (max_outer + 1), nkeep + nroots));
+  // vectors: V[kmax], HV[kmax], W[nkeep] (collapse target, then residuals), PCG: x r z p q
+  size_t nvec = (size_t)2 * kmax + nkeep + 5;
   size_t small_off = sizeof(double) * nvec * N;
   int rc = ctx->sc_dv.ensure(small_off + sizeof(double) * (64 * 64 + 4 * 66) + 256);
   if (rc) return rc;
   double *V = (double *)ctx->sc_dv.ptr;
   double *HV = V + (size_t)kmax * N;
   double *W = HV + (size_t)kmax * N;
-  double *px = W + (size_t)nroots * N, *pr = px + N, *pz = pr + N, *pp = pz + N, *pq = pp + N;
+  double *px = W + (size_t)nkeep * N, *pr = px + N, *pz = pr + N, *pp = pz + N, *pq = pp + N;
   double *d_coef = (double *)((char *)ctx->sc_dv.ptr + small_off);
   double *d_a = d_coef + 64 * 64, *d_b = d_a + 66, *d_s = d_b + 66;
   auto fetch = [&](const double *src, int cnt, double *dst) -> int {
@@ -544,15 +592,16 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
     w.assign(k, 0.0);
     U.assign((size_t)k * k, 0.0);
     sym_eig(k, Gk.data(), w.data(), U.data());
-    coef.assign((size_t)k * nroots, 0.0);
+    const int nk = std::min(k, nkeep);  // Ritz vectors kept
+    coef.assign((size_t)k * nk, 0.0);
     for (int i = 0; i < k; ++i)
-      for (int r = 0; r < nroots; ++r) coef[(size_t)i * nroots + r] = U[(size_t)i * k + r];
+      for (int r = 0; r < nk; ++r) coef[(size_t)i * nk + r] = U[(size_t)i * k + r];
     FORTE_CUDA_TRY(cudaMemcpyAsync(d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st));
-    if ((rc = vk_combine(ctx, V, k, N, d_coef, nroots, W, N, N))) return rc;
-    FORTE_CUDA_TRY(cudaMemcpyAsync(V, W, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
-    if ((rc = vk_combine(ctx, HV, k, N, d_coef, nroots, W, N, N))) return rc;
-    FORTE_CUDA_TRY(cudaMemcpyAsync(HV, W, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
-    k = nroots;
+    if ((rc = vk_combine(ctx, V, k, N, d_coef, nk, W, N, N))) return rc;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(V, W, sizeof(double) * nk * N, cudaMemcpyDeviceToDevice, st));
+    if ((rc = vk_combine(ctx, HV, k, N, d_coef, nk, W, N, N))) return rc;
+    FORTE_CUDA_TRY(cudaMemcpyAsync(HV, W, sizeof(double) * nk * N, cudaMemcpyDeviceToDevice, st));
+    k = nk;
     // exact residuals R_r = HV_r - theta_r V_r (kept in W)
     bool all = true;
     for (int r = 0; r < nroots; ++r) {
@@ -729,7 +778,7 @@ void forte_destroy(forte_ctx *ctx) {
   cudaFree(ctx->d_ozT); cudaFree(ctx->d_g1tmp); cudaFree(ctx->d_gpair2);
   cudaFree(ctx->d_ozG); cudaFree(ctx->d_ozGa); cudaFree(ctx->d_ozTabT);
   cudaFree(ctx->d_abPosOf); cudaFree(ctx->d_abStrOf); cudaFree(ctx->d_abTab); cudaFree(ctx->d_abTabL);
-  cudaFree(ctx->d_gTT_hi); cudaFree(ctx->d_gTT_lo);
+  cudaFree(ctx->d_gTT_hi); cudaFree(ctx->d_gTT_lo); cudaFree(ctx->d_abDcnt); cudaFree(ctx->d_vk_count);
   cudaFree(ctx->d_csr_val2[0]);
   if (!ctx->same_strings) cudaFree(ctx->d_csr_val2[1]);
   for (int s = 0; s < (ctx->same_strings ? 1 : 2); ++s) {
@@ -929,6 +978,33 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
                   long long *ndet_out) {
   if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
   return gas_set(ctx, nspace, size, gmin, gmax, ndet_out);
+}
+
+int forte_set_gas_route(forte_ctx *ctx, int route) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  if (route < -1 || route > 1) { set_error("route must be -1, 0 or 1"); return FORTE_ERR_ARG; }
+  ctx->gas_route = route;
+  for (int t = 0; t < 2; ++t) ctx->gas_pick[t] = ctx->gas_pick_mode[t] = -1;
+  return FORTE_OK;
+}
+
+int forte_get_gas_route(const forte_ctx *ctx, int *route_fp64, int *route_fp32, double *ms) {
+  if (!ctx) { set_error("NULL context"); return FORTE_ERR_ARG; }
+  const bool cand = ctx->gas_on && !ctx->detmask_on && ctx->d_gas_reach;
+  for (int t = 0; t < 2; ++t) {
+    int r = -1;
+    if (!ctx->gas_on) r = -1;
+    else if (!gas_sparse(ctx)) r = 0;
+    else if (ctx->gas_route == 1) r = 1;
+    else r = ctx->gas_pick[t];
+    if (t == 0 && route_fp64) *route_fp64 = r;
+    if (t == 1 && route_fp32) *route_fp32 = r;
+    if (ms) {
+      ms[2 * t] = cand ? ctx->gas_pick_ms[t][0] : 0.0;
+      ms[2 * t + 1] = cand ? ctx->gas_pick_ms[t][1] : 0.0;
+    }
+  }
+  return FORTE_OK;
 }
 
 int forte_aci(forte_ctx *ctx, double sigma, double gamma, int max_cycles, double tol, int parity, double *E_out,

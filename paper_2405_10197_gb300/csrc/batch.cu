@@ -26,13 +26,17 @@
 // the per-CTA sigma runs once on the first problems of the class for every
 // candidate (threads per CTA x beta tile width of the alpha-beta term) that fits
 // in shared memory; the fastest candidate (CUDA events) is used for the solve
-// and reported by forte_batch_tuning.
+// and reported by forte_batch_tuning.  It then times one Davidson iteration of
+// the class's first problem on the single-problem path (forte_cas_create /
+// forte_davidson, with the tensor-core sigma in the reduced-precision modes) and
+// sends the class there when P iterations of that path cost less than one class
+// sigma round (t_sigma x waves of resident CTAs).
 //
 // Problems with more than BT_MAX_DET determinants are large enough to occupy the
-// whole GPU on their own: they take the single-problem path (forte_cas_create /
-// forte_davidson, with the tensor-core sigma in the reduced-precision modes), four
-// at a time on their own streams, before the class launches of the small problems.
-// (One CTA per such problem would spend minutes per FP64 solve on one SM.)
+// whole GPU on their own and always take the single-problem path.  (One CTA per
+// such problem would spend minutes per FP64 solve on one SM.)  The class launches
+// are captured into one graph and launched without waiting; the single-problem
+// path runs meanwhile on BT_WORKERS host threads with their own streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +45,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <chrono>
 #include <thread>
 #include <type_traits>
 #include <vector>
@@ -58,6 +63,7 @@ constexpr int BT_LD = 37;                 // leading dimension of the small matr
 constexpr int BT_SEG = 512;               // CSR entries staged per pass
 constexpr long long BT_MAX_DET = 100000;  // larger problems take the single-problem path
 constexpr int BT_MAX_ROOTS = 3;
+constexpr int BT_WORKERS = 8;             // host threads of the single-problem path
 
 enum { AR_F64 = 0, AR_F32 = 1, AR_DF = 2 };
 
@@ -756,13 +762,17 @@ struct ClassHost {
   std::vector<int> probs;  // indices into the batch
   BClass dev{};
   int NT = 256, TJ = 32;
-  double probe_ms = 0.0;
+  double probe_ms = 0.0, single_ms = 0.0;
+  int path = 0;  // 0: class launch, 1: single-problem path
   long long work_doubles = 0;
 };
 
 struct TuneRecord {
   int n, na, nb, threads, tile;
-  double sigma_ms;
+  double sigma_ms;        // one per-CTA sigma of the class's first problems (one CTA each)
+  int path;               // 0: class launch, 1: single-problem path
+  double single_iter_ms;  // one Davidson iteration of one problem on the single-problem path
+  int problems, ctas_per_sm;
 };
 std::mutex g_tune_mu;
 std::vector<TuneRecord> g_tune;
@@ -1020,8 +1030,8 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
   const size_t table_bytes = pool.used;
   const size_t total_bytes = ((table_bytes + 255) & ~(size_t)255) + sizeof(double) * (size_t)work_total;
 
-  // ---- problems beyond the in-CTA limit: the single-problem path, on four worker
-  // threads with their own streams
+  // ---- the single-problem path (problems beyond the in-CTA limits and classes the
+  // autotuner sends there), on worker threads with their own streams
   std::mutex mu;
   std::atomic<int> next_single(0);
   auto single_worker = [&]() {
@@ -1054,12 +1064,27 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
       cudaStreamDestroy(sx);
     }
   };
-  // (before the class launches: a context's cudaFree would wait for them anyway)
-  {
-    std::vector<std::thread> workers;
-    for (int w = 0; w < std::min<int>(4, (int)singles.size()); ++w) workers.emplace_back(single_worker);
-    for (auto &x : workers) x.join();
-  }
+  // Host wall time (ms) of one Davidson iteration of problem i on the single-problem
+  // path: forte_davidson capped at 2 and at 6 iterations after a 1-iteration run
+  // that builds the lazy tables; (t6 - t2) / 4 leaves out the set-up and the first
+  // sigma builds and keeps the per-iteration launch and host costs.
+  auto single_iter_ms = [&](int i) -> double {
+    forte_ctx *ctx = forte_cas_create(norb[i], nalpha[i], nbeta[i], h[i], eri[i]);
+    if (!ctx) return INFINITY;
+    const int cap[3] = {1, 2, 6};
+    double t[3] = {0.0, 0.0, 0.0};
+    bool ok = forte_set_precision(ctx, precision) == FORTE_OK;
+    for (int r = 0; r < 3 && ok; ++r) {
+      ok = forte_set_davidson_params(ctx, 12, 2, cap[r], 1e-8) == FORTE_OK;
+      const auto t0 = std::chrono::steady_clock::now();
+      const int rc = ok ? forte_davidson(ctx, nroots[i], 1e-14) : FORTE_ERR_ARG;
+      t[r] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      ok = (rc == FORTE_OK || rc == FORTE_ERR_NOT_CONVERGED);
+    }
+    forte_destroy(ctx);
+    clear_error();
+    return ok ? std::max(1e-3, (t[2] - t[1]) / 4.0) : INFINITY;
+  };
 
   // ---- one pooled device allocation for the batch
   char *dbuf = nullptr;
@@ -1172,22 +1197,42 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     ch.probe_ms = best;
     ch.dev.TJ = ch.TJ;
     ch.dev.probe = 0;
+    // path: one class launch costs about probe_ms per sigma round for every wave of
+    // resident CTAs; the single-problem path costs single_iter_ms per problem and
+    // iteration (no credit for overlap between workers)
+    int per_sm = 0;
+    cudaError_t oe = cudaSuccess;
+    const size_t smem = class_smem(ch.dev, ar, ch.TJ);
+    if (ch.NT == 128) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_davidson<128>, 128, smem);
+    else if (ch.NT == 512) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_davidson<512>, 512, smem);
+    else oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_davidson<256>, 256, smem);
+    if (oe != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int P = ch.dev.P;
+    const double waves = std::ceil((double)P / (double)(per_sm * nsm));
+    ch.single_ms = single_iter_ms(ch.probs[0]);
+    ch.path = (best * waves <= (double)P * ch.single_ms) ? 0 : 1;
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune.push_back(TuneRecord{ch.n, ch.na, ch.nb, ch.NT, ch.TJ, best});
+    g_tune.push_back(TuneRecord{ch.n, ch.na, ch.nb, ch.NT, ch.TJ, best, ch.path, ch.single_ms, P, per_sm});
   }
+  for (const ClassHost &ch : classes)
+    if (ch.path == 1) singles.insert(singles.end(), ch.probs.begin(), ch.probs.end());
 
-  // ---- the solve: one launch per class on its own stream, captured as one graph
-  if (!classes.empty()) {
-    cudaStream_t s0 = guard.s[0];
-    cudaEvent_t fork, join;
+  // ---- the solve: one launch per class-launch class on its own stream, captured
+  // as one graph and launched without waiting; the single-problem path runs on
+  // the worker threads meanwhile (their kernels take the SMs the classes leave)
+  std::vector<size_t> launched;
+  for (size_t ci = 0; ci < classes.size(); ++ci)
+    if (classes[ci].path == 0) launched.push_back(ci);
+  cudaError_t ce = cudaSuccess;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  if (!launched.empty()) {
+    cudaStream_t s0 = guard.s[launched[0]];
     FORTE_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    FORTE_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-    std::vector<cudaEvent_t> joins;
     FORTE_CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
-    cudaError_t ce = cudaEventRecord(fork, s0);
+    ce = cudaEventRecord(fork, s0);
     // the largest class first: its CTAs run longest
-    std::vector<size_t> order(classes.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::vector<size_t> order = launched;
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return classes[x].dev.N > classes[y].dev.N; });
     for (size_t oi = 0; oi < order.size() && ce == cudaSuccess; ++oi) {
       const size_t ci = order[oi];
@@ -1209,10 +1254,16 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     if (ce == cudaSuccess) ce = ce2;
     if (ce == cudaSuccess) ce = cudaGraphInstantiate(&guard.ge, guard.g, 0);
     if (ce == cudaSuccess) ce = cudaGraphLaunch(guard.ge, s0);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s0);
+  }
+  {
+    std::vector<std::thread> workers;
+    for (int w = 0; w < std::min<int>(BT_WORKERS, (int)singles.size()); ++w) workers.emplace_back(single_worker);
+    for (auto &x : workers) x.join();
+  }
+  if (!launched.empty()) {
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(guard.s[launched[0]]);
     for (auto ev : joins) cudaEventDestroy(ev);
     cudaEventDestroy(fork);
-    cudaEventDestroy(join);
     if (ce != cudaSuccess) {
       set_error("forte_batch_solve: batched launch failed: %s", cudaGetErrorString(ce));
       return FORTE_ERR_CUDA;
@@ -1222,8 +1273,8 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     FORTE_CUDA_TRY(cudaMemcpy(Eh.data(), dbuf + off_E, sizeof(double) * nE, cudaMemcpyDeviceToHost));
     FORTE_CUDA_TRY(cudaMemcpy(sth.data(), dbuf + off_st, sizeof(int) * nprob, cudaMemcpyDeviceToHost));
     std::lock_guard<std::mutex> lock(mu);
-    for (const ClassHost &ch : classes)
-      for (int i : ch.probs) {
+    for (size_t ci : launched)
+      for (int i : classes[ci].probs) {
         for (int r = 0; r < nroots[i]; ++r) E_out[eoff[i] + r] = Eh[eoff[i] + r];
         note(i, sth[i], sth[i] == FORTE_ERR_NOT_CONVERGED ? "Davidson did not converge"
                                                             : (sth[i] ? "non-finite residual" : ""));
@@ -1235,7 +1286,8 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
 }
 
 extern "C" int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads,
-                                  int *tile, double *sigma_ms) {
+                                  int *tile, double *sigma_ms, int *path, double *single_iter_ms, int *problems,
+                                  int *ctas_per_sm) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   if (nclass) *nclass = (int)g_tune.size();
   for (int i = 0; i < (int)g_tune.size() && i < max_classes; ++i) {
@@ -1245,6 +1297,10 @@ extern "C" int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *
     if (threads) threads[i] = g_tune[i].threads;
     if (tile) tile[i] = g_tune[i].tile;
     if (sigma_ms) sigma_ms[i] = g_tune[i].sigma_ms;
+    if (path) path[i] = g_tune[i].path;
+    if (single_iter_ms) single_iter_ms[i] = g_tune[i].single_iter_ms;
+    if (problems) problems[i] = g_tune[i].problems;
+    if (ctas_per_sm) ctas_per_sm[i] = g_tune[i].ctas_per_sm;
   }
   return FORTE_OK;
 }

@@ -123,6 +123,8 @@ struct forte_ctx {
   uint16_t *d_abTab = nullptr;    // [tiles * 128][128]: position of E_rs (string at pos) | sign << 14
   uint16_t *d_abTabL = nullptr;   // the same entries lane-contiguous: [tiles][4][16 chunks][32 lanes][8]
   uint16_t *d_gTT_hi = nullptr, *d_gTT_lo = nullptr;  // [npair][128]: gT transposed (pair-major)
+  bool ab_split = false;          // scatter into separate positive / negative accumulator words
+  int8_t *d_abDcnt = nullptr;     // [N_beta]: (+) minus (-) signs of the replacements reaching each string
   // dense same-spin string Hamiltonians for the tensor-core same-spin sigma,
   // [N][N padded to 16] per spin (aliases when alpha and beta strings coincide)
   uint16_t *d_hd_hi[2] = {nullptr, nullptr}, *d_hd_lo[2] = {nullptr, nullptr};
@@ -153,6 +155,7 @@ struct forte_ctx {
   forte::Scratch sc_t1, sc_t2;     // sigma: transposes for the beta-beta term
   forte::Scratch sc_dv;            // Davidson subspace and work vectors
   forte::Scratch sc_small;         // small device arrays (dots, norms)
+  unsigned *d_vk_count = nullptr;  // arrival counter of the fused reductions (zero between launches)
   forte::Scratch sc_rdm;           // RDM intermediates
   forte::Scratch sc_mixed;         // reduced-precision copies of vectors
   forte::Scratch sc_grad;          // per-state RDMs of the state-averaged gradient
@@ -175,7 +178,15 @@ struct forte_ctx {
   long long gas_nrows = 0;
   int *d_gas_boff = nullptr, *d_gas_blist = nullptr;
   int gas_maxnnz = 0;                      // longest same-spin CSR row (alpha)
+  int *d_gas_coff = nullptr, *d_gas_cstr = nullptr;  // beta strings by class: [ncB + 1], [N_beta]
+  unsigned long long *d_gas_reach = nullptr;         // [ncB]: classes reached by one beta replacement
+  int gas_route = -1;                      // restricted sigma: -1 timed choice, 0 full grid, 1 kept only
   long long gas_ndiag = 0;                 // kept determinants with I_alpha == I_beta (n_alpha == n_beta)
+  // restricted sigma path per vector type [FP64, FP32]: -1 not yet timed, 0 full
+  // grid + projection, 1 kept determinants only; timed for the mode in gas_pick_mode
+  int gas_pick[2] = {-1, -1};
+  int gas_pick_mode[2] = {-1, -1};
+  float gas_pick_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};  // [type][grid, sparse]
   // spin-parity sector (Ms = 0): 0 off, +1 even S, -1 odd S
   int spin_parity = 0;
   // arbitrary determinant mask [Ndet] (the P and M spaces of adaptive CI)

@@ -46,70 +46,120 @@ __global__ void k_det_fill(T *__restrict__ x, long long total, long long nd, con
     if (!mask[i % nd]) x[i] = value;
 }
 
-// sigma[Ia][Ib] for the kept determinants of the kept alpha row rows[blockIdx.x]
-// (vector blockIdx.y); threads over the allowed beta strings of the row's class:
-//   sum_Ja H_aa[Ia][Ja] C[Ja][Ib] + sum_Jb H_bb[Ib][Jb] C[Ia][Jb]
-//   + sum_{m in L(Ib)} s_m sum_{k in L(Ia)} s_k (pq_k|rs_m) C[J_k][J_m]
-// (the last sum only over source determinants of allowed class pairs; C is zero
-// elsewhere).  T: FP64, or FP32 for the FP32 vectors of the reduced-precision phase.
+constexpr int GAS_THREADS = 256;
+
+// P H P C for the kept determinants of the kept alpha row Ia = rows[blockIdx.x]
+// (vector blockIdx.y), every other entry of S left as it is (zero).
+//  (1) alpha-beta, driven by the source beta strings: for each beta class cb whose
+//      strings carry weight (some J_k of the row, k in L(Ia), has an allowed
+//      (class(J_k), cb) pair: elsewhere C is zero) and reach an allowed output
+//      class, tiles of TJ strings Jb of that class are gathered as
+//      D[k][j] = C[J_k][Jb_j] for the allowed k only, and every replacement
+//      E_rs Jb = s I_b with an allowed output adds
+//      s * sum_k s_k (pq_k|rs) D[k][j] to the row accumulator (shared memory);
+//  (2) per kept output: the accumulator plus the same-spin CSR terms
+//      sum_Ja H_aa[Ia][Ja] C[Ja][Ib] + sum_Jb H_bb[Ib][Jb] C[Ia][Jb].
+// Each (output, replacement pair) of Eq. 1's two-body alpha-beta part is formed
+// once, and only where both its source and its output are kept.  T: FP64, or FP32
+// for the FP32 vectors of the reduced-precision phase.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gas_sigma(
-    const T *__restrict__ C, T *__restrict__ S, long long NA, long long NB, long long vstride,
+__global__ void __launch_bounds__(GAS_THREADS) k_gas_sigma(
+    const T *__restrict__ C, T *__restrict__ S, long long NB, long long vstride,
     const Repl *__restrict__ listA, int nkA, const Repl *__restrict__ listB, int nkB,
     const int *__restrict__ ptrA, const int *__restrict__ colA, const T *__restrict__ valA,
     const int *__restrict__ ptrB, const int *__restrict__ colB, const T *__restrict__ valB,
     const T *__restrict__ gpair, int npair, const int *__restrict__ clsA, const int *__restrict__ clsB,
-    const uint8_t *__restrict__ ok, int ncA, int ncB, const int *__restrict__ rows, const int *__restrict__ boff,
-    const int *__restrict__ blist) {
+    const uint8_t *__restrict__ ok, int ncB, const unsigned long long *__restrict__ reachB,
+    const int *__restrict__ rows, const int *__restrict__ boff, const int *__restrict__ blist,
+    const int *__restrict__ coff, const int *__restrict__ cstr, int TJ) {
   extern __shared__ __align__(16) uint8_t gsm[];
-  T *Gs = (T *)gsm;                                   // [nkA][npair]
-  T *sval = Gs + (size_t)nkA * npair;                 // [nnz of CSR row Ia]
   const int Ia = rows[blockIdx.x];
-  const int rb = ptrA[Ia], re = ptrA[Ia + 1], nnz = re - rb;
-  int *scol = (int *)(sval + nnz);                    // [nnz]
-  int *sJ = scol + nnz;                               // [nkA]
-  int *sJc = sJ + nkA;                                // [nkA]: classes of the J_k
-  uint8_t *sok = (uint8_t *)(sJc + nkA);              // [ncA][ncB]
+  const int rb = ptrA[Ia], nnz = ptrA[Ia + 1] - rb;
+  T *Gs = (T *)gsm;                                         // [nkA][npair] signed integral rows
+  T *srow = Gs + (size_t)nkA * npair;                       // [NB] alpha-beta accumulator
+  T *D = srow + NB;                                         // [nkA][TJ] gathered C rows
+  T *sval = D + (size_t)nkA * TJ;                           // [nnz] CSR row Ia of H_aa
+  Repl *Lb = (Repl *)(((uintptr_t)(sval + nnz) + 7) & ~(uintptr_t)7);  // [TJ][nkB]
+  int *scol = (int *)(Lb + (size_t)TJ * nkB);               // [nnz]
+  int *sJ = scol + nnz;                                     // [nkA]
+  int *kcnt = sJ + nkA;                                     // [ncB]
+  uint16_t *klist = (uint16_t *)(kcnt + ncB);               // [ncB][nkA]: k * npair of the allowed k
+  uint8_t *sclsB = (uint8_t *)(klist + (size_t)ncB * nkA);  // [NB] beta classes
   const Repl *la = listA + (long long)Ia * nkA;
-  for (int i = threadIdx.x; i < nkA * npair; i += blockDim.x) {
+  const int ca = clsA[Ia];
+  const uint8_t *okA = ok + (size_t)ca * ncB;
+  for (int i = threadIdx.x; i < nkA * npair; i += GAS_THREADS) {
     const int e = i / npair, rs = i % npair;
     const Repl r = la[e];
     const T g = gpair[(size_t)r.pair * npair + rs];
     Gs[i] = r.sgn < 0 ? -g : g;
   }
-  for (int i = threadIdx.x; i < nnz; i += blockDim.x) {
+  for (long long i = threadIdx.x; i < NB; i += GAS_THREADS) {
+    srow[i] = T(0);
+    sclsB[i] = (uint8_t)clsB[i];
+  }
+  for (int i = threadIdx.x; i < nnz; i += GAS_THREADS) {
     sval[i] = valA[rb + i];
     scol[i] = colA[rb + i];
   }
-  for (int e = threadIdx.x; e < nkA; e += blockDim.x) {
-    sJ[e] = la[e].J;
-    sJc[e] = clsA[la[e].J];
+  for (int e = threadIdx.x; e < nkA; e += GAS_THREADS) sJ[e] = la[e].J;
+  // allowed k per source beta class (ascending k: deterministic sums)
+  for (int cb = threadIdx.x; cb < ncB; cb += GAS_THREADS) {
+    int m = 0;
+    for (int e = 0; e < nkA; ++e)
+      if (ok[(size_t)clsA[la[e].J] * ncB + cb]) klist[(size_t)cb * nkA + m++] = (uint16_t)(e * npair);
+    kcnt[cb] = m;
   }
-  for (int i = threadIdx.x; i < ncA * ncB; i += blockDim.x) sok[i] = ok[i];
+  unsigned long long okmask = 0ull;
+  for (int b = 0; b < ncB; ++b)
+    if (okA[b]) okmask |= 1ull << b;
   __syncthreads();
   const T *Cv = C + (long long)blockIdx.y * vstride;
   T *Sv = S + (long long)blockIdx.y * vstride;
-  const int ca = clsA[Ia];
-  for (int b = boff[ca] + threadIdx.x; b < boff[ca + 1]; b += blockDim.x) {
+  for (int cb = 0; cb < ncB; ++cb) {
+    const int kc = kcnt[cb];
+    if (kc == 0 || !(reachB[cb] & okmask)) continue;
+    const uint16_t *kl = klist + (size_t)cb * nkA;
+    for (int s0 = coff[cb]; s0 < coff[cb + 1]; s0 += TJ) {
+      const int tj = min(TJ, coff[cb + 1] - s0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < kc * tj; i += GAS_THREADS) {
+        const int kk = i / tj, j = i % tj;
+        D[kk * TJ + j] = Cv[(long long)sJ[kl[kk] / npair] * NB + cstr[s0 + j]];
+      }
+      for (int i = threadIdx.x; i < tj * nkB; i += GAS_THREADS)
+        Lb[i] = listB[(long long)cstr[s0 + i / nkB] * nkB + i % nkB];
+      __syncthreads();
+      for (int w = threadIdx.x; w < tj * nkB; w += GAS_THREADS) {
+        const Repl rf = Lb[w];
+        if (!((okmask >> sclsB[rf.J]) & 1ull)) continue;
+        const int j = w / nkB;
+        const T *g = Gs + rf.pair;
+        const T *d = D + j;
+        T acc = T(0);
+        for (int kk = 0; kk < kc; ++kk) acc += g[kl[kk]] * d[kk * TJ];
+        atomicAdd(&srow[rf.J], rf.sgn < 0 ? -acc : acc);
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = boff[ca] + threadIdx.x; b < boff[ca + 1]; b += GAS_THREADS) {
     const long long Ib = blist[b];
-    T acc = T(0);
+    T acc = srow[Ib];
     for (int e = 0; e < nnz; ++e) acc += sval[e] * Cv[(long long)scol[e] * NB + Ib];
     for (int f = ptrB[Ib]; f < ptrB[Ib + 1]; ++f) acc += valB[f] * Cv[(long long)Ia * NB + colB[f]];
-    const Repl *lb = listB + Ib * nkB;
-    for (int m = 0; m < nkB; ++m) {
-      const Repl r = lb[m];
-      const uint8_t *okb = sok + clsB[r.J];
-      T in = T(0);
-      for (int k = 0; k < nkA; ++k)
-        if (okb[sJc[k] * ncB]) in += Gs[k * npair + r.pair] * Cv[(long long)sJ[k] * NB + r.J];
-      acc += r.sgn < 0 ? -in : in;
-    }
     Sv[(long long)Ia * NB + Ib] = acc;
   }
 }
 
+static size_t gas_smem_bytes(size_t tsz, int nkA, int nkB, int npair, long long NB, int maxnnz, int ncB, int TJ) {
+  return tsz * ((size_t)nkA * npair + NB + (size_t)nkA * TJ + maxnnz) + 8 + sizeof(Repl) * (size_t)TJ * nkB +
+         sizeof(int) * ((size_t)maxnnz + nkA + ncB) + sizeof(uint16_t) * (size_t)ncB * nkA + NB + 16;
+}
+
 bool gas_sparse(const forte_ctx *ctx) {
-  return ctx->gas_on && !ctx->detmask_on && ctx->d_gas_rows && 4 * ctx->gas_ndet <= ctx->Ndet;
+  if (!ctx->gas_on || ctx->detmask_on || !ctx->d_gas_rows || !ctx->d_gas_reach || ctx->gas_route == 0) return false;
+  return ctx->gas_route == 1 || 4 * ctx->gas_ndet <= ctx->Ndet;
 }
 
 template <typename T>
@@ -117,10 +167,20 @@ static int gas_sigma_t(forte_ctx *ctx, const T *C, T *S, int nvec) {
   if (nvec <= 0) return FORTE_OK;
   cudaStream_t st = ctx->stream;
   FORTE_CUDA_TRY(cudaMemsetAsync(S, 0, sizeof(T) * ctx->Ndet * nvec, st));
-  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[1].nk, np = ctx->npair;
-  const size_t smem = sizeof(T) * ((size_t)nkA * np + ctx->gas_maxnnz) + sizeof(int) * ((size_t)ctx->gas_maxnnz + 2 * nkA) +
-                      (size_t)ctx->gas_nc[0] * ctx->gas_nc[1] + 64;
-  if (smem > 200 * 1024) {
+  if (ctx->gas_nrows == 0) return FORTE_OK;
+  const int nkA = ctx->sh[0].nk, nkB = ctx->sh[1].nk, np = ctx->npair, ncB = ctx->gas_nc[1];
+  // the widest source tile that keeps two blocks per SM, else one
+  int TJ = 64;
+  size_t smem = gas_smem_bytes(sizeof(T), nkA, nkB, np, ctx->Nb, ctx->gas_maxnnz, ncB, TJ);
+  while (TJ > 16 && smem > 113 * 1024) {
+    TJ /= 2;
+    smem = gas_smem_bytes(sizeof(T), nkA, nkB, np, ctx->Nb, ctx->gas_maxnnz, ncB, TJ);
+  }
+  while (TJ > 8 && smem > 220 * 1024) {
+    TJ /= 2;
+    smem = gas_smem_bytes(sizeof(T), nkA, nkB, np, ctx->Nb, ctx->gas_maxnnz, ncB, TJ);
+  }
+  if (smem > 220 * 1024) {
     set_error("restricted sigma needs %zu bytes of shared memory", smem);
     return FORTE_ERR_ARG;
   }
@@ -131,11 +191,11 @@ static int gas_sigma_t(forte_ctx *ctx, const T *C, T *S, int nvec) {
   const T *gp = f32 ? (const T *)(const void *)ctx->d_gpair32 : (const T *)(const void *)ctx->d_gpair;
   dim3 grid((unsigned)ctx->gas_nrows, (unsigned)nvec);
   FORTE_PROF(ctx, f32 ? "gas_sigma_f32" : "gas_sigma");
-  k_gas_sigma<T><<<grid, 256, smem, st>>>(C, S, ctx->Na, ctx->Nb, ctx->Ndet, ctx->sd[0].list, nkA, ctx->sd[1].list,
-                                          nkB, ctx->sd[0].csr_ptr, ctx->sd[0].csr_col, valA, ctx->sd[1].csr_ptr,
-                                          ctx->sd[1].csr_col, valB, gp, np, ctx->d_gas_cls[0], ctx->d_gas_cls[1],
-                                          ctx->d_gas_ok, ctx->gas_nc[0], ctx->gas_nc[1], ctx->d_gas_rows,
-                                          ctx->d_gas_boff, ctx->d_gas_blist);
+  k_gas_sigma<T><<<grid, GAS_THREADS, smem, st>>>(
+      C, S, ctx->Nb, ctx->Ndet, ctx->sd[0].list, nkA, ctx->sd[1].list, nkB, ctx->sd[0].csr_ptr, ctx->sd[0].csr_col,
+      valA, ctx->sd[1].csr_ptr, ctx->sd[1].csr_col, valB, gp, np, ctx->d_gas_cls[0], ctx->d_gas_cls[1],
+      ctx->d_gas_ok, ncB, ctx->d_gas_reach, ctx->d_gas_rows, ctx->d_gas_boff, ctx->d_gas_blist, ctx->d_gas_coff,
+      ctx->d_gas_cstr, TJ);
   FORTE_LAUNCH_CHECK();
   return FORTE_OK;
 }
@@ -192,8 +252,13 @@ static void gas_release(forte_ctx *ctx) {
   cudaFree(ctx->d_gas_rows);
   cudaFree(ctx->d_gas_boff);
   cudaFree(ctx->d_gas_blist);
-  ctx->d_gas_rows = ctx->d_gas_boff = ctx->d_gas_blist = nullptr;
+  cudaFree(ctx->d_gas_coff);
+  cudaFree(ctx->d_gas_cstr);
+  cudaFree(ctx->d_gas_reach);
+  ctx->d_gas_rows = ctx->d_gas_boff = ctx->d_gas_blist = ctx->d_gas_coff = ctx->d_gas_cstr = nullptr;
+  ctx->d_gas_reach = nullptr;
   ctx->gas_nrows = 0;
+  for (int t = 0; t < 2; ++t) ctx->gas_pick[t] = ctx->gas_pick_mode[t] = -1;
   ctx->gas_on = false;
   ctx->gas_ndet = 0;
   ctx->gas_ndiag = 0;
@@ -304,6 +369,31 @@ int gas_set(forte_ctx *ctx, int nspace, const int *size, const int *gmin, const 
     FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_blist, blist.data(), sizeof(int) * blist.size(), cudaMemcpyHostToDevice));
     ctx->gas_nrows = (long long)rowsv.size();
     ctx->gas_maxnnz = maxnnz;
+  }
+  // per beta class its strings (ascending) and the classes its replacements reach
+  // (bit masks: the kept-only sigma needs at most 64 beta classes)
+  if (ncB <= 64) {
+    const SpinHost &B = ctx->sh[1];
+    std::vector<int> coff(ncB + 1, 0), cstr;
+    for (int b = 0; b < ncB; ++b) {
+      for (long long j = 0; j < B.N; ++j)
+        if (cls[1][j] == b) cstr.push_back((int)j);
+      coff[b + 1] = (int)cstr.size();
+    }
+    std::vector<unsigned long long> reach(ncB, 0ull);
+    for (long long j = 0; j < B.N; ++j)
+      for (int m = 0; m < B.nk; ++m) reach[cls[1][j]] |= 1ull << cls[1][B.list[(size_t)j * B.nk + m].J];
+    if (cudaMalloc(&ctx->d_gas_coff, sizeof(int) * coff.size()) != cudaSuccess ||
+        cudaMalloc(&ctx->d_gas_cstr, sizeof(int) * std::max<size_t>(1, cstr.size())) != cudaSuccess ||
+        cudaMalloc(&ctx->d_gas_reach, sizeof(unsigned long long) * reach.size()) != cudaSuccess) {
+      gas_release(ctx);
+      set_error("cudaMalloc of the restricted-sigma class lists failed");
+      return FORTE_ERR_ALLOC;
+    }
+    FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_coff, coff.data(), sizeof(int) * coff.size(), cudaMemcpyHostToDevice));
+    FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_cstr, cstr.data(), sizeof(int) * cstr.size(), cudaMemcpyHostToDevice));
+    FORTE_CUDA_TRY(cudaMemcpy(ctx->d_gas_reach, reach.data(), sizeof(unsigned long long) * reach.size(),
+                              cudaMemcpyHostToDevice));
   }
   ctx->gas_nc[0] = ncA;
   ctx->gas_nc[1] = ncB;

@@ -229,6 +229,10 @@ constexpr int WS_OFF_ACC = WS_OFF_B + WS_STAGES * MX_STAGE;
 // build A[i&1] and the gather rows of item i (`aFull`).  The producers, the MMA
 // thread and the epilogue run their tile rings across item boundaries, so the
 // set-up and the drain of one item overlap the tiles of its neighbours.
+// Shared-memory integer reduction at byte address addr.
+__device__ __forceinline__ void red_add(uint32_t addr, int v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 // Shared-memory integer reduction at byte address addr unless bit 1 of en is set (the
 // "no target" marker 0xFFFF of the scatter table), without a branch.
 __device__ __forceinline__ void red_add_if(uint32_t addr, int v, uint32_t en) {
@@ -253,10 +257,11 @@ __device__ __forceinline__ void red_add_if(uint32_t addr, int v, uint32_t en) {
 // Chi / Clo / Ct32: the C copies in positions, rows of NBpos.
 // Warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 5-7 item set-up and
 // write-out, 8 .. 8 + MX_EPI - 1 epilogue (MX_EPI / 4 warps per TMEM lane quarter).
-template <int MODE, typename TO>
+template <int MODE, typename TO, bool SPLIT>
 __global__ void __launch_bounds__(MX_THREADS, 1)
     k_ab_mma(const Repl *__restrict__ listA, int nkA, int nkB,
-             const uint16_t *__restrict__ tabL, const uint16_t *__restrict__ posOf, int nN, long long NA,
+             const uint16_t *__restrict__ tabL, const uint16_t *__restrict__ posOf, const int8_t *__restrict__ dcnt,
+             int nN, long long NA,
              long long NB, long long NBpos, const uint16_t *__restrict__ gTT_hi, const uint16_t *__restrict__ gTT_lo,
              const float *__restrict__ gT_t32, int npair, float gmax, const unsigned *__restrict__ cmax_bits,
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
@@ -266,8 +271,11 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sB = sm + WS_OFF_B;
   const long long NB4 = NBpos;                   // a multiple of 32
-  int *accb = (int *)(sm + WS_OFF_ACC);          // acc[2][NBpos], indexed by position
-  int *sJb = accb + 2 * NB4;                     // gathered strings J_k [2][64]
+  // accumulator row per buffer: [NBpos] by position, or with SPLIT [NBpos] for the
+  // positive contributions, [NBpos] for the negative ones and 32 spare words
+  const long long ACCW = SPLIT ? 2 * NB4 + 32 : NB4;
+  int *accb = (int *)(sm + WS_OFF_ACC);          // acc[2][ACCW]
+  int *sJb = accb + 2 * ACCW;                    // gathered strings J_k [2][64]
   uint64_t *bar = (uint64_t *)(((uintptr_t)(sJb + 128) + 15) & ~(uintptr_t)15);
   uint64_t *full = bar, *empty = bar + WS_STAGES, *tfull = bar + 2 * WS_STAGES, *tempty = tfull + WS_ACC;
   uint64_t *aFull = tempty + WS_ACC, *aEmpty = aFull + 2, *accReady = aEmpty + 2, *accDone = accReady + 2;
@@ -324,7 +332,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     const int st = tid - 160;
     for (long long i = 0; i < nloc + 2; ++i) {
       const int buf = (int)(i & 1);
-      int *acc = accb + buf * NB4;
+      int *acc = accb + buf * ACCW;
       if (i >= 2) {
         // write out item i-2 and clear its accumulator row
         if (!__all_sync(0xffffffffu, mbar_wait_ab(&accDone[buf], (uint32_t)(((i - 2) >> 1) & 1), sAbort))) {
@@ -336,15 +344,24 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
         const float *ss = Sss + v * v64 + Ia * NB;
         TO *out = S + v * v64 + Ia * NB;
         // every output received n_kl(beta) contributions carrying bits(1.5 2^23) each
+        // (SPLIT: npos(x) of them in the positive word, nneg(x) in the negative one,
+        // dcnt[x] = npos(x) - nneg(x))
         const uint32_t bias = (uint32_t)nkB * 0x4B400000u;
         // padding positions never receive a contribution and stay zero
         for (long long x = st; x < NB; x += 96) {
           const int ps = __ldg(posOf + x);
-          out[x] = (TO)((double)ss[x] + ldexp((double)(int)((uint32_t)acc[ps] - bias), -Sx));
+          uint32_t vfix;
+          if (SPLIT) {
+            vfix = (uint32_t)acc[ps] - (uint32_t)acc[NB4 + ps] - (uint32_t)(int)__ldg(dcnt + x) * 0x4B400000u;
+            acc[NB4 + ps] = 0;
+          } else {
+            vfix = (uint32_t)acc[ps] - bias;
+          }
+          out[x] = (TO)((double)ss[x] + ldexp((double)(int)vfix, -Sx));
           acc[ps] = 0;
         }
       } else {
-        for (long long x = st; x < NB4; x += 96) acc[x] = 0;
+        for (long long x = st; x < (SPLIT ? 2 * NB4 : NB4); x += 96) acc[x] = 0;
       }
       if (i >= nloc) continue;
       __syncwarp();
@@ -587,7 +604,7 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
     bool ok = true;
     for (long long i = 0; i < nloc && ok; ++i) {
       const int buf = (int)(i & 1);
-      int *acc = accb + buf * NB4;
+      int *acc = accb + buf * ACCW;
       const float fscale = ldexpf(1.f, sx_of((blockIdx.x + i * gridDim.x) / NA));
       const uint32_t acc_s = smem_u32(acc);
       if (!__all_sync(0xffffffffu, mbar_wait_ab(&accReady[buf], (uint32_t)((i >> 1) & 1), sAbort))) {
@@ -636,6 +653,19 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
           if (q >= nq) break;
           const uint4 tq = tg[q];
           const uint32_t wv[4] = {tq.x, tq.y, tq.z, tq.w};
+          if (SPLIT) {
+            // entry = byte offset of the word that takes the contribution: the target's
+            // positive or negative word (the sign of the replacement), or for a slot
+            // without target one of the 32 spare words, in the bank its target would
+            // have had, so every reduction of the warp still meets 32 distinct banks
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const uint32_t off = (c & 1) ? (wv[c >> 1] >> 16) : (wv[c >> 1] & 0xFFFFu);
+              const float tv = fmaf(__uint_as_float(ra[8 * q + c]), fscale, 12582912.0f);
+              red_add(acc_s + off, __float_as_int(tv));
+            }
+            continue;
+          }
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             // entry in the low half of en (the high half is ignored by the masks below)
@@ -669,8 +699,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 
 // ------------------------------------------------------------ host side
 
-static size_t mx_smem_bytes(long long NBpos) {
-  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)NBpos + 2 * 64 * 4 + 16 +
+static size_t mx_smem_bytes(long long NBpos, bool split) {
+  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)(split ? 2 * NBpos + 32 : NBpos) + 2 * 64 * 4 + 16 +
          8 * (2 * WS_STAGES + 2 * WS_ACC + 9) + 16 + 64;
 }
 
@@ -733,20 +763,44 @@ static int ab_positions(forte_ctx *ctx) {
       tab[(size_t)pos * 128 + r.pair] = (uint16_t)(posOf[r.J] | (r.sgn < 0 ? 0x4000 : 0));
     }
   }
-  // the same entries lane-contiguous for the epilogue's coalesced loads, each as the
-  // byte offset of the target in the accumulator row with the sign in bit 0
-  // (positions < 16384, so offsets fit 16 bits with bits 0-1 free; 0xFFFF, bit 1 set,
-  // marks "no target")
+  // The same entries lane-contiguous for the epilogue's coalesced loads.  When the
+  // split accumulator row fits in shared memory, an entry is the byte offset of the
+  // word that takes the contribution: 4 pos(target) for a positive sign,
+  // 4 (NBpos + pos(target)) for a negative one, and for a slot without target
+  // 4 (2 NBpos + (lane ^ h_rs)), the spare word in the bank the target would have had
+  // (pos = 32 j + h(string) and h(E_rs J) = h(J) ^ code[r] ^ code[s]).  Otherwise it is
+  // the byte offset of the target with the sign in bit 0 (positions < 16384, so
+  // offsets fit 16 bits with bits 0-1 free; 0xFFFF, bit 1 set, marks "no target").
+  const bool split = mx_smem_bytes(NBpos, true) <= 232448;
+  std::vector<unsigned> hpair(128, 0u);
+  for (int r = 0; r < n; ++r)
+    for (int s2 = 0; s2 <= r; ++s2) hpair[r * (r + 1) / 2 + s2] = (r == s2) ? 0u : (best[r] ^ best[s2]);
   std::vector<uint16_t> tabL(tab.size(), 0xFFFFu);
   for (long long pos = 0; pos < rows; ++pos) {
     const long long t = pos / 128, g = (pos % 128) / 32, ln = pos % 32;
     for (int c = 0; c < 16; ++c)
       for (int e = 0; e < 8; ++e) {
-        const uint16_t en = tab[(size_t)pos * 128 + c * 8 + e];
-        tabL[(size_t)((((t * 4 + g) * 16 + c) * 32 + ln) * 8 + e)] =
-            en == 0xFFFFu ? (uint16_t)0xFFFFu : (uint16_t)(((en & 0x3FFFu) << 2) | ((en >> 14) & 1u));
+        const int rs = c * 8 + e;
+        const uint16_t en = tab[(size_t)pos * 128 + rs];
+        uint16_t v;
+        if (split)
+          v = en == 0xFFFFu ? (uint16_t)(4 * (2 * NBpos + (long long)((unsigned)ln ^ hpair[rs])))
+                            : (uint16_t)(4 * ((en & 0x3FFFu) + ((en >> 14) & 1u ? NBpos : 0)));
+        else
+          v = en == 0xFFFFu ? (uint16_t)0xFFFFu : (uint16_t)(((en & 0x3FFFu) << 2) | ((en >> 14) & 1u));
+        tabL[(size_t)((((t * 4 + g) * 16 + c) * 32 + ln) * 8 + e)] = v;
       }
   }
+  // npos(x) - nneg(x): signs of the replacements that reach each beta string
+  std::vector<int8_t> dcnt((size_t)NB, 0);
+  for (long long J = 0; J < NB; ++J)
+    for (int e = 0; e < B.nk; ++e) {
+      const Repl &r = B.list[(size_t)J * B.nk + e];
+      dcnt[r.J] = (int8_t)(dcnt[r.J] + (r.sgn < 0 ? -1 : 1));
+    }
+  FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abDcnt, dcnt.size()));
+  FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abDcnt, dcnt.data(), dcnt.size(), cudaMemcpyHostToDevice));
+  ctx->ab_split = split;
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abTabL, sizeof(uint16_t) * tabL.size()));
   FORTE_CUDA_TRY(cudaMemcpy(ctx->d_abTabL, tabL.data(), sizeof(uint16_t) * tabL.size(), cudaMemcpyHostToDevice));
   FORTE_CUDA_TRY(cudaMalloc(&ctx->d_abPosOf, sizeof(uint16_t) * posOf.size()));
@@ -866,7 +920,8 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   if (rc) return rc;
   if (ab) {
     const int nN = ctx->npair <= 112 ? 112 : 128;
-    const size_t smem = mx_smem_bytes(NBpos);
+    const bool split = ctx->ab_split;
+    const size_t smem = mx_smem_bytes(NBpos, split);
     if (smem > 232448) {
       set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;
@@ -875,21 +930,22 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
     FORTE_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
     const long long nitems = NA * nvec;
     dim3 grid((unsigned)std::min<long long>(nitems, nsm));
-    if (mode == FORTE_BF16X2) {
-      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_BF16X2, T>));
-      FORTE_PROF(ctx, "ab_mma_bf16x2");
-      k_ab_mma<FORTE_BF16X2, T><<<grid, MX_THREADS, smem, st>>>(
-          ctx->sd[0].list, nkA, nkB, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
-          ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, Phi, Plo, nullptr, S32, S, nitems, ctx->d_err);
+    auto launch = [&](auto kern, const char *name, const uint16_t *ph, const uint16_t *pl, const float *pt) -> int {
+      FORTE_CUDA_TRY(set_smem_optin_max((const void *)kern));
+      FORTE_PROF(ctx, name);
+      kern<<<grid, MX_THREADS, smem, st>>>(ctx->sd[0].list, nkA, nkB, ctx->d_abTabL, ctx->d_abPosOf, ctx->d_abDcnt, nN,
+                                           NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo, ctx->d_gT_t32, ctx->npair,
+                                           ctx->gmax, cmax, ph, pl, pt, S32, S, nitems, ctx->d_err);
       FORTE_LAUNCH_CHECK();
-    } else {
-      FORTE_CUDA_TRY(set_smem_optin_max((const void *)k_ab_mma<FORTE_TF32, T>));
-      FORTE_PROF(ctx, "ab_mma_tf32");
-      k_ab_mma<FORTE_TF32, T><<<grid, MX_THREADS, smem, st>>>(
-          ctx->sd[0].list, nkA, nkB, ctx->d_abTabL, ctx->d_abPosOf, nN, NA, NB, NBpos, ctx->d_gTT_hi, ctx->d_gTT_lo,
-          ctx->d_gT_t32, ctx->npair, ctx->gmax, cmax, nullptr, nullptr, Pt32, S32, S, nitems, ctx->d_err);
-      FORTE_LAUNCH_CHECK();
-    }
+      return FORTE_OK;
+    };
+    if (mode == FORTE_BF16X2)
+      rc = split ? launch(k_ab_mma<FORTE_BF16X2, T, true>, "ab_mma_bf16x2", Phi, Plo, nullptr)
+                 : launch(k_ab_mma<FORTE_BF16X2, T, false>, "ab_mma_bf16x2", Phi, Plo, nullptr);
+    else
+      rc = split ? launch(k_ab_mma<FORTE_TF32, T, true>, "ab_mma_tf32", nullptr, nullptr, Pt32)
+                 : launch(k_ab_mma<FORTE_TF32, T, false>, "ab_mma_tf32", nullptr, nullptr, Pt32);
+    if (rc) return rc;
   } else if (sizeof(T) == 8) {
     FORTE_PROF(ctx, "f32_to_f64");
     k_f32_to_f64<<<(unsigned)std::min<size_t>((nf + 255) / 256, 152 * 32), 256, 0, st>>>(S32, (double *)(void *)S,

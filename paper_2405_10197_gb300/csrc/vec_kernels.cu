@@ -51,20 +51,36 @@ __device__ __forceinline__ double block_sum_t(T v, double *red) {
   return red[0];
 }
 
-// part[b][m] -> out[m] (sum over b).  grid.x = m.
-__global__ void k_sum_partials(const double *__restrict__ part, int nblk, int m, double *__restrict__ out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[(long long)b * m + blockIdx.x];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) out[blockIdx.x] = s;
+// Second pass of a reduction, fused into the kernel that writes the partials: every
+// block publishes its partials part[block][0..m) and counts itself in; the last block
+// to arrive sums part[b][c] over b (strided by thread, then block_sum: the order of
+// a separate 256-thread pass) into out[c] and resets the counter for the next
+// launch on the stream.  No block waits for another.
+__device__ __forceinline__ void last_block_sums(const double *part, int m, double *__restrict__ out,
+                                                unsigned *counter, double *red) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nblk = (int)gridDim.x;
+  for (int c = 0; c < m; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += __ldcg(part + (long long)b * m + c);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) out[c] = s;
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 // part[block][i] = sum over the block's chunk of V_i . x   (i < nv)
 template <typename T>
 __global__ void __launch_bounds__(VK_THREADS) k_multidot(const T *__restrict__ V, int nv, long long ld,
                                                          const T *__restrict__ x, long long n,
-                                                         double *__restrict__ part) {
+                                                         double *__restrict__ part, double *__restrict__ out,
+                                                         unsigned *counter) {
   __shared__ double red[32];
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
   T xr[VK_EPT];
@@ -84,6 +100,7 @@ __global__ void __launch_bounds__(VK_THREADS) k_multidot(const T *__restrict__ V
     const double at = block_sum_t<T>(a, red);
     if (threadIdx.x == 0) part[(long long)blockIdx.x * nv + i] = at;
   }
+  last_block_sums(part, nv, out, counter, red);
 }
 
 // out_{c0+c} = sum_i coef[i*ncomb + c0 + c] V_i  for c < NC.  NC is a template
@@ -118,7 +135,7 @@ template <typename T>
 __global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
     const T *__restrict__ B, const T *__restrict__ S, int k, long long ld,
     const double *__restrict__ u, double theta, const double *__restrict__ hd, double guard,
-    T *__restrict__ t, long long n, double *__restrict__ part) {
+    T *__restrict__ t, long long n, double *__restrict__ part, double *__restrict__ out, unsigned *counter) {
   __shared__ double red[32];
   __shared__ T su[VK_MAXV];
   for (int i = threadIdx.x; i < k; i += blockDim.x) su[i] = (T)u[i];
@@ -143,6 +160,7 @@ __global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
   }
   const double rt = block_sum_t<T>(rr, red);
   if (threadIdx.x == 0) part[blockIdx.x] = rt;
+  last_block_sums(part, 1, out, counter, red);
 }
 
 // t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2.
@@ -152,7 +170,8 @@ template <typename T, bool DOTS>
 __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict__ Bm, int k,
                                                             long long ld, const double *__restrict__ c,
                                                             const T *t_in, T *t_out, long long n,
-                                                            double *__restrict__ part) {
+                                                            double *__restrict__ part, double *__restrict__ out,
+                                                            unsigned *counter) {
   __shared__ double red[32];
   __shared__ T sc[VK_MAXV];
   for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = (T)c[i];
@@ -198,6 +217,7 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict_
   }
   const double nt = block_sum_t<T>(nn, red);
   if (threadIdx.x == 0) part[(long long)blockIdx.x * (k + 1) + k] = nt;
+  last_block_sums(part, k + 1, out, counter, red);
 }
 
 // y = a x + b y
@@ -211,7 +231,8 @@ __global__ void k_axpby(double a, const double *__restrict__ x, double b, double
 __global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__restrict__ r, double theta,
                                                             const double *__restrict__ hd, double guard,
                                                             double *__restrict__ z, long long n,
-                                                            double *__restrict__ part) {
+                                                            double *__restrict__ part, double *__restrict__ out,
+                                                            unsigned *counter) {
   __shared__ double red[32];
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
   double acc = 0.0;
@@ -228,6 +249,7 @@ __global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__rest
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  last_block_sums(part, 1, out, counter, red);
 }
 
 template <typename T>
@@ -285,10 +307,17 @@ __global__ void k_nonfinite(const double *__restrict__ x, long long n, int *flag
 
 // ------------------------------------------------------------------ host wrappers
 
-static int part_buffer(forte_ctx *ctx, size_t doubles, double **p) {
+// Partials of the reductions in the context's small scratch, and the arrival counter
+// of the fused second pass (zeroed once; every reduction leaves it at zero).
+static int part_buffer(forte_ctx *ctx, size_t doubles, double **p, unsigned **counter) {
   int rc = ctx->sc_small.ensure(sizeof(double) * (doubles + 64));
   if (rc) return rc;
   *p = (double *)ctx->sc_small.ptr;
+  if (!ctx->d_vk_count) {
+    FORTE_CUDA_TRY(cudaMalloc(&ctx->d_vk_count, sizeof(unsigned)));
+    FORTE_CUDA_TRY(cudaMemsetAsync(ctx->d_vk_count, 0, sizeof(unsigned), ctx->stream));
+  }
+  *counter = ctx->d_vk_count;
   return FORTE_OK;
 }
 
@@ -298,18 +327,12 @@ static int vk_multidot_t(forte_ctx *ctx, const T *V, int nv, long long ld, const
   if (nv > VK_MAXV) { set_error("multidot: too many vectors (%d)", nv); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
-  int rc = part_buffer(ctx, (size_t)nb * nv, &part);
+  unsigned *cnt;
+  int rc = part_buffer(ctx, (size_t)nb * nv, &part, &cnt);
   if (rc) return rc;
-  {
-    FORTE_PROF(ctx, "multidot");
-    k_multidot<T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part);
+  FORTE_PROF(ctx, "multidot");
+  k_multidot<T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part, out, cnt);
   FORTE_LAUNCH_CHECK();
-  }
-  {
-    FORTE_PROF(ctx, "sum_partials");
-    k_sum_partials<<<nv, 256, 0, ctx->stream>>>(part, (int)nb, nv, out);
-  FORTE_LAUNCH_CHECK();
-  }
   return FORTE_OK;
 }
 
@@ -342,19 +365,13 @@ static int vk_residual_precond_t(forte_ctx *ctx, const T *B, const T *S, int k, 
   if (k > VK_MAXV) { set_error("residual: subspace too large (%d)", k); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
-  int rc = part_buffer(ctx, nb, &part);
+  unsigned *cnt;
+  int rc = part_buffer(ctx, nb, &part, &cnt);
   if (rc) return rc;
-  {
-    FORTE_PROF(ctx, "residual_precond");
-    k_residual_precond<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
-                                                          n, part);
+  FORTE_PROF(ctx, "residual_precond");
+  k_residual_precond<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t, n,
+                                                            part, rnorm2, cnt);
   FORTE_LAUNCH_CHECK();
-  }
-  {
-    FORTE_PROF(ctx, "sum_partials");
-    k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, rnorm2);
-  FORTE_LAUNCH_CHECK();
-  }
   return FORTE_OK;
 }
 
@@ -364,21 +381,15 @@ static int vk_orth_update_t(forte_ctx *ctx, const T *B, int k, long long ld, con
   if (k + 1 > VK_MAXV) { set_error("orth: subspace too large (%d)", k); return FORTE_ERR_ARG; }
   unsigned nb = vk_blocks(n);
   double *part;
-  int rc = part_buffer(ctx, (size_t)nb * (k + 1), &part);
+  unsigned *cnt;
+  int rc = part_buffer(ctx, (size_t)nb * (k + 1), &part, &cnt);
   if (rc) return rc;
-  {
-    FORTE_PROF(ctx, "orth_update");
-    if (dots)
-      k_orth_update<T, true><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
-    else
-      k_orth_update<T, false><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part);
+  FORTE_PROF(ctx, "orth_update");
+  if (dots)
+    k_orth_update<T, true><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part, dots_out, cnt);
+  else
+    k_orth_update<T, false><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n, part, dots_out, cnt);
   FORTE_LAUNCH_CHECK();
-  }
-  {
-    FORTE_PROF(ctx, "sum_partials");
-    k_sum_partials<<<k + 1, 256, 0, ctx->stream>>>(part, (int)nb, k + 1, dots_out);
-  FORTE_LAUNCH_CHECK();
-  }
   return FORTE_OK;
 }
 
@@ -454,18 +465,12 @@ int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, 
                    long long n) {
   unsigned nb = vk_blocks(n);
   double *part;
-  int rc = part_buffer(ctx, nb, &part);
+  unsigned *cnt;
+  int rc = part_buffer(ctx, nb, &part, &cnt);
   if (rc) return rc;
-  {
-    FORTE_PROF(ctx, "precond_dot");
-    k_precond_dot<<<nb, VK_THREADS, 0, ctx->stream>>>(r, theta, ctx->d_hdiag, guard, z, n, part);
-    FORTE_LAUNCH_CHECK();
-  }
-  {
-    FORTE_PROF(ctx, "sum_partials");
-    k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, (int)nb, 1, dot_out);
-    FORTE_LAUNCH_CHECK();
-  }
+  FORTE_PROF(ctx, "precond_dot");
+  k_precond_dot<<<nb, VK_THREADS, 0, ctx->stream>>>(r, theta, ctx->d_hdiag, guard, z, n, part, dot_out, cnt);
+  FORTE_LAUNCH_CHECK();
   return FORTE_OK;
 }
 

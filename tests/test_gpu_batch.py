@@ -85,8 +85,17 @@ def test_batch_autotuner_reports_every_class():
     tun = fg.forte_batch_tuning()
     classes = {(p["norb"], p["nalpha"], p["nbeta"]) for p in probs}
     assert {(t["norb"], t["nalpha"], t["nbeta"]) for t in tun} == classes
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
     for t in tun:
         assert t["threads"] in (128, 256, 512) and t["tile"] in (16, 32, 64) and t["sigma_ms"] > 0
+        assert t["single_iter_ms"] > 0 and t["ctas_per_sm"] >= 1
+        assert t["problems"] == sum(1 for p in probs if (p["norb"], p["nalpha"], p["nbeta"]) ==
+                                    (t["norb"], t["nalpha"], t["nbeta"]))
+        # the documented rule: class launch when one sigma round of the class costs
+        # no more than one single-path iteration of each of its problems
+        waves = math.ceil(t["problems"] / (t["ctas_per_sm"] * nsm))
+        cta = t["sigma_ms"] * waves <= t["problems"] * t["single_iter_ms"]
+        assert t["path"] == ("class launch" if cta else "single-problem path")
 
 
 @pytest.mark.parametrize("name", ["cas1010_seed5_3roots", "cas1212_seed1_4roots"])

@@ -36,10 +36,13 @@ def _problem(n, na, nb, spaces, gmin, gmax, precision=fg.FORTE_FP64, seed=None):
     return prob, h, eri, nd
 
 
+@pytest.mark.parametrize("route", [-1, 0, 1])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("n,na,nb,spaces,gmin,gmax", GAS_SETS)
-def test_gas_sigma_matches_oracle(n, na, nb, spaces, gmin, gmax, mode):
+def test_gas_sigma_matches_oracle(n, na, nb, spaces, gmin, gmax, mode, route):
+    # route -1: timed choice, 0: full grid + projection, 1: kept-determinant kernel
     prob, h, eri, nd = _problem(n, na, nb, spaces, gmin, gmax, mode)
+    fg.forte_set_gas_route(prob.ctx, route)
     try:
         keep = oracle.gas_allowed(n, na, nb, spaces, gmin, gmax)
         assert nd == int(keep.sum())
@@ -56,10 +59,14 @@ def test_gas_sigma_matches_oracle(n, na, nb, spaces, gmin, gmax, mode):
         prob.close()
 
 
+@pytest.mark.parametrize("route", [0, 1])
 @pytest.mark.parametrize("mode", [fg.FORTE_FP64, fg.FORTE_OZ64, fg.FORTE_BF16X2])
 @pytest.mark.parametrize("n,na,nb,spaces,gmin,gmax", GAS_SETS[:3])
-def test_gas_davidson_matches_dense(n, na, nb, spaces, gmin, gmax, mode):
+def test_gas_davidson_matches_dense(n, na, nb, spaces, gmin, gmax, mode, route):
+    # route 1 in the BF16x2 mode runs the FP32 kept-determinant kernel in the
+    # reduced-precision phase and the FP64 one in the refinement
     prob, h, eri, nd = _problem(n, na, nb, spaces, gmin, gmax, mode)
+    fg.forte_set_gas_route(prob.ctx, route)
     try:
         w, V = oracle.solve_dense_gas(n, na, nb, h, eri, spaces, gmin, gmax, nroots=3)
         E, C, rn, it = prob.davidson(nroots=3, tol=1e-9)
@@ -122,5 +129,26 @@ def test_gas_reset_and_errors():
         assert prob.set_gas((), (), ()) == prob.ndet
         assert float((prob.sigma(C) - S_full).abs().max()) <= 1e-13 * float(S_full.abs().max())
         assert bool(torch.isfinite(prob.hdiag()).all())
+    finally:
+        prob.close()
+
+
+def test_gas_timed_route_records_both_timings():
+    # CAS(10,10) under RAS(2h, 2p) keeps well below a quarter of the determinants:
+    # the first sigma times both routes and keeps the faster
+    n, na, nb, spaces, gmin, gmax = 10, 5, 5, (3, 4, 3), (4, 0, 0), (6, 10, 2)
+    prob, h, eri, nd = _problem(n, na, nb, spaces, gmin, gmax, fg.FORTE_FP64)
+    try:
+        assert 4 * nd <= prob.ndet
+        assert fg.forte_get_gas_route(prob.ctx)[0] == -1
+        C = si.random_vectors(1, prob.na, prob.nb, seed=4)
+        S = prob.sigma(torch.tensor(C, device="cuda")).cpu().numpy()
+        r64, r32, ms = fg.forte_get_gas_route(prob.ctx)
+        assert r64 in (0, 1) and ms[0] > 0 and ms[1] > 0
+        assert r64 == (1 if ms[1] <= ms[0] else 0)
+        S_ref = oracle.sigma_gas(n, na, nb, h, eri, C, spaces, gmin, gmax)
+        assert np.abs(S - S_ref).max() < 1e-12 * np.abs(S_ref).max()
+        with pytest.raises(fg.ForteError):
+            fg.forte_set_gas_route(prob.ctx, 2)
     finally:
         prob.close()
