@@ -560,7 +560,7 @@ def run_batch(args):
         out[name] = {"seconds": _sig(dt), "solves_per_s": _sig(len(probs) / dt), "not_converged": int((st != 0).sum()),
                      "not_converged_instances": [dict(index=int(i), norb=probs[i]["norb"], nroots=probs[i]["nroots"],
                                                       status=int(st[i])) for i in np.nonzero(st)[0][:16]],
-                     "single_path_above_1e5_det": big, "tuning": tun}
+                     "single_path_above_1e5_det": big, "paths": fg.forte_batch_stats(), "tuning": tun}
     diffs = [float(np.max(np.abs(np.array(a) - np.array(b)))) for a, b in zip(energies["fp64"], energies[mixed])]
     out["max_energy_diff_mixed_vs_fp64"] = max(diffs)
     worst = np.argsort(diffs)[::-1][:5]

@@ -216,8 +216,15 @@ int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
  * (theta - H_II)^-1 with |denominator| clamped to denom_guard; classical
  * Gram-Schmidt, with a second pass when the first removes more than half of
  * the correction's squared norm; subspace collapse (forte_set_davidson_params).
+ * When the largest residual has not halved over 50 iterations (the target state
+ * is not dominated by the determinants of lowest H_II, where the diagonal
+ * preconditioner fails), the solve continues from the Ritz vectors with
+ * Jacobi-Davidson (corrections from preconditioned CG on the projected
+ * correction equation, thick restart) in the same arithmetic, within the same
+ * max_iter budget (Davidson-Liu iterations + Jacobi-Davidson outer steps).
  * In a mixed mode the inner iterations use that mode's sigma and the final
- * residuals and energies are refined with FP64 sigma builds until the FP64
+ * residuals and energies are refined with FP64-class sigma builds
+ * (Jacobi-Davidson whose inner solves use the mode's sigma) until the FP64
  * residual meets tol.  Results stay in the context (forte_get_roots).
  * Returns FORTE_ERR_NOT_CONVERGED when max_iter is reached (results kept). */
 int forte_davidson(forte_ctx *ctx, int nroots, double tol);
@@ -313,7 +320,9 @@ int forte_rdm3(forte_ctx *ctx, const double *C, double *g3);
  *              Vectors, subspace and eigenproblem are FP64 in every mode.
  *   tol        max residual 2-norm per root; max_iter the iteration cap (<= 0: 400)
  * Davidson as forte_davidson (guess, preconditioner, 12 vectors per root,
- * collapse to 2 per root).  status_out (host [nprob], may be NULL) gets each
+ * collapse to 2 per root); a problem whose in-CTA solve does not converge within
+ * max_iter is solved again on the single-problem path (which continues a stalled
+ * Davidson-Liu with Jacobi-Davidson).  status_out (host [nprob], may be NULL) gets each
  * problem's status.  Returns the worst status (FORTE_ERR_NOT_CONVERGED keeps
  * energies); FORTE_ERR_ALLOC when the pooled workspace (about
  * (2 * 12 * nroots + 2 * nroots + 4) * N_det doubles per class-launch problem)
@@ -332,6 +341,11 @@ int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *
  * and the resident CTAs per SM of its launch. */
 int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads, int *tile,
                        double *sigma_ms, int *path, double *single_iter_ms, int *problems, int *ctas_per_sm);
+
+/* Problem counts of the last forte_batch_solve (host outputs, may be NULL): solved
+ * in class launches, sent to the single-problem path, and solved again on the
+ * single-problem path after their in-CTA Davidson-Liu did not converge. */
+int forte_batch_stats(int *class_launch, int *single_path, int *retried);
 
 /* FP64 sigma = H C that allocates no device memory (the paper has no
  * counterpart; this is a service for callers of the library).  It is meant for

@@ -89,6 +89,7 @@ def library():
         "forte_set_wait_budget": [vp, ctypes.c_ulonglong],
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
         "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
+        "forte_batch_stats": [vp, vp, vp],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -361,6 +362,13 @@ def forte_batch_tuning():
                         path="class launch" if path[k] == 0 else "single-problem path",
                         single_iter_ms=float(single[k]), problems=int(nprob[k]), ctas_per_sm=int(occ[k])))
     return out
+
+
+def forte_batch_stats():
+    """Problem counts of the last forte_batch_solve: class launches, single-problem path, retried."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(library().forte_batch_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return dict(class_launch=a.value, single_path=b.value, retried=c.value)
 
 
 def forte_profile_enable(ctx, on):

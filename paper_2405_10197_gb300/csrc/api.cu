@@ -197,7 +197,15 @@ struct DvResult {
   std::vector<double> E, rn;
   int iters = 0;
   bool converged = false;
+  bool stalled = false;  // Davidson-Liu stopped early: the residual stopped falling
 };
+
+// Davidson-Liu with the diagonal preconditioner stalls when the target state is
+// not dominated by the determinants of lowest H_II (theta then sits among many
+// diagonal values and the corrections are nearly unit vectors).  The iteration is
+// declared stalled when its largest residual has not halved over DV_STALL
+// iterations; the solve then continues with Jacobi-Davidson from the Ritz vectors.
+constexpr int DV_STALL = 50;
 
 // Index of the largest |x| (ties: lowest index) and the sign of that entry.
 __global__ void k_absmax(const double *__restrict__ x, long long n, double *bval, long long *bidx) {
@@ -408,6 +416,9 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
   res.E.assign(nroots, 0.0);
   res.rn.assign(nroots, INFINITY);
   res.converged = false;
+  res.stalled = false;
+  double best_rn = INFINITY;
+  int best_it = 0;
   for (int it = 1;; ++it) {
     // Rayleigh-Ritz on the symmetrised subspace matrix
     Gk.assign((size_t)k * k, 0.0);
@@ -437,7 +448,13 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     }
     res.iters = it;
     if (bad) { set_error("non-finite residual or eigenvalue in Davidson"); return FORTE_ERR_NUMERIC; }
-    bool stop = all || it >= max_iter || k >= Nsp;
+    const double max_rn = *std::max_element(res.rn.begin(), res.rn.end());
+    if (max_rn < 0.5 * best_rn) {
+      best_rn = max_rn;
+      best_it = it;
+    }
+    res.stalled = !all && it - best_it >= DV_STALL;
+    bool stop = all || it >= max_iter || k >= Nsp || res.stalled;
     if (stop) {
       coef.assign((size_t)k * nroots, 0.0);
       for (int i = 0; i < k; ++i)
@@ -918,6 +935,15 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;  // an expired wait explains the failure
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = res.iters;
+    if (res.stalled && res.iters < ctx->dv_max_iter) {
+      // Jacobi-Davidson from the Ritz vectors, inner solves in the same arithmetic
+      const int it_dl = res.iters;
+      rc = refine_jd(ctx, nroots, tol, ctx->precision, ctx->precision, ctx->d_roots, ctx->d_roots,
+                     std::max(1, std::min(60, ctx->dv_max_iter - it_dl)), res);
+      if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;
+      if ((rc = mixed_status(ctx))) return rc;
+      ctx->dv_iters = it_dl + res.iters;
+    }
   } else {
     // Davidson with the reduced-precision sigma down to a residual the mixed
     // operator can still resolve, then FP64 Jacobi-Davidson refinement whose

@@ -776,6 +776,7 @@ struct TuneRecord {
 };
 std::mutex g_tune_mu;
 std::vector<TuneRecord> g_tune;
+int g_stats[3] = {0, 0, 0};  // last batch: problems in class launches, on the single-problem path, retried
 
 template <int NT>
 cudaError_t launch_class(const BClass &c, size_t smem, cudaStream_t st) {
@@ -1221,8 +1222,13 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
   // as one graph and launched without waiting; the single-problem path runs on
   // the worker threads meanwhile (their kernels take the SMs the classes leave)
   std::vector<size_t> launched;
+  int n_launched = 0, n_retried = 0;
+  const int n_single = (int)singles.size();
   for (size_t ci = 0; ci < classes.size(); ++ci)
-    if (classes[ci].path == 0) launched.push_back(ci);
+    if (classes[ci].path == 0) {
+      launched.push_back(ci);
+      n_launched += (int)classes[ci].probs.size();
+    }
   cudaError_t ce = cudaSuccess;
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
@@ -1272,17 +1278,48 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     std::vector<int> sth(nprob, FORTE_OK);
     FORTE_CUDA_TRY(cudaMemcpy(Eh.data(), dbuf + off_E, sizeof(double) * nE, cudaMemcpyDeviceToHost));
     FORTE_CUDA_TRY(cudaMemcpy(sth.data(), dbuf + off_st, sizeof(int) * nprob, cudaMemcpyDeviceToHost));
-    std::lock_guard<std::mutex> lock(mu);
-    for (size_t ci : launched)
-      for (int i : classes[ci].probs) {
-        for (int r = 0; r < nroots[i]; ++r) E_out[eoff[i] + r] = Eh[eoff[i] + r];
-        note(i, sth[i], sth[i] == FORTE_ERR_NOT_CONVERGED ? "Davidson did not converge"
-                                                            : (sth[i] ? "non-finite residual" : ""));
-      }
+    // a problem whose in-CTA Davidson-Liu did not converge is solved again on the
+    // single-problem path, whose solver continues a stalled Davidson-Liu with
+    // Jacobi-Davidson
+    std::vector<int> retry;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      for (size_t ci : launched)
+        for (int i : classes[ci].probs) {
+          for (int r = 0; r < nroots[i]; ++r) E_out[eoff[i] + r] = Eh[eoff[i] + r];
+          if (sth[i] == FORTE_ERR_NOT_CONVERGED) {
+            retry.push_back(i);
+            continue;
+          }
+          note(i, sth[i], sth[i] ? "non-finite residual" : "");
+        }
+    }
+    if (!retry.empty()) {
+      singles = retry;
+      next_single = 0;
+      std::vector<std::thread> workers;
+      for (int w = 0; w < std::min<int>(BT_WORKERS, (int)singles.size()); ++w) workers.emplace_back(single_worker);
+      for (auto &x : workers) x.join();
+    }
+    n_retried = (int)retry.size();
   }
 
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_stats[0] = n_launched;
+    g_stats[1] = n_single;
+    g_stats[2] = n_retried;
+  }
   if (worst) set_error("%s", first_msg.c_str());
   return worst;
+}
+
+extern "C" int forte_batch_stats(int *class_launch, int *single_path, int *retried) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (class_launch) *class_launch = g_stats[0];
+  if (single_path) *single_path = g_stats[1];
+  if (retried) *retried = g_stats[2];
+  return FORTE_OK;
 }
 
 extern "C" int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads,

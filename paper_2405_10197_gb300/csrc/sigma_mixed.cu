@@ -215,7 +215,13 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 // reductions are native on the SM, FP32 ones are not; the sum is exact and
 // independent of the order of the atomics.
 
-constexpr int WS_STAGES = 3;                              // B operand ring
+// C-tile stages of the producer ring.  Each stage is 32 KB of shared memory, and
+// what the kernel leaves of the SM's 256 KB is the L1 cache that holds the
+// scatter table of the current and the next tile (28 KB each).
+#ifndef FORTE_AB_STAGES
+#define FORTE_AB_STAGES 3
+#endif
+constexpr int WS_STAGES = FORTE_AB_STAGES;                // B operand ring
 constexpr int WS_ACC = 4;                                 // TMEM accumulators of 128 columns
 constexpr int MX_A_BYTES = 32768;                         // A operand: 2 x 16 KB
 constexpr int WS_OFF_B = 2 * MX_A_BYTES;                  // A double-buffered across items

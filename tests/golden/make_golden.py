@@ -31,6 +31,9 @@ JOBS = {
     "cas1212_seed3_3roots": dict(kind="integrals", norb=12, nalpha=6, nbeta=6, n_l=24, seed=3, nroots=3,
                                  tol=1e-10, sa_rdms=True),
     "cas1010_seed5_3roots": dict(kind="integrals", norb=10, nalpha=5, nbeta=5, n_l=20, seed=5, nroots=3),
+    # instance 58 of the batched workload (seed 1058): its ground state is not carried by
+    # the determinants of lowest H_II, where the diagonal-preconditioned Davidson-Liu stalls
+    "batch1058_cas1010": dict(kind="integrals", norb=10, nalpha=5, nbeta=5, n_l=20, seed=1058, nroots=1, tol=1e-7),
 }
 
 
