@@ -215,17 +215,24 @@ __global__ void k_f32_to_f64(const float *__restrict__ a, double *__restrict__ b
 // reductions are native on the SM, FP32 ones are not; the sum is exact and
 // independent of the order of the atomics.
 
-// C-tile stages of the producer ring.  Each stage is 32 KB of shared memory, and
-// what the kernel leaves of the SM's 256 KB is the L1 cache that holds the
-// scatter table of the current and the next tile (28 KB each).
-#ifndef FORTE_AB_STAGES
-#define FORTE_AB_STAGES 3
+// C-tile stages of the producer ring, per mode.  Each stage is 32 KB of shared
+// memory, and what the kernel leaves of the SM's 256 KB is the L1 cache that holds
+// the scatter table of the current and the next tile (28 KB each).  Measured at
+// CAS(14,14): BF16x2 0.82 ms with 3 stages, 1.09 ms with 2; TF32 (whose producers
+// transpose through registers) 1.72 ms with 3, 1.50 ms with 2.
+#ifndef FORTE_AB_STAGES_BF16
+#define FORTE_AB_STAGES_BF16 3
 #endif
-constexpr int WS_STAGES = FORTE_AB_STAGES;                // B operand ring
+#ifndef FORTE_AB_STAGES_TF32
+#define FORTE_AB_STAGES_TF32 2
+#endif
+__host__ __device__ constexpr int ws_stages(int mode) {
+  return mode == FORTE_BF16X2 ? FORTE_AB_STAGES_BF16 : FORTE_AB_STAGES_TF32;
+}
 constexpr int WS_ACC = 4;                                 // TMEM accumulators of 128 columns
 constexpr int MX_A_BYTES = 32768;                         // A operand: 2 x 16 KB
 constexpr int WS_OFF_B = 2 * MX_A_BYTES;                  // A double-buffered across items
-constexpr int WS_OFF_ACC = WS_OFF_B + WS_STAGES * MX_STAGE;
+__host__ __device__ constexpr int ws_off_acc(int mode) { return WS_OFF_B + ws_stages(mode) * MX_STAGE; }
 // warp roles: 0-3 producers, 4 MMA issuer (and TMEM owner), 5-7 item set-up and
 // write-out, 8-15 epilogue
 
@@ -273,6 +280,8 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
              const uint16_t *__restrict__ Chi, const uint16_t *__restrict__ Clo, const float *__restrict__ Ct32,
              const float *__restrict__ Sss, TO *__restrict__ S, long long nitems, int *__restrict__ err) {
   extern __shared__ uint8_t smem_raw[];
+  constexpr int WS_STAGES = ws_stages(MODE);
+  constexpr int WS_OFF_ACC = ws_off_acc(MODE);
   // the swizzle pattern is a function of the shared-space address: align there
   uint8_t *sm = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sB = sm + WS_OFF_B;
@@ -705,9 +714,9 @@ __global__ void __launch_bounds__(MX_THREADS, 1)
 
 // ------------------------------------------------------------ host side
 
-static size_t mx_smem_bytes(long long NBpos, bool split) {
-  return 1024 + (size_t)WS_OFF_ACC + 2 * sizeof(int) * (size_t)(split ? 2 * NBpos + 32 : NBpos) + 2 * 64 * 4 + 16 +
-         8 * (2 * WS_STAGES + 2 * WS_ACC + 9) + 16 + 64;
+static size_t mx_smem_bytes(long long NBpos, bool split, int mode) {
+  return 1024 + (size_t)ws_off_acc(mode) + 2 * sizeof(int) * (size_t)(split ? 2 * NBpos + 32 : NBpos) + 2 * 64 * 4 +
+         16 + 8 * (2 * ws_stages(mode) + 2 * WS_ACC + 9) + 16 + 64;
 }
 
 static uint64_t splitmix64_next(uint64_t &state) {
@@ -777,7 +786,8 @@ static int ab_positions(forte_ctx *ctx) {
   // (pos = 32 j + h(string) and h(E_rs J) = h(J) ^ code[r] ^ code[s]).  Otherwise it is
   // the byte offset of the target with the sign in bit 0 (positions < 16384, so
   // offsets fit 16 bits with bits 0-1 free; 0xFFFF, bit 1 set, marks "no target").
-  const bool split = mx_smem_bytes(NBpos, true) <= 232448;
+  // (one table for both modes: decided with the larger stage ring)
+  const bool split = std::max(mx_smem_bytes(NBpos, true, FORTE_BF16X2), mx_smem_bytes(NBpos, true, FORTE_TF32)) <= 232448;
   std::vector<unsigned> hpair(128, 0u);
   for (int r = 0; r < n; ++r)
     for (int s2 = 0; s2 <= r; ++s2) hpair[r * (r + 1) / 2 + s2] = (r == s2) ? 0u : (best[r] ^ best[s2]);
@@ -927,7 +937,7 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
   if (ab) {
     const int nN = ctx->npair <= 112 ? 112 : 128;
     const bool split = ctx->ab_split;
-    const size_t smem = mx_smem_bytes(NBpos, split);
+    const size_t smem = mx_smem_bytes(NBpos, split, mode);
     if (smem > 232448) {
       set_error("alpha-beta MMA kernel needs %zu bytes of shared memory", smem);
       return FORTE_ERR_ARG;

@@ -15,8 +15,6 @@ namespace forte {
 // default of the pipeline waits and the fixed budget of the waits that drain a
 // CTA's own MMAs and copies before it exits.
 constexpr unsigned long long MX_WAIT_CYCLES = 4000000000ull;
-// suspend-time hint of one pipeline wait step (the clock budget is checked between steps)
-constexpr uint32_t MX_WAIT_SLEEP_NS = 20000u;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -33,18 +31,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
       : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// try_wait with a suspend-time hint: the waiting thread sleeps until the phase
-// completes or about `ns` nanoseconds pass, instead of returning at once, so
-// waiting warps take no issue slots from the warps that do the work.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t ns) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity), "r"(ns)
       : "memory");
   return ok != 0;
 }
@@ -206,7 +192,7 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity, vol
   const unsigned long long budget =
       ((unsigned long long)(unsigned)abort_flag[2] << 32) | (unsigned long long)(unsigned)abort_flag[1];
   const long long t0 = clock64();
-  while (!mbar_try_wait_sleep(bar, parity, MX_WAIT_SLEEP_NS)) {
+  while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
     if ((unsigned long long)(clock64() - t0) > budget) return false;
   }
