@@ -580,6 +580,70 @@ def run_batch(args):
     return 0
 
 
+def run_sci(args):
+    """Determinant-list sigma (selected-CI data path): lists grown from the aufbau
+    determinant (it and all its singles and doubles; a third list adds random
+    determinants of the sector), one vector, CUDA events around forte_sci_sigma;
+    rows sampled against the oracle's matrix elements; the oracle's own list sigma
+    timed on a 4,000-determinant head of the first list (same screen: every pair)."""
+    import torch
+    import paper_2405_10197_gb300 as fg
+    import oracle
+    torch.cuda.set_device(0)
+    cases = [("CAS-size reference list: 24 orbitals, 6a+6b, singles+doubles", 24, 6, 6, 0),
+             ("30 orbitals, 10a+10b, singles+doubles", 30, 10, 10, 0),
+             ("30 orbitals, 10a+10b, singles+doubles + 150,000 random determinants", 30, 10, 10, 150000)]
+    pc = np.vectorize(lambda x: bin(int(x)).count("1"))
+    out = {"metric": "determinant-list sigma", "unit": "ms", "cases": []}
+    for name, n, na, nb, extra in cases:
+        h, eri = si.integrals(n, 2 * n, seed=90 + n)
+        words = si.excitation_list(n, na, nb)
+        if extra:
+            words = np.unique(np.concatenate([words, si.random_determinants(n, na, nb, extra, seed=5)]))
+        nd = len(words)
+        d = torch.tensor(words.view(np.int64), device="cuda")
+        C = torch.tensor(np.random.default_rng(3).normal(size=(1, nd)), device="cuda")
+        S = torch.empty_like(C)
+        sci = fg.forte_sci_create(n, h, eri)
+        try:
+            for _ in range(2):
+                fg.forte_sci_sigma(sci, d, C, S, 1)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 5
+            a.record()
+            for _ in range(reps):
+                fg.forte_sci_sigma(sci, d, C, S, 1)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+        finally:
+            fg.forte_sci_destroy(sci)
+        Sh, Ch = S.cpu().numpy()[0], C.cpu().numpy()[0]
+        rng = np.random.default_rng(7)
+        worst = 0.0
+        for i in rng.choice(nd, size=4, replace=False):
+            near = np.nonzero(pc(words ^ words[i]) <= 4)[0]
+            ref = sum(oracle.hij(n, h, eri, int(words[i]), int(words[j])) * Ch[j] for j in near)
+            worst = max(worst, abs(Sh[i] - ref) / max(1.0, abs(ref)))
+        out["cases"].append({"workload": name, "n_det": nd, "ms": _sig(ms), "det_per_s": _sig(nd / (ms * 1e-3)),
+                             "pair_screens_per_s": _sig(float(nd) * nd / (ms * 1e-3)),
+                             "sampled_rows_rel_err_vs_oracle": _sig(worst, 3)})
+    # the oracle on a bounded head of the first list
+    n, na, nb = 24, 6, 6
+    h, eri = si.integrals(n, 2 * n, seed=90 + n)
+    words = si.excitation_list(n, na, nb)[:4000]
+    C = np.random.default_rng(3).normal(size=(1, len(words)))
+    t0 = time.perf_counter()
+    oracle.sci_sigma(n, words, h, eri, C)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"kind": "oracle", "cores": oracle.num_threads(), "sample": "oracle.sci_sigma on the first "
+                           "4,000 determinants of the 24-orbital list", "pair_screens_per_s": _sig(4000.0 * 4000 / dt),
+                           "seconds": _sig(dt)}
+    print(json.dumps(out))
+    return 0
+
+
 def run_configs(args):
     """One JSON line per measurement config besides the headline CAS(14,14) step:
     C0 CAS(8,8) FP64 (latency: us per sigma and per iteration), C1 CAS(12,12) 4 roots
@@ -823,6 +887,26 @@ def run_extensions(args):
     lines.append({"config": "X3 CAS(14,14) seed 2, even-S sector vs unrestricted, BF16x2 Davidson refined to 1e-8",
                   "davidson": {"unrestricted": full, "even_S": even}})
     prob.close()
+    # X4: adaptive CI at CAS(12,12) seed 1, sigma = 1e-3, in the even-S sector and without
+    cfg = si.CAS1212
+    h, eri = si.integrals(12, cfg["n_l"], cfg["seed"])
+    x4 = {"config": "X4 adaptive CI, CAS(12,12) seed 1, sigma 1e-3, gamma 1, FP64-class screening", "runs": []}
+    for parity in (1, 0):
+        prob = fg.CASProblem(12, 6, 6, h, eri, precision=fg.FORTE_BF16X2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            e, ec, C, nm, np_, cyc = prob.aci(1e-3, 1.0, 30, 1e-8, parity)
+            st = "ok"
+        except fg.ForteError as err:
+            e = ec = float("nan")
+            nm = np_ = cyc = -1
+            st = str(err)[:120]
+        torch.cuda.synchronize()
+        x4["runs"].append({"parity": parity, "seconds": _sig(time.perf_counter() - t0), "E_M": e, "E_corrected": ec,
+                           "n_M": nm, "n_P": np_, "cycles": cyc, "status": st})
+        prob.close()
+    lines.append(x4)
     for ln in lines:
         print(json.dumps(ln))
     return 0
@@ -865,6 +949,8 @@ def main():
     ap.add_argument("--fd-dirs", type=int, default=4, help="central-difference directions for the C3 gradient check")
     ap.add_argument("--extensions", action="store_true",
                     help="measure the 3-RDM, the occupation restriction and the spin-parity sector")
+    ap.add_argument("--sci", action="store_true",
+                    help="measure the determinant-list (selected-CI) sigma on reference-grown lists")
     ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
                     help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
     args = ap.parse_args()
@@ -878,6 +964,8 @@ def main():
         return run_configs(args)
     if args.extensions:
         return run_extensions(args)
+    if args.sci:
+        return run_sci(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

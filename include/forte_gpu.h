@@ -30,11 +30,14 @@
 #ifndef FORTE_GPU_H
 #define FORTE_GPU_H
 
+#include <stdint.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
 
 typedef struct forte_ctx forte_ctx;
+typedef struct forte_sci forte_sci;
 
 enum {
   FORTE_OK = 0,
@@ -404,6 +407,35 @@ const char *forte_profile_kernel_name(forte_ctx *ctx, int i);
  * created, in FP64 and in a reduced-precision mode (host outputs, may be NULL). */
 int forte_get_counters(const forte_ctx *ctx, long long *sigma_vectors_fp64,
                        long long *sigma_vectors_mixed);
+
+/* ---- determinant-list sigma (selected CI, Sec. II.A.2) ----
+ *
+ * Handle holding the integrals of an n-orbital problem for sigma over arbitrary
+ * lists of determinants, the data path of adaptive CI: no string tables, so n may
+ * exceed the CAS grid's limit.  norb in 1..32; h [norb][norb], eri
+ * [norb]^4 (chemist order) host arrays, copied to the current device.  Returns
+ * NULL (reason in forte_last_error) for a bad norb, NULL or non-finite integrals,
+ * or a failed device allocation.  Release with forte_sci_destroy. */
+forte_sci *forte_sci_create(int norb, const double *h, const double *eri);
+void forte_sci_destroy(forte_sci *sci);
+/* Stream of the handle's work (default: the legacy default stream). */
+int forte_sci_set_stream(forte_sci *sci, void *cuda_stream);
+
+/* S[v][i] = sum_j <D_i|H|D_j> C[v][j] over a list of determinants (H of Eq. 1;
+ * the elements follow the Slater-Condon rules, pairs more than two replacements
+ * apart vanish).
+ *   dets  device [ndet] 64-bit words: alpha orbital p at bit p, beta orbital p at
+ *         bit norb + p (creation operators ordered by that index, alpha first);
+ *         any order, any mix of (n_alpha, n_beta) sectors (sectors do not couple);
+ *         a word listed twice counts twice
+ *   C, S  device [nvec][ndet] FP64; S overwritten, must not overlap C
+ *   ndet >= 0 (<= 2^31), nvec >= 0; 0 is a no-op
+ * Every pair (i, j) is screened by popcount(D_i ^ D_j) <= 4 (cost ndet^2 / 32
+ * warp steps), so the call suits lists up to ~1e6 determinants.  Deterministic:
+ * per-row sums are taken in list order within fixed splits, added in split order.
+ * Asynchronous on the handle's stream; grows a scratch buffer (nvec <= 4 at a time
+ * x splits x ndet doubles) on demand. */
+int forte_sci_sigma(forte_sci *sci, long long ndet, const uint64_t *dets, const double *C, double *S, int nvec);
 
 #ifdef __cplusplus
 }

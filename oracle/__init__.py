@@ -14,6 +14,7 @@ from .driver import (  # noqa: F401
     build,
     strings,
     single_table,
+    hij,
     hmat_dense,
     hdiag,
     sigma,

@@ -61,6 +61,10 @@ def library():
     L.forte_cas_create.argtypes = [i, i, i, vp, vp]
     L.forte_destroy.restype = None
     L.forte_destroy.argtypes = [vp]
+    L.forte_sci_create.restype = vp
+    L.forte_sci_create.argtypes = [i, vp, vp]
+    L.forte_sci_destroy.restype = None
+    L.forte_sci_destroy.argtypes = [vp]
     L.forte_last_error.restype = ctypes.c_char_p
     L.forte_last_error.argtypes = []
     sigs = {
@@ -90,6 +94,8 @@ def library():
         "forte_batch_solve": [i, vp, vp, vp, vp, vp, vp, i, d, i, vp, vp],
         "forte_batch_tuning": [i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
         "forte_batch_stats": [vp, vp, vp],
+        "forte_sci_set_stream": [vp, vp],
+        "forte_sci_sigma": [vp, ll, vp, vp, vp, i],
         "forte_profile_enable": [vp, i],
         "forte_profile_query": [vp, ctypes.c_char_p, vp, vp],
         "forte_get_counters": [vp, vp, vp],
@@ -369,6 +375,36 @@ def forte_batch_stats():
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(library().forte_batch_stats(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return dict(class_launch=a.value, single_path=b.value, retried=c.value)
+
+
+def forte_sci_create(norb, h, eri):
+    """Handle for sigma over determinant lists (norb <= 32); h, eri: host arrays."""
+    h = _host_f64(h, (norb, norb))
+    eri = _host_f64(eri, (norb,) * 4)
+    sci = library().forte_sci_create(norb, h.ctypes.data, eri.ctypes.data)
+    if not sci:
+        raise ForteError(FORTE_ERR_ARG, forte_last_error())
+    return sci
+
+
+def forte_sci_destroy(sci):
+    library().forte_sci_destroy(sci)
+
+
+def forte_sci_set_stream(sci, stream):
+    s = getattr(stream, "cuda_stream", stream)
+    return _check(library().forte_sci_set_stream(sci, s))
+
+
+def forte_sci_sigma(sci, dets, C, S, nvec):
+    """dets: CUDA int64/uint64 tensor [ndet] of determinant words; C, S: CUDA FP64 [nvec][ndet]."""
+    import torch
+    if not isinstance(dets, torch.Tensor) or not dets.is_cuda or dets.dtype not in (torch.int64, torch.uint64) \
+            or not dets.is_contiguous():
+        raise ValueError("dets must be a contiguous CUDA int64 tensor of determinant words")
+    nd = dets.numel()
+    return _check(library().forte_sci_sigma(sci, nd, dets.data_ptr(), _ptr(C, nvec * nd), _ptr(S, nvec * nd),
+                                            int(nvec)))
 
 
 def forte_profile_enable(ctx, on):

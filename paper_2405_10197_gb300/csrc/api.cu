@@ -344,8 +344,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
         if ((rc = vk_convert(ctx, guess + (size_t)i * N, (float *)(void *)(B + (size_t)k * N), N))) return rc;
         t = B + (size_t)k * N;
       }
-      FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
-      if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, B + (size_t)k * N, d_d0, N))) return rc;
+      if ((rc = vk_orth_update(ctx, B, k, N, nullptr, t, B + (size_t)k * N, d_d0, N))) return rc;
       FORTE_CUDA_TRY(cudaMemcpyAsync(h_d.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
       FORTE_CUDA_TRY(cudaStreamSynchronize(st));
       double n0 = h_d[k];
@@ -488,8 +487,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       T *b = B + (size_t)k * N;
       if ((rc = spin_project(ctx, t, 1))) return rc;  // the sigma rounding leaves the sector slightly
       std::vector<double> h_d(65);
-      FORTE_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * 64, st));
-      if ((rc = vk_orth_update(ctx, B, k, N, d_u, t, b, d_d0, N))) return rc;     // copy + B^T t + |t|^2
+      if ((rc = vk_orth_update(ctx, B, k, N, nullptr, t, b, d_d0, N))) return rc;  // copy + B^T t + |t|^2
       std::vector<double> h0(65);
       FORTE_CUDA_TRY(cudaMemcpyAsync(h0.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
       FORTE_CUDA_TRY(cudaStreamSynchronize(st));
@@ -572,7 +570,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
     int r2;
     if ((r2 = vk_multidot(ctx, V, nk, N, v, N, d_a))) return r2;
     if ((r2 = vk_orth_update(ctx, V, nk, N, d_a, v, v, d_b, N))) return r2;
-    return vk_orth_update(ctx, V, nk, N, d_b, v, v, d_a, N);
+    return vk_orth_update(ctx, V, nk, N, d_b, v, v, d_a, N, false);
   };
   FORTE_CUDA_TRY(cudaMemcpyAsync(V, X0, sizeof(double) * nroots * N, cudaMemcpyDeviceToDevice, st));
   // the start vectors come from a reduced-precision (FP32) phase: orthonormalise
@@ -686,8 +684,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       double *vk = V + (size_t)k * N;
       FORTE_CUDA_TRY(cudaMemcpyAsync(vk, px, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
       if ((rc = spin_project(ctx, vk, 1))) return rc;
-      FORTE_CUDA_TRY(cudaMemsetAsync(d_a, 0, sizeof(double) * 64, st));
-      if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
+      if ((rc = vk_orth_update(ctx, V, k, N, nullptr, vk, vk, d_b, N))) return rc;
       if ((rc = fetch(d_b, k + 1, h.data()))) return rc;
       const double n0 = h[k];
       double proj = 0.0;

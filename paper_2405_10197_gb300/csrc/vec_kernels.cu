@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(VK_THREADS) k_residual_precond(
 
 // t_out = t_in - sum_i c_i B_i ; part[block][i] = B_i . t_out (i < k), part[block][k] = |t_out|^2.
 // Without DOTS the B_i . t_out are not formed (a second read of every B_i) and part
-// holds zeros there.
+// holds zeros there.  c == nullptr: no update (t_out = t_in; the B_i are read once,
+// for the dots).
 template <typename T, bool DOTS>
 __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict__ Bm, int k,
                                                             long long ld, const double *__restrict__ c,
@@ -174,7 +175,8 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict_
                                                             unsigned *counter) {
   __shared__ double red[32];
   __shared__ T sc[VK_MAXV];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sc[i] = (T)c[i];
+  const int ku = c ? k : 0;  // vectors to subtract
+  for (int i = threadIdx.x; i < ku; i += blockDim.x) sc[i] = (T)c[i];
   __syncthreads();
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
   T tr[VK_EPT];
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(VK_THREADS) k_orth_update(const T *__restrict_
     long long j = base + (long long)e * VK_THREADS;
     tr[e] = (j < n) ? t_in[j] : T(0);
   }
-  for (int i = 0; i < k; ++i) {
+  for (int i = 0; i < ku; ++i) {
     const T *b = Bm + (long long)i * ld;
 #pragma unroll
     for (int e = 0; e < VK_EPT; ++e) {

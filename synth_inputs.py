@@ -97,3 +97,55 @@ def batch_instances(count: int = 512, seed: int = 4242):
     nroots = rng.integers(1, 4, size=count)
     return [dict(norb=int(n), nalpha=int(n) // 2, nbeta=int(n) // 2, n_l=2 * int(n),
                  seed=1000 + i, nroots=int(k)) for i, (n, k) in enumerate(zip(norbs, nroots))]
+
+
+def _replace(mask: int, holes, particles) -> int:
+    for p in holes:
+        mask &= ~(1 << p)
+    for p in particles:
+        mask |= 1 << p
+    return mask
+
+
+def excitation_list(norb: int, nalpha: int, nbeta: int, max_rank: int = 2):
+    """Determinant words (alpha orbital p at bit p, beta orbital p at bit norb + p)
+    of the aufbau determinant (lowest orbitals occupied in both spins) and of every
+    determinant within max_rank (<= 2) orbital replacements of it, sorted: the shape
+    of a selected-CI space grown from one reference."""
+    import itertools
+    a0 = (1 << nalpha) - 1
+    b0 = (1 << nbeta) - 1
+
+    def moves(mask, nel, rank):
+        occ = [p for p in range(norb) if (mask >> p) & 1]
+        vir = [p for p in range(norb) if not (mask >> p) & 1]
+        return [_replace(mask, h, q) for h in itertools.combinations(occ, rank)
+                for q in itertools.combinations(vir, rank)]
+
+    words = set()
+    alpha = {0: [a0]}
+    beta = {0: [b0]}
+    for r in range(1, max_rank + 1):
+        alpha[r] = moves(a0, nalpha, r)
+        beta[r] = moves(b0, nbeta, r)
+    for ra in range(max_rank + 1):
+        for rb in range(max_rank + 1 - ra):
+            for a in alpha[ra]:
+                for b in beta[rb]:
+                    words.add(a | (b << norb))
+    return np.array(sorted(words), dtype=np.uint64)
+
+
+def random_determinants(norb: int, nalpha: int, nbeta: int, count: int, seed: int):
+    """count distinct determinant words with nalpha / nbeta electrons, uniformly
+    drawn (same bit layout as excitation_list), in drawing order."""
+    rng = np.random.default_rng(seed)
+    out, seen = [], set()
+    while len(out) < count:
+        a = rng.choice(norb, size=nalpha, replace=False)
+        b = rng.choice(norb, size=nbeta, replace=False)
+        w = int(np.sum(1 << a.astype(np.uint64))) | (int(np.sum(1 << b.astype(np.uint64))) << norb)
+        if w not in seen:
+            seen.add(w)
+            out.append(w)
+    return np.array(out, dtype=np.uint64)
