@@ -932,7 +932,13 @@ int forte_davidson(forte_ctx *ctx, int nroots, double tol) {
     if (rc) return mixed_status(ctx) ? FORTE_ERR_TIMEOUT : rc;  // an expired wait explains the failure
     if ((rc = mixed_status(ctx))) return rc;
     ctx->dv_iters = res.iters;
-    if (res.stalled && res.iters < ctx->dv_max_iter) {
+    // A converged Davidson-Liu is verified: its residuals come from the stored basis
+    // and sigma vectors, which a long run can leave inconsistent (lost
+    // orthogonality).  The Jacobi-Davidson pass below starts by orthonormalising the
+    // Ritz vectors, recomputing their sigma and forming the exact residuals; when
+    // those meet tol it returns at once (one sigma per root), otherwise it iterates.
+    // A stalled Davidson-Liu continues there the same way.
+    if (res.converged || res.stalled) {
       // Jacobi-Davidson from the Ritz vectors, inner solves in the same arithmetic
       const int it_dl = res.iters;
       rc = refine_jd(ctx, nroots, tol, ctx->precision, ctx->precision, ctx->d_roots, ctx->d_roots,

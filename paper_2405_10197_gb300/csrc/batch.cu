@@ -85,10 +85,11 @@ struct BClass {
   const float2 *gp2;
   const int *nroots;            // [P]
   const int *eoff;              // [P]: offset of the problem's energies
+  const int *gidx;              // [P]: index of the problem in the batch (status, iterations)
   const long long *woff;        // [P]: offset of the problem's workspace (doubles)
   double *work;
   double *E, *rn;               // [sum nroots]
-  int *iters, *status;          // [P]
+  int *iters, *status;          // [nprob], by batch index (gidx)
   double tol, tol1;             // final tolerance; end of the FP32 phase (mixed)
   int max_iter, mode, TJ;       // mode: 0 FP64, 1 FP32 then double-FP32, 2 double-FP32
   int probe;                    // > 0: run `probe` sigma builds only (autotuner)
@@ -671,14 +672,18 @@ __global__ void __launch_bounds__(NT) k_batch_davidson(const BClass c) {
     if (st == FORTE_ERR_NUMERIC) break;
     // end of the FP32 phase (a residual below tol there certifies nothing): restart
     // from the Ritz vectors with the FP64-class sigma
-    if (phase == AR_F32 && (all || rmax < c.tol1 || it >= p1_cap)) {
+    // the Ritz vectors x_r = B u_r into W
+    auto ritz_to_W = [&]() {
       for (int i = threadIdx.x; i < k * nr; i += NT) coef[i] = U[(i / nr) * BT_LD + perm[i % nr]];
       __syncthreads();
       cta_combine<NT>(B, k, N, coef, nr, W, N, N);
+    };
+    // restart the subspace from the vectors in W: orthonormalised (two Gram-Schmidt
+    // passes), sigma recomputed in the current arithmetic
+    auto restart_from_W = [&]() {
       for (long long i = threadIdx.x; i < (long long)nr * N; i += NT) B[i] = W[i];
       __syncthreads();
       k = nr;
-      // re-orthonormalise (the FP32-phase basis is orthonormal to rounding)
       for (int r = 0; r < nr; ++r) {
         double *b = B + (long long)r * N;
         double nn = 0.0;
@@ -690,14 +695,55 @@ __global__ void __launch_bounds__(NT) k_batch_davidson(const BClass c) {
         for (long long i = threadIdx.x; i < N; i += NT) b[i] *= s;
         __syncthreads();
       }
-      phase = AR_DF;
       for (int j = 0; j < k; ++j) sigma(B + (long long)j * N, S + (long long)j * N);
       build_G(0, k);
+    };
+    if (phase == AR_F32 && (all || rmax < c.tol1 || it >= p1_cap)) {
+      ritz_to_W();
+      phase = AR_DF;
+      restart_from_W();
       continue;
     }
     if (all) {
-      st = FORTE_OK;
-      break;
+      // Verified convergence: the residual above is formed from the stored basis and
+      // its sigma, and a basis that has lost orthogonality over a long run can show
+      // a small residual for a vector that is not an eigenvector (a combination of
+      // nearly parallel basis vectors).  Each Ritz vector is therefore formed, its
+      // sigma recomputed, and the residual of the normalised vector at its Rayleigh
+      // quotient must meet tol; otherwise the subspace restarts from these vectors.
+      ritz_to_W();
+      bool verified = true;
+      for (int r = 0; r < nr; ++r) {
+        const double *x = W + (long long)r * N;
+        double *sx = T + (long long)r * N;
+        sigma(x, sx);
+        double p[4] = {0.0, 0.0, 0.0, 0.0};
+        for (long long i = threadIdx.x; i < N; i += NT) {
+          p[0] = fma(x[i], x[i], p[0]);
+          p[1] = fma(x[i], sx[i], p[1]);
+        }
+        cta_sum4<NT>(p, 2, red);
+        const double xx = p[0], th = p[1] / fmax(xx, 1e-300);
+        double q[4] = {0.0, 0.0, 0.0, 0.0};
+        for (long long i = threadIdx.x; i < N; i += NT) {
+          const double v = fma(-th, x[i], sx[i]);
+          q[0] = fma(v, v, q[0]);
+        }
+        cta_sum4<NT>(q, 1, red);
+        const double rn = sqrt(fmax(0.0, q[0]) / fmax(xx, 1e-300));
+        if (threadIdx.x == 0) {
+          wv[r] = th;
+          d2[r] = rn;
+        }
+        if (!(rn < c.tol) || !isfinite(th)) verified = false;
+      }
+      __syncthreads();
+      if (verified) {
+        st = FORTE_OK;
+        break;
+      }
+      restart_from_W();
+      continue;
     }
     int nnew = 0;
     for (int r = 0; r < nr; ++r) nnew += (d2[r] < c.tol) ? 0 : 1;
@@ -751,8 +797,8 @@ __global__ void __launch_bounds__(NT) k_batch_davidson(const BClass c) {
     c.rn[c.eoff[q] + threadIdx.x] = d2[threadIdx.x];
   }
   if (threadIdx.x == 0) {
-    c.iters[q] = min(it, c.max_iter);
-    c.status[q] = st;
+    c.iters[c.gidx[q]] = min(it, c.max_iter);
+    c.status[c.gidx[q]] = st;
   }
 }
 
@@ -895,7 +941,7 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
   } pool;
   struct Off {
     size_t listA, listB, ptrA, colA, ptrB, colB, valA, valB, valA32, valB32, valA2, valB2, diagA, diagB, Wd, strB,
-        gp, gp32, gp2, nroots, eoff, woff;
+        gp, gp32, gp2, nroots, eoff, gidx, woff;
   };
   std::vector<Off> offs(classes.size());
   long long work_total = 0;
@@ -993,11 +1039,13 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     o.gp2 = pool.add(gp2.data(), sizeof(float) * gp2.size());
     std::vector<int> nr(P), eo(P);
     std::vector<long long> wo(P);
+    std::vector<int> gi(P);
     const long long N = A.N * Bs.N;
     for (int pi = 0; pi < P; ++pi) {
       const int i = ch.probs[pi];
       nr[pi] = nroots[i];
       eo[pi] = (int)eoff[i];
+      gi[pi] = i;
       const int maxsub = (int)std::min<long long>(std::min(12 * nroots[i], BT_MAXK), N);
       const int keep = std::max(nroots[i], std::min(2 * nroots[i], maxsub - 1));
       wo[pi] = work_total;
@@ -1006,6 +1054,7 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     }
     o.nroots = pool.add(nr.data(), sizeof(int) * P);
     o.eoff = pool.add(eo.data(), sizeof(int) * P);
+    o.gidx = pool.add(gi.data(), sizeof(int) * P);
     o.woff = pool.add(wo.data(), sizeof(long long) * P);
     BClass &c = ch.dev;
     c.n = n;
@@ -1141,6 +1190,7 @@ extern "C" int forte_batch_solve(int nprob, const int *norb, const int *nalpha, 
     c.gp2 = (const float2 *)(dbuf + o.gp2);
     c.nroots = (const int *)(dbuf + o.nroots);
     c.eoff = (const int *)(dbuf + o.eoff);
+    c.gidx = (const int *)(dbuf + o.gidx);
     c.woff = (const long long *)(dbuf + o.woff);
     c.work = dwork;
     c.E = (double *)(dbuf + off_E);

@@ -125,3 +125,18 @@ def test_batch_reports_bad_input():
              dict(norb=4, nalpha=2, nbeta=2, nroots=1, h=bad, eri=eri)]
     with pytest.raises(fg.ForteError):
         fg.forte_batch_solve(probs)
+
+
+def test_batch_head_128_mixed_instance_1058_matches_oracle():
+    # The first 128 instances of the batched workload in the mixed mode: three size
+    # classes in one graph next to the single-problem path.  Instance 58 (seed 1058)
+    # is the one whose in-CTA Davidson-Liu does not converge within the iteration cap;
+    # its status must reach the host at its own batch index, so that it is solved
+    # again on the single-problem path (a status written at the CTA's index within
+    # its class was read as converged, 8.5e-4 Eh above the ground state).
+    g = json.load(open(os.path.join(HERE, "golden", "batch1058_cas1010.json")))
+    probs = _workload(128)
+    k = [i for i, q in enumerate(si.batch_instances()[:128]) if q["seed"] == 1058][0]
+    E, st = fg.forte_batch_solve(probs, precision=fg.FORTE_BF16X2, tol=1e-7)
+    assert np.all(st == 0)
+    assert abs(E[k][0] - g["energies"][0]) < 1e-9
