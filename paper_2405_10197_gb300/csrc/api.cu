@@ -319,7 +319,8 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
   // device layout: B[maxsub], S[maxsub], T[nroots], W[keep] vectors; then small arrays
   size_t nvecs = (size_t)maxsub * 2 + nroots + keep;
   size_t small_off = ((sizeof(T) * nvecs * N + 255) / 256) * 256;
-  size_t small_bytes = sizeof(double) * (64 * 64 + 4 * 64 + 64);
+  // coef, u, d0, d1, d2 (4416 doubles), then per root [|r|^2, B^T t, |t|^2] (66 each)
+  size_t small_bytes = sizeof(double) * (64 * 64 + 4 * 64 + 64 + 64 * 66);
   int rc = ctx->sc_dv.ensure(small_off + small_bytes + 256);
   if (rc) return rc;
   T *B = (T *)ctx->sc_dv.ptr;
@@ -331,6 +332,7 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
   double *d_d0 = d_u + 64;                                           // [65]
   double *d_d1 = d_d0 + 65;                                          // [65]
   double *d_d2 = d_d1 + 65;                                          // [65]
+  double *d_rd = d_coef + 64 * 64 + 4 * 64 + 64;                     // [64][66]
 
   int k = 0;
   if (ng > 0) {
@@ -426,18 +428,35 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     w.assign(k, 0.0);
     U.assign((size_t)k * k, 0.0);
     sym_eig(k, Gk.data(), w.data(), U.data());
-    // residuals and preconditioned corrections
-    std::vector<double> rn2(nroots);
+    // residuals and preconditioned corrections; where the packet kernel applies, the
+    // same pass forms B^T t and |t|^2 for the Gram-Schmidt step of the new direction
+    // (not in a spin-parity sector, where t is projected before that step)
+    std::vector<double> rn2(nroots), hrd((size_t)nroots * 66);
+    std::vector<char> fused(nroots, 0);
+    bool any_fused = false;
     for (int r = 0; r < nroots; ++r) {
       std::vector<double> u(k);
       for (int i = 0; i < k; ++i) u[i] = U[(size_t)i * k + r];
       FORTE_CUDA_TRY(cudaMemcpyAsync(d_u, u.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-      if ((rc = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, Tv + (size_t)r * N,
-                                    d_d0 + r, N)))
-        return rc;
+      T *t = Tv + (size_t)r * N;
+      int rr = -1;
+      if (ctx->spin_parity == 0)
+        rr = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, t, nullptr, N, d_rd + (size_t)r * 66);
+      if (rr == -1) {
+        rr = vk_residual_precond(ctx, B, S, k, N, d_u, w[r], ctx->dv_guard, t, d_d0 + r, N);
+      } else if (rr == FORTE_OK) {
+        fused[r] = 1;
+        any_fused = true;
+      }
+      if (rr) return rr;
     }
     FORTE_CUDA_TRY(cudaMemcpyAsync(rn2.data(), d_d0, sizeof(double) * nroots, cudaMemcpyDeviceToHost, st));
+    if (any_fused)
+      FORTE_CUDA_TRY(cudaMemcpyAsync(hrd.data(), d_rd, sizeof(double) * hrd.size(), cudaMemcpyDeviceToHost, st));
     FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int r = 0; r < nroots; ++r)
+      if (fused[r]) rn2[r] = hrd[(size_t)r * 66];
+    const int k_res = k;  // B[0..k_res) as the fused dots saw it
     bool all = true, bad = false;
     for (int r = 0; r < nroots; ++r) {
       res.E[r] = w[r];
@@ -465,7 +484,9 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
     }
     int nnew_want = 0;
     for (int r = 0; r < nroots; ++r) nnew_want += (res.rn[r] < tol) ? 0 : 1;
+    bool collapsed = false;
     if (k + nnew_want > maxsub && k > keep) {
+      collapsed = true;
       // collapse onto the lowest `keep` Ritz vectors
       coef.assign((size_t)k * keep, 0.0);
       for (int i = 0; i < k; ++i)
@@ -487,10 +508,20 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       T *b = B + (size_t)k * N;
       if ((rc = spin_project(ctx, t, 1))) return rc;  // the sigma rounding leaves the sector slightly
       std::vector<double> h_d(65);
-      if ((rc = vk_orth_update(ctx, B, k, N, nullptr, t, b, d_d0, N))) return rc;  // copy + B^T t + |t|^2
       std::vector<double> h0(65);
-      FORTE_CUDA_TRY(cudaMemcpyAsync(h0.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
-      FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      const double *c0 = d_d0;  // device B^T t
+      const T *src = b;         // vector pass 1 reads
+      if (fused[r] && !collapsed && k == k_res) {
+        // B^T t and |t|^2 from the residual pass: no copy pass, no host wait
+        for (int i = 0; i <= k; ++i) h0[i] = hrd[(size_t)r * 66 + 1 + i];
+        c0 = d_rd + (size_t)r * 66 + 1;
+        src = t;
+      } else {
+        if ((rc = vk_orth_update(ctx, B, k, N, nullptr, t, b, d_d0, N))) return rc;  // copy + B^T t + |t|^2
+        FORTE_CUDA_TRY(cudaMemcpyAsync(h0.data(), d_d0, sizeof(double) * (k + 1), cudaMemcpyDeviceToHost, st));
+        FORTE_CUDA_TRY(cudaStreamSynchronize(st));
+      }
+      if (!(h0[k] > 0.0) || !isfinite(h0[k])) continue;  // no new direction from this root
       // second pass only when the first removes more than half of |t|^2 (the
       // criterion of Daniel, Gragg, Kaufman and Stewart, Math. Comp. 30 (1976) 772:
       // ||t1|| >= ||t0|| / sqrt(2), with ||t1||^2 = ||t0||^2 - ||B^T t0||^2), which is
@@ -498,7 +529,16 @@ static int davidson_run(forte_ctx *ctx, int nroots, double tol, int mode, const 
       double proj = 0.0;
       for (int i = 0; i < k; ++i) proj += h0[i] * h0[i];
       const bool second = !(h0[k] - proj >= 0.5 * h0[k]);
-      if ((rc = vk_orth_update(ctx, B, k, N, d_d0, b, b, d_d1, N, second))) return rc;  // CGS pass 1
+      if (!second) {
+        // one pass, normalised in the same pass: |t - B c|^2 = |t|^2 - |c|^2 for
+        // orthonormal B (relative error ~ |B^T B - I| |c|^2 / |t|^2, with
+        // |c|^2 <= |t|^2 / 2 here)
+        const double nn = h0[k] - proj;
+        if ((rc = vk_orth_update(ctx, B, k, N, c0, src, b, d_d1, N, false, 1.0 / sqrt(nn)))) return rc;
+        ++k;
+        continue;
+      }
+      if ((rc = vk_orth_update(ctx, B, k, N, c0, src, b, d_d1, N, second))) return rc;  // CGS pass 1
       const double *dfin = d_d1;
       if (second) {
         if ((rc = vk_orth_update(ctx, B, k, N, d_d1, b, b, d_d2, N, false))) return rc;  // CGS pass 2
@@ -550,14 +590,15 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
   const int nkeep = nroots + nextra;
   const int kmax = std::min(63, std::max(nroots * (max_outer + 1), nkeep + nroots));
   // vectors: V[kmax], HV[kmax], W[nkeep] (collapse target, then residuals), PCG: x r z p q
-  size_t nvec = (size_t)2 * kmax + nkeep + 5;
+  // and the inverse preconditioner diagonal
+  size_t nvec = (size_t)2 * kmax + nkeep + 6;
   size_t small_off = sizeof(double) * nvec * N;
   int rc = ctx->sc_dv.ensure(small_off + sizeof(double) * (64 * 64 + 4 * 66) + 256);
   if (rc) return rc;
   double *V = (double *)ctx->sc_dv.ptr;
   double *HV = V + (size_t)kmax * N;
   double *W = HV + (size_t)kmax * N;
-  double *px = W + (size_t)nkeep * N, *pr = px + N, *pz = pr + N, *pp = pz + N, *pq = pp + N;
+  double *px = W + (size_t)nkeep * N, *pr = px + N, *pz = pr + N, *pp = pz + N, *pq = pp + N, *pinv = pq + N;
   double *d_coef = (double *)((char *)ctx->sc_dv.ptr + small_off);
   double *d_a = d_coef + 64 * 64, *d_b = d_a + 66, *d_s = d_b + 66;
   auto fetch = [&](const double *src, int cnt, double *dst) -> int {
@@ -649,7 +690,8 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       // PCG on P (H~ - theta) P x = -R_r, starting from x = 0
       FORTE_CUDA_TRY(cudaMemsetAsync(px, 0, sizeof(double) * N, st));
       if ((rc = vk_scale(ctx, pr, W + (size_t)r * N, -1.0, N))) return rc;
-      if ((rc = vk_precond_dot(ctx, pr, theta, ctx->dv_guard, pz, d_s, N))) return rc;
+      if ((rc = vk_precond_inv(ctx, theta, ctx->dv_guard, pinv, N))) return rc;
+      if ((rc = vk_precond_dot(ctx, pr, pinv, pz, d_s, N))) return rc;
       if ((rc = fetch(d_s, 1, h.data()))) return rc;
       double rz = h[0];
       if ((rc = project(pz, nroots))) return rc;
@@ -672,7 +714,7 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
         if ((rc = vk_multidot(ctx, pr, 1, N, pr, N, d_s))) return rc;
         if ((rc = fetch(d_s, 1, h.data()))) return rc;
         if (sqrt(std::max(0.0, h[0])) < 0.02 * bnorm) break;
-        if ((rc = vk_precond_dot(ctx, pr, theta, ctx->dv_guard, pz, d_s, N))) return rc;
+        if ((rc = vk_precond_dot(ctx, pr, pinv, pz, d_s, N))) return rc;
         if ((rc = fetch(d_s, 1, h.data()))) return rc;
         const double rz_new = h[0];
         if ((rc = project(pz, nroots))) return rc;
@@ -689,13 +731,17 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       const double n0 = h[k];
       double proj = 0.0;
       for (int i = 0; i < k; ++i) proj += h[i] * h[i];
-      if ((rc = vk_orth_update(ctx, V, k, N, d_b, vk, vk, d_a, N))) return rc;
-      const double *dfin = d_a;
-      if (!(n0 - proj >= 0.5 * n0)) {  // second Gram-Schmidt pass only when needed (as in davidson_run)
-        if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N))) return rc;
-        dfin = d_b;
+      if (!(n0 > 0.0) || !isfinite(n0)) continue;
+      if (n0 - proj >= 0.5 * n0) {
+        // one Gram-Schmidt pass suffices (as in davidson_run); normalised in the same
+        // pass with |v - V c|^2 = |v|^2 - |c|^2
+        if ((rc = vk_orth_update(ctx, V, k, N, d_b, vk, vk, d_a, N, false, 1.0 / sqrt(n0 - proj)))) return rc;
+        ++k;
+        continue;
       }
-      if ((rc = fetch(dfin + k, 1, h.data()))) return rc;
+      if ((rc = vk_orth_update(ctx, V, k, N, d_b, vk, vk, d_a, N))) return rc;        // pass 1
+      if ((rc = vk_orth_update(ctx, V, k, N, d_a, vk, vk, d_b, N, false))) return rc;  // pass 2
+      if ((rc = fetch(d_b + k, 1, h.data()))) return rc;
       if (!(h[0] > 1e-24 * n0) || !(h[0] > 0.0)) continue;
       if ((rc = vk_scale(ctx, vk, vk, 1.0 / sqrt(h[0]), N))) return rc;
       ++k;

@@ -266,22 +266,28 @@ int vk_combine(forte_ctx *ctx, const double *V, int nv, long long ld, const doub
                long long ldo, long long n);
 int vk_combine(forte_ctx *ctx, const float *V, int nv, long long ld, const double *coef, int ncomb, float *out,
                long long ldo, long long n);
+// t = (H x - theta x) / (theta - H_II) for x = B u, |r|^2 into rnorm2.  With dots
+// (not null) the residual norm goes to dots[0] instead, and dots[1 + i] = B_i . t
+// (i < k), dots[1 + k] = |t|^2 are formed in the same pass; returns -1 (nothing
+// launched) when the vectors do not suit the packet kernel that does this.
 int vk_residual_precond(forte_ctx *ctx, const double *B, const double *S, int k, long long ld, const double *u,
-                        double theta, double guard, double *t, double *rnorm2, long long n);
+                        double theta, double guard, double *t, double *rnorm2, long long n,
+                        double *dots = nullptr);
 int vk_residual_precond(forte_ctx *ctx, const float *B, const float *S, int k, long long ld, const double *u,
-                        double theta, double guard, float *t, double *rnorm2, long long n);
-// t_out = t_in - B c, dots_out = [B^T t_out (zeros unless dots), |t_out|^2]
+                        double theta, double guard, float *t, double *rnorm2, long long n, double *dots = nullptr);
+// t_out = scale (t_in - B c), dots_out = [B^T t_out (zeros unless dots), |t_out|^2]
 int vk_orth_update(forte_ctx *ctx, const double *B, int k, long long ld, const double *c, const double *t_in,
-                   double *t_out, double *dots_out, long long n, bool dots = true);
+                   double *t_out, double *dots_out, long long n, bool dots = true, double scale = 1.0);
 int vk_orth_update(forte_ctx *ctx, const float *B, int k, long long ld, const double *c, const float *t_in,
-                   float *t_out, double *dots_out, long long n, bool dots = true);
+                   float *t_out, double *dots_out, long long n, bool dots = true, double scale = 1.0);
 int vk_scale(forte_ctx *ctx, double *x, const double *src, double alpha, long long n);
 int vk_scale(forte_ctx *ctx, float *x, const float *src, double alpha, long long n);
 int vk_convert(forte_ctx *ctx, const double *x, float *y, long long n);
 int vk_convert(forte_ctx *ctx, const float *x, double *y, long long n);
 int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n);
-int vk_precond_dot(forte_ctx *ctx, const double *r, double theta, double guard, double *z, double *dot_out,
-                   long long n);
+// rinv = 1 / max(|theta - H_II|, guard); z = r * rinv with dot_out = r . z
+int vk_precond_inv(forte_ctx *ctx, double theta, double guard, double *rinv, long long n);
+int vk_precond_dot(forte_ctx *ctx, const double *r, const double *rinv, double *z, double *dot_out, long long n);
 int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out);
 int vk_any_nonfinite(forte_ctx *ctx, const double *x, long long n, int *flag_host);
 

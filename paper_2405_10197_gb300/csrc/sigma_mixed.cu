@@ -49,6 +49,7 @@
 #include <algorithm>
 #include <string>
 
+#include "bf16_split.h"
 #include "forte_internal.h"
 #include "tc_ptx.cuh"
 
@@ -118,9 +119,16 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t &h, uint16_t &l) {
   l = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hb)));
 }
 __device__ __forceinline__ void split_bf16(double x, uint16_t &h, uint16_t &l) {
+  if (bf16_split_bits(x, h, l)) return;  // integer path; conversions for the rest
   const __nv_bfloat16 hb = __double2bfloat16(x);
   h = __bfloat16_as_ushort(hb);
   l = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(hb)));
+}
+// bits of (float)|x| (non-negative floats order as their bit patterns)
+__device__ __forceinline__ unsigned abs_bits(float x) { return __float_as_uint(fabsf(x)); }
+__device__ __forceinline__ unsigned abs_bits(double x) {
+  uint32_t b;
+  return f32_abs_bits(x, b) ? b : __float_as_uint(fabsf((float)x));
 }
 __device__ __forceinline__ float tf32_rne(float x) {
   uint32_t u = __float_as_uint(x);
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(256) k_split_rows(const TI *__restrict__ C, ui
   unsigned mx = 0u;
   if (b < NBp && (hi || t32)) {
     const TI x = b < NB ? C[(v * NA + row) * NB + b] : TI(0);
-    mx = __float_as_uint(fabsf((float)x));
+    mx = abs_bits(x);
     const long long o = (v * NA + row) * NBp + b;
     if (MODE == FORTE_BF16X2)
       split_bf16(x, hi[o], lo[o]);

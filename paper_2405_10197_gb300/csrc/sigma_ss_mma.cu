@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "bf16_split.h"
 #include "forte_internal.h"
 #include "tc_ptx.cuh"
 
@@ -277,6 +278,8 @@ __device__ __forceinline__ uint32_t ssm_bf16_hi(float x, uint16_t &lo) {
   return __bfloat16_as_ushort(h);
 }
 __device__ __forceinline__ uint32_t ssm_bf16_hi(double x, uint16_t &lo) {
+  uint16_t hb;
+  if (bf16_split_bits(x, hb, lo)) return hb;  // integer path; conversions for the rest
   const __nv_bfloat16 h = __double2bfloat16(x);
   lo = __bfloat16_as_ushort(__double2bfloat16(x - (double)__bfloat162float(h)));
   return __bfloat16_as_ushort(h);
