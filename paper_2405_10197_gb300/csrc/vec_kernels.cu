@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_orth_update_p(const T *_
   for (int i = threadIdx.x; i < (k + 1) * VP_WARPS; i += blockDim.x) sw[i] = 0.0;
   __syncthreads();
   const T s = (T)scale;
+  const bool scaled = scale != 1.0;  // FP64 multiplies cost FP64-pipe slots: skip the identity
   const long long nch = (np + VP_CH - 1) / VP_CH;
   for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
     const long long q0 = ch * VP_CH + threadIdx.x;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_orth_update_p(const T *_
       if (q < np) {
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-          tr[e][p] *= s;
+          if (scaled) tr[e][p] *= s;
           nn += tr[e][p] * tr[e][p];
         }
         pk_st(t_out, q, tr[e]);
@@ -645,14 +646,18 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_precond_dot_p(const doub
   last_block_sums(part, 1, out, counter, red);
 }
 
-// y = a x + b y and x = alpha src over packets (grid-stride)
+// y = a x + b y and x = alpha src over packets (grid-stride).  With a or b equal to 1
+// the update is one fused multiply-add per element (the FP64 pipe is the bound of
+// these kernels on this GPU, not HBM).
 __global__ void k_axpby_p(double a, const double *__restrict__ x, double b, double *__restrict__ y, long long np) {
+  const int form = b == 1.0 ? 1 : (a == 1.0 ? 2 : 0);
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (long long)gridDim.x * blockDim.x) {
     double xv[2], yv[2];
     pk_ld(x, q, xv);
     pk_ld((const double *)y, q, yv);
 #pragma unroll
-    for (int p = 0; p < 2; ++p) yv[p] = a * xv[p] + b * yv[p];
+    for (int p = 0; p < 2; ++p)
+      yv[p] = form == 1 ? fma(a, xv[p], yv[p]) : form == 2 ? fma(b, yv[p], xv[p]) : a * xv[p] + b * yv[p];
     pk_st(y, q, yv);
   }
 }
