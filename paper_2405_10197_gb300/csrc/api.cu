@@ -687,6 +687,10 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
       if (res.rn[r] < tol || k >= kmax) continue;
       const double theta = w[r];
       const double bnorm = res.rn[r];
+      // inner stopping rule: the correction equation's residual reduced 50-fold
+      // (measured at CAS(14,14): a tighter inner solve, aimed at reaching tol in one
+      // outer step, took more inner sigmas and the same number of outer ones)
+      const double inner_rtol = 0.02;
       // PCG on P (H~ - theta) P x = -R_r, starting from x = 0
       FORTE_CUDA_TRY(cudaMemsetAsync(px, 0, sizeof(double) * N, st));
       if ((rc = vk_scale(ctx, pr, W + (size_t)r * N, -1.0, N))) return rc;
@@ -711,11 +715,10 @@ static int refine_jd(forte_ctx *ctx, int nroots, double tol, int inner_mode, int
         const double alpha = rz / pAp;
         if ((rc = vk_axpby(ctx, alpha, pp, 1.0, px, N))) return rc;
         if ((rc = vk_axpby(ctx, -alpha, pq, 1.0, pr, N))) return rc;
-        if ((rc = vk_multidot(ctx, pr, 1, N, pr, N, d_s))) return rc;
-        if ((rc = fetch(d_s, 1, h.data()))) return rc;
-        if (sqrt(std::max(0.0, h[0])) < 0.02 * bnorm) break;
+        // preconditioned residual, r . z and |r|^2 in one pass (z unused on exit)
         if ((rc = vk_precond_dot(ctx, pr, pinv, pz, d_s, N))) return rc;
-        if ((rc = fetch(d_s, 1, h.data()))) return rc;
+        if ((rc = fetch(d_s, 2, h.data()))) return rc;
+        if (sqrt(std::max(0.0, h[1])) < inner_rtol * bnorm) break;
         const double rz_new = h[0];
         if ((rc = project(pz, nroots))) return rc;
         const double beta = rz_new / rz;

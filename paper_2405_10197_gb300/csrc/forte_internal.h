@@ -285,7 +285,7 @@ int vk_scale(forte_ctx *ctx, float *x, const float *src, double alpha, long long
 int vk_convert(forte_ctx *ctx, const double *x, float *y, long long n);
 int vk_convert(forte_ctx *ctx, const float *x, double *y, long long n);
 int vk_axpby(forte_ctx *ctx, double a, const double *x, double b, double *y, long long n);
-// rinv = 1 / max(|theta - H_II|, guard); z = r * rinv with dot_out = r . z
+// rinv = 1 / max(|theta - H_II|, guard); z = r * rinv with dot_out = [r . z, r . r]
 int vk_precond_inv(forte_ctx *ctx, double theta, double guard, double *rinv, long long n);
 int vk_precond_dot(forte_ctx *ctx, const double *r, const double *rinv, double *z, double *dot_out, long long n);
 int vk_argmin_k(forte_ctx *ctx, const double *x, long long n, int k, long long *idx_out);

@@ -26,7 +26,7 @@
 // TF32 with round-to-nearest-even before the MMA (kind::tf32, FP32 accumulate).
 //
 // Kernel structure (persistent: one CTA per SM loops over the items (vector, Ia);
-// 16 warps, warp-specialised):
+// 8 + MX_EPI = 24 warps, warp-specialised):
 //   * warps 5-7 (set-up) build A for the next item in the other half of a double
 //     buffer (K-major, 128-byte swizzle) and write out the sigma row of the item
 //     before last from the other half of a double-buffered accumulator row;
@@ -36,9 +36,10 @@
 //   * one thread of warp 4 issues the tcgen05.mma chain of the tile into one of
 //     four 128-column TMEM accumulators and commits to the stage's `empty` and the
 //     accumulator's `tfull` mbarriers;
-//   * warps 8-15 (epilogue) read the accumulator with tcgen05.ld, convert each
-//     valid element to fixed point and add it to the sigma row in shared memory
-//     with integer reductions, then arrive on the accumulator's `tempty` mbarrier.
+//   * warps 8-23 (epilogue, four per TMEM lane quarter) read the accumulator with
+//     tcgen05.ld, convert each valid element to fixed point and add it to the sigma
+//     row in shared memory with integer reductions (positive and negative parts in
+//     separate words), then arrive on the accumulator's `tempty` mbarrier.
 // The rings run across item boundaries, so one item's set-up and drain overlap
 // its neighbours' tiles.
 // Every mbarrier wait is bounded by a clock budget; on expiry the kernel raises the

@@ -229,14 +229,14 @@ __global__ void k_axpby(double a, const double *__restrict__ x, double b, double
     y[j] = a * x[j] + b * y[j];
 }
 
-// z = r * rinv (the inverse of the preconditioner's diagonal); part[block] = r . z
+// z = r * rinv (the inverse of the preconditioner's diagonal); out = [r . z, r . r]
 __global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__restrict__ r, const double *__restrict__ rinv,
                                                             double *__restrict__ z, long long n,
                                                             double *__restrict__ part, double *__restrict__ out,
                                                             unsigned *counter) {
   __shared__ double red[32];
   const long long base = (long long)blockIdx.x * VK_CHUNK + threadIdx.x;
-  double acc = 0.0;
+  double acc = 0.0, rr = 0.0;
 #pragma unroll 4
   for (int e = 0; e < VK_EPT; ++e) {
     long long j = base + (long long)e * VK_THREADS;
@@ -245,10 +245,15 @@ __global__ void __launch_bounds__(VK_THREADS) k_precond_dot(const double *__rest
     const double zv = rv * rinv[j];
     z[j] = zv;
     acc += rv * zv;
+    rr += rv * rv;
   }
   acc = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
-  last_block_sums(part, 1, out, counter, red);
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = acc;
+    part[2 * blockIdx.x + 1] = rr;
+  }
+  last_block_sums(part, 2, out, counter, red);
 }
 
 // rinv = 1 / |theta - hdiag| with the magnitude clamped below at guard: the FP64
@@ -440,6 +445,59 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_multidot_p(const T *__re
   last_block_sums(part, nv, out, counter, red);
 }
 
+// The same for nv <= KMAX: loop over the vectors unrolled, partial sums of the
+// block's chunks in registers, one warp reduction per vector and block.
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_multidot_u(const T *__restrict__ V, int nv, long long ld,
+                                                                   const T *__restrict__ x, long long np,
+                                                                   double *__restrict__ part,
+                                                                   double *__restrict__ out, unsigned *counter) {
+  constexpr int P = Pk<T>::P;
+  __shared__ double red[32];
+  __shared__ double sw[KMAX * VP_WARPS];
+  for (int i = threadIdx.x; i < nv * VP_WARPS; i += blockDim.x) sw[i] = 0.0;
+  __syncthreads();
+  T acc[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) acc[i] = T(0);
+  const long long nch = (np + VP_CH - 1) / VP_CH;
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long q0 = ch * VP_CH + threadIdx.x;
+    T xr[VP_PER][P];
+#pragma unroll
+    for (int e = 0; e < VP_PER; ++e) {
+      const long long q = q0 + (long long)e * VK_THREADS;
+      if (q < np) {
+        pk_ld(x, q, xr[e]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) xr[e][p] = T(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if (i < nv) {
+        const T *v = V + (long long)i * ld;
+#pragma unroll
+        for (int e = 0; e < VP_PER; ++e) {
+          const long long q = q0 + (long long)e * VK_THREADS;
+          if (q < np) {
+            T vv[P];
+            pk_ld(v, q, vv);
+#pragma unroll
+            for (int p = 0; p < P; ++p) acc[i] += vv[p] * xr[e][p];
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i)
+    if (i < nv) warp_add(acc[i], sw + i * VP_WARPS);
+  block_partials(sw, nv, part);
+  last_block_sums(part, nv, out, counter, red);
+}
+
 // t_out = scale (t_in - sum_i c_i B_i); out = [B_i . t_out (i < k, zeros unless DOTS),
 // |t_out|^2].  c == nullptr: no update.  t_in may alias t_out.
 template <typename T, bool DOTS>
@@ -517,6 +575,98 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_orth_update_p(const T *_
         warp_add(a, sw + i * VP_WARPS);
       }
     }
+  }
+  block_partials(sw, k + 1, part);
+  last_block_sums(part, k + 1, out, counter, red);
+}
+
+// The same for k <= KMAX: loops over the basis unrolled, partial sums in registers.
+template <typename T, bool DOTS, int KMAX>
+__global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_orth_update_u(const T *__restrict__ Bm, int k, long long ld,
+                                                                      const double *__restrict__ c, const T *t_in,
+                                                                      T *t_out, long long np, double scale,
+                                                                      double *__restrict__ part,
+                                                                      double *__restrict__ out, unsigned *counter) {
+  constexpr int P = Pk<T>::P;
+  __shared__ double red[32];
+  __shared__ double sw[(KMAX + 1) * VP_WARPS];
+  __shared__ T sc[KMAX];
+  const int ku = c ? k : 0;
+  for (int i = threadIdx.x; i < ku; i += blockDim.x) sc[i] = (T)c[i];
+  for (int i = threadIdx.x; i < (k + 1) * VP_WARPS; i += blockDim.x) sw[i] = 0.0;
+  __syncthreads();
+  const T s = (T)scale;
+  const bool scaled = scale != 1.0;
+  T nn = 0, acc[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) acc[i] = T(0);
+  const long long nch = (np + VP_CH - 1) / VP_CH;
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long q0 = ch * VP_CH + threadIdx.x;
+    T tr[VP_PER][P];
+#pragma unroll
+    for (int e = 0; e < VP_PER; ++e) {
+      const long long q = q0 + (long long)e * VK_THREADS;
+      if (q < np) {
+        pk_ld(t_in, q, tr[e]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) tr[e][p] = T(0);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if (i < ku) {
+        const T *b = Bm + (long long)i * ld;
+        const T ci = sc[i];
+#pragma unroll
+        for (int e = 0; e < VP_PER; ++e) {
+          const long long q = q0 + (long long)e * VK_THREADS;
+          if (q < np) {
+            T bv[P];
+            pk_ld(b, q, bv);
+#pragma unroll
+            for (int p = 0; p < P; ++p) tr[e][p] -= ci * bv[p];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < VP_PER; ++e) {
+      const long long q = q0 + (long long)e * VK_THREADS;
+      if (q < np) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          if (scaled) tr[e][p] *= s;
+          nn += tr[e][p] * tr[e][p];
+        }
+        pk_st(t_out, q, tr[e]);
+      }
+    }
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) {
+        if (i < k) {
+          const T *b = Bm + (long long)i * ld;
+#pragma unroll
+          for (int e = 0; e < VP_PER; ++e) {
+            const long long q = q0 + (long long)e * VK_THREADS;
+            if (q < np) {
+              T bv[P];
+              pk_ld(b, q, bv);
+#pragma unroll
+              for (int p = 0; p < P; ++p) acc[i] += bv[p] * tr[e][p];
+            }
+          }
+        }
+      }
+    }
+  }
+  warp_add(nn, sw + k * VP_WARPS);
+  if (DOTS) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+      if (i < k) warp_add(acc[i], sw + i * VP_WARPS);
   }
   block_partials(sw, k + 1, part);
   last_block_sums(part, k + 1, out, counter, red);
@@ -611,20 +761,120 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_residual_precond_p(
   last_block_sums(part, m, out, counter, red);
 }
 
-// z = r * rinv; out = r . z
+// The same for k <= KMAX with the loops over the basis unrolled (the loads of all k
+// vectors of a chunk can be in flight together) and the partial sums of the block's
+// chunks kept in registers, reduced over the warp once per block.
+template <typename T, bool DOTS, int PER, int KMAX>
+__global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_residual_precond_u(
+    const T *__restrict__ B, const T *__restrict__ S, int k, long long ld, const double *__restrict__ u,
+    double theta, const double *__restrict__ hd, double guard, T *__restrict__ t, long long np,
+    double *__restrict__ part, double *__restrict__ out, unsigned *counter) {
+  constexpr int P = Pk<T>::P;
+  __shared__ double red[32];
+  __shared__ double sw[(KMAX + 2) * VP_WARPS];
+  __shared__ T su[KMAX];
+  const int m = DOTS ? k + 2 : 1;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) su[i] = (T)u[i];
+  for (int i = threadIdx.x; i < m * VP_WARPS; i += blockDim.x) sw[i] = 0.0;
+  __syncthreads();
+  const T th = (T)theta;
+  T rr = 0, tt = 0, acc[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) acc[i] = T(0);
+  const long long nch = (np + (VK_THREADS * PER) - 1) / (VK_THREADS * PER);
+  for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+    const long long q0 = ch * (VK_THREADS * PER) + threadIdx.x;
+    T hx[PER][P], xv[PER][P];
+#pragma unroll
+    for (int e = 0; e < PER; ++e)
+#pragma unroll
+      for (int p = 0; p < P; ++p) hx[e][p] = xv[e][p] = T(0);
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if (i < k) {
+        const T ui = su[i];
+        const T *sp = S + (long long)i * ld, *bp = B + (long long)i * ld;
+#pragma unroll
+        for (int e = 0; e < PER; ++e) {
+          const long long q = q0 + (long long)e * VK_THREADS;
+          if (q < np) {
+            T sv[P], bv[P];
+            pk_ld(sp, q, sv);
+            pk_ld(bp, q, bv);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+              hx[e][p] += ui * sv[p];
+              xv[e][p] += ui * bv[p];
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const long long q = q0 + (long long)e * VK_THREADS;
+      if (q < np) {
+        double h[P];
+        hd_ld<P>(hd, q, h);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+          const T r = hx[e][p] - th * xv[e][p];
+          rr += r * r;
+          double den = theta - h[p];
+          if (fabs(den) < guard) den = (den >= 0.0) ? guard : -guard;
+          hx[e][p] = r / (T)den;  // hx now holds t
+          tt += hx[e][p] * hx[e][p];
+        }
+        pk_st(t, q, hx[e]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) hx[e][p] = T(0);
+      }
+    }
+    if (DOTS) {
+#pragma unroll
+      for (int i = 0; i < KMAX; ++i) {
+        if (i < k) {
+          const T *bp = B + (long long)i * ld;
+#pragma unroll
+          for (int e = 0; e < PER; ++e) {
+            const long long q = q0 + (long long)e * VK_THREADS;
+            if (q < np) {
+              T bv[P];
+              pk_ld(bp, q, bv);
+#pragma unroll
+              for (int p = 0; p < P; ++p) acc[i] += bv[p] * hx[e][p];
+            }
+          }
+        }
+      }
+    }
+  }
+  warp_add(rr, sw);
+  if (DOTS) {
+    warp_add(tt, sw + (k + 1) * VP_WARPS);
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i)
+      if (i < k) warp_add(acc[i], sw + (1 + i) * VP_WARPS);
+  }
+  block_partials(sw, m, part);
+  last_block_sums(part, m, out, counter, red);
+}
+
+// z = r * rinv; out[0] = r . z, out[1] = r . r
 __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_precond_dot_p(const double *__restrict__ r,
                                                                       const double *__restrict__ rinv,
                                                                       double *__restrict__ z, long long np,
                                                                       double *__restrict__ part, double *__restrict__ out,
                                                                       unsigned *counter) {
   __shared__ double red[32];
-  __shared__ double sw[VP_WARPS];
-  if (threadIdx.x < VP_WARPS) sw[threadIdx.x] = 0.0;
+  __shared__ double sw[2 * VP_WARPS];
+  if (threadIdx.x < 2 * VP_WARPS) sw[threadIdx.x] = 0.0;
   __syncthreads();
   const long long nch = (np + VP_CH - 1) / VP_CH;
   for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
     const long long q0 = ch * VP_CH + threadIdx.x;
-    double acc = 0.0;
+    double acc = 0.0, rr = 0.0;
 #pragma unroll
     for (int e = 0; e < VP_PER; ++e) {
       const long long q = q0 + (long long)e * VK_THREADS;
@@ -636,14 +886,16 @@ __global__ void __launch_bounds__(VK_THREADS, VP_BPS) k_precond_dot_p(const doub
         for (int p = 0; p < 2; ++p) {
           zv[p] = rv[p] * iv[p];
           acc += rv[p] * zv[p];
+          rr += rv[p] * rv[p];
         }
         pk_st(z, q, zv);
       }
     }
     warp_add(acc, sw);
+    warp_add(rr, sw + VP_WARPS);
   }
-  block_partials(sw, 1, part);
-  last_block_sums(part, 1, out, counter, red);
+  block_partials(sw, 2, part);
+  last_block_sums(part, 2, out, counter, red);
 }
 
 // y = a x + b y and x = alpha src over packets (grid-stride).  With a or b equal to 1
@@ -722,7 +974,13 @@ static int vk_multidot_t(forte_ctx *ctx, const T *V, int nv, long long ld, const
   int rc = part_buffer(ctx, (size_t)nb * nv, &part, &cnt);
   if (rc) return rc;
   FORTE_PROF(ctx, "multidot");
-  if (pk)
+  if (pk && nv <= 4)
+    k_multidot_u<T, 4><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n / Pk<T>::P, part, out, cnt);
+  else if (pk && nv <= 8)
+    k_multidot_u<T, 8><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n / Pk<T>::P, part, out, cnt);
+  else if (pk && nv <= 16)
+    k_multidot_u<T, 16><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n / Pk<T>::P, part, out, cnt);
+  else if (pk)
     k_multidot_p<T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n / Pk<T>::P, part, out, cnt);
   else
     k_multidot<T><<<nb, VK_THREADS, 0, ctx->stream>>>(V, nv, ld, x, n, part, out, cnt);
@@ -766,12 +1024,30 @@ static int vk_residual_precond_t(forte_ctx *ctx, const T *B, const T *S, int k, 
   int rc = part_buffer(ctx, (size_t)nb * m, &part, &cnt);
   if (rc) return rc;
   FORTE_PROF(ctx, "residual_precond");
-  if (pk && dots)
-    k_residual_precond_p<T, true, 2><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t,
-                                                                      n / Pk<T>::P, part, dots, cnt);
+  const long long npk = n / Pk<T>::P;
+  const double *hd = ctx->d_hdiag;
+#define FORTE_RESID_U(KM)                                                                                            \
+  do {                                                                                                               \
+    if (dots)                                                                                                        \
+      k_residual_precond_u<T, true, 2, KM><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, hd, guard, t,  \
+                                                                               npk, part, dots, cnt);                \
+    else                                                                                                             \
+      k_residual_precond_u<T, false, 2, KM><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, hd, guard, t, \
+                                                                                npk, part, rnorm2, cnt);             \
+  } while (0)
+  if (pk && k <= 4)
+    FORTE_RESID_U(4);
+  else if (pk && k <= 8)
+    FORTE_RESID_U(8);
+  else if (pk && k <= 16 && sizeof(T) == 4)  // FP64 accumulators for 16 vectors would spill
+    FORTE_RESID_U(16);
+#undef FORTE_RESID_U
+  else if (pk && dots)
+    k_residual_precond_p<T, true, 2><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, hd, guard, t, npk,
+                                                                         part, dots, cnt);
   else if (pk)
-    k_residual_precond_p<T, false, 2><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard,
-                                                                       t, n / Pk<T>::P, part, rnorm2, cnt);
+    k_residual_precond_p<T, false, 2><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, hd, guard, t, npk,
+                                                                          part, rnorm2, cnt);
   else
     k_residual_precond<T><<<nb, VK_THREADS, 0, ctx->stream>>>(B, S, k, ld, u, theta, ctx->d_hdiag, guard, t, n,
                                                               part, rnorm2, cnt);
@@ -807,7 +1083,24 @@ static int vk_orth_update_t(forte_ctx *ctx, const T *B, int k, long long ld, con
     return vk_rescale_dots(ctx, dots_out, k, scale);
   }
   FORTE_PROF(ctx, "orth_update");
-  if (pk && dots)
+  const long long npk = n / Pk<T>::P;
+#define FORTE_ORTH_U(KM)                                                                                    \
+  do {                                                                                                      \
+    if (dots)                                                                                               \
+      k_orth_update_u<T, true, KM><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, npk, scale, \
+                                                                       part, dots_out, cnt);                \
+    else                                                                                                    \
+      k_orth_update_u<T, false, KM><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, npk,      \
+                                                                        scale, part, dots_out, cnt);        \
+  } while (0)
+  if (pk && k <= 4)
+    FORTE_ORTH_U(4);
+  else if (pk && k <= 8)
+    FORTE_ORTH_U(8);
+  else if (pk && k <= 16 && sizeof(T) == 4)
+    FORTE_ORTH_U(16);
+#undef FORTE_ORTH_U
+  else if (pk && dots)
     k_orth_update_p<T, true><<<nb, VK_THREADS, 0, ctx->stream>>>(B, k, ld, c, t_in, t_out, n / Pk<T>::P, scale,
                                                                  part, dots_out, cnt);
   else if (pk)
@@ -907,7 +1200,7 @@ int vk_precond_dot(forte_ctx *ctx, const double *r, const double *rinv, double *
   const unsigned nb = pk ? vp_grid(ctx, n / 2) : vk_blocks(n);
   double *part;
   unsigned *cnt;
-  int rc = part_buffer(ctx, nb, &part, &cnt);
+  int rc = part_buffer(ctx, (size_t)2 * nb, &part, &cnt);
   if (rc) return rc;
   FORTE_PROF(ctx, "precond_dot");
   if (pk)
