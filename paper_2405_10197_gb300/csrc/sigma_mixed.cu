@@ -149,26 +149,30 @@ __global__ void __launch_bounds__(256) k_split_rows(const TI *__restrict__ C, ui
                                                     uint16_t *__restrict__ phi, uint16_t *__restrict__ plo,
                                                     float *__restrict__ pt32) {
   __shared__ unsigned red[8];
-  const long long v = blockIdx.z, row = blockIdx.y;
-  const long long b = (long long)blockIdx.x * 256 + threadIdx.x;
+  // grid-stride over (row, 256-column block) pairs; one atomic per block at the end
+  const long long v = blockIdx.z;
+  const long long nbx = (std::max(NBp, strOf ? NBpos : 0LL) + 255) / 256;
   unsigned mx = 0u;
-  if (b < NBp && (hi || t32)) {
-    const TI x = b < NB ? C[(v * NA + row) * NB + b] : TI(0);
-    mx = abs_bits(x);
-    const long long o = (v * NA + row) * NBp + b;
-    if (MODE == FORTE_BF16X2)
-      split_bf16(x, hi[o], lo[o]);
-    else
-      t32[o] = tf32_rne(x);
-  }
-  if (strOf && b < NBpos) {
-    const int J = strOf[b];
-    const TI x = J >= 0 ? C[(v * NA + row) * NB + J] : TI(0);
-    const long long o = (v * NA + row) * NBpos + b;
-    if (MODE == FORTE_BF16X2)
-      split_bf16(x, phi[o], plo[o]);
-    else
-      pt32[o] = tf32_rne(x);
+  for (long long w = blockIdx.x; w < NA * nbx; w += gridDim.x) {
+    const long long row = w / nbx, b = (w % nbx) * 256 + threadIdx.x;
+    if (b < NBp && (hi || t32)) {
+      const TI x = b < NB ? C[(v * NA + row) * NB + b] : TI(0);
+      mx = max(mx, abs_bits(x));
+      const long long o = (v * NA + row) * NBp + b;
+      if (MODE == FORTE_BF16X2)
+        split_bf16(x, hi[o], lo[o]);
+      else
+        t32[o] = tf32_rne(x);
+    }
+    if (strOf && b < NBpos) {
+      const int J = strOf[b];
+      const TI x = J >= 0 ? C[(v * NA + row) * NB + J] : TI(0);
+      const long long o = (v * NA + row) * NBpos + b;
+      if (MODE == FORTE_BF16X2)
+        split_bf16(x, phi[o], plo[o]);
+      else
+        pt32[o] = tf32_rne(x);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -913,7 +917,7 @@ static int sigma_mixed_t(forte_ctx *ctx, const T *C, T *S, int nvec, int mode) {
     dim3 grid((unsigned)std::min<long long>((per + 255) / 256, 152LL * 16), (unsigned)nvec);
     FORTE_PROF(ctx, "split");
     const long long wcols = std::max(NBp, ab ? NBpos : 0LL);
-    dim3 g2((unsigned)((wcols + 255) / 256), (unsigned)NA, (unsigned)nvec);
+    dim3 g2((unsigned)std::min<long long>(NA * ((wcols + 255) / 256), 152LL * 8), 1u, (unsigned)nvec);
     if (!C32w) {  // no FP32 copy wanted: the row kernel writes both copies
       if (mode == FORTE_BF16X2)
         k_split_rows<FORTE_BF16X2, T><<<g2, 256, 0, st>>>(C, Chi, Clo, nullptr, NA, NB, NBp, cmax, strOf, NBpos, Phi,
