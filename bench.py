@@ -245,6 +245,20 @@ SOLVERS = {
 }
 
 
+def combine_ranks(t_ms, units, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks processed over the
+    slowest rank's time.  Returns (max time in ms, summed units, units per second)."""
+    if dist is None:
+        return t_ms, units, units / (t_ms / 1000.0)
+    import torch
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    t, u = float(tt.item()), float(uu.item())
+    return t, u, u / (t / 1000.0)
+
+
 def run_ours(args):
     import torch
     import paper_2405_10197_gb300 as fg
@@ -349,11 +363,7 @@ def run_ours(args):
     n_sig64, n_sigm = s1[0] - s0[0], s1[1] - s0[1]
     prof = fg.profile_table(prob.ctx)
     launches = sum(v[0] for v in prof.values())
-    if dist:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = nd * (n_sig64 + n_sigm) * world / (t_ms / 1000.0)
+    t_ms, _, value = combine_ranks(t_ms, nd * (n_sig64 + n_sigm), dist, "cuda")
 
     # rooflines
     traffic = traffic_table()
@@ -457,7 +467,8 @@ def run_ours(args):
             fg.forte_destroy(ctx)
             e2e_t.append(time.perf_counter() - t0)
             e2e_units += nd * (c[0] + c[1])
-        out["e2e"] = {"value": e2e_units * world / sum(e2e_t), "unit": "det/s",
+        _, _, e2e_value = combine_ranks(1000.0 * sum(e2e_t), e2e_units, dist, "cuda")
+        out["e2e"] = {"value": e2e_value, "unit": "det/s",
                       "h2d_bytes_per_step": 8 * (n * n + n ** 4),
                       "d2h_bytes_per_step": 8 * (nroots + n * n + n ** 4),
                       "s_per_step": _sig(sum(e2e_t) / len(e2e_t))}
@@ -923,7 +934,7 @@ def fg_nnz(prob):
     return prob.na * per_row(prob.nalpha), prob.nb * per_row(prob.nbeta)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -953,9 +964,14 @@ def main():
                     help="measure the determinant-list (selected-CI) sigma on reference-grown lists")
     ap.add_argument("--kernel-case", choices=["sigma", "rdm"], default=None,
                     help="profiling helper: run one sigma (or RDM) call twice on the workload and exit")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.steps < 1:
         ap.error("--steps must be >= 1")
+    return args
+
+
+def main():
+    args = parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
     if args.batch > 0:
