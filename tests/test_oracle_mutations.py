@@ -57,6 +57,13 @@ MUTATIONS = {
         ("    d[i] = ora_hij(n, h, eri, I, I);", "    d[(i % sp.Nb) * sp.Na + i / sp.Nb] = ora_hij(n, h, eri, I, I);"),
     "model space without the reference determinants":
         ("        M = ~excl\n", "        M = ~excl & ~P\n", "aci.py"),
+    "first-order space of a list without the mixed alpha-beta doubles":
+        ("    for x in a1:\n        for y in b1:\n            out.add(x | (y << norb))\n", "", "aci_list.py"),
+    "list coupling to the reference determinants without their coefficients":
+        ("    x[len(F):] = cP\n", "    x[len(F):] = 1.0\n", "aci_list.py"),
+    "list exclusion by the signed estimate":
+        ("excl = aci_excluded(_mirror_max(np.abs(eps), F, norb, pair), sigma)",
+         "excl = aci_excluded(_mirror_max(eps, F, norb, pair), sigma)", "aci_list.py"),
 }
 
 
@@ -68,7 +75,10 @@ PIN_FILTER = {
     "gas.py": "gas",
     "spin.py": "spin",
     "aci.py": "aci",
+    "aci_list.py": "",
 }
+# the pin file of each mutated file (test_oracle_pins.py unless named here)
+PIN_FILE = {"aci_list.py": "test_oracle_aci_list.py"}
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
@@ -83,9 +93,10 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     (tmp_path / "oracle" / fname).write_text(src.replace(old, new))
     shutil.copy(os.path.join(ROOT, "synth_inputs.py"), tmp_path)
     os.makedirs(tmp_path / "tests")
-    for f in ("conftest.py", "fock_ref.py", "test_oracle_pins.py"):
+    pins = PIN_FILE.get(fname, "test_oracle_pins.py")
+    for f in ("conftest.py", "fock_ref.py", pins):
         shutil.copy(os.path.join(ROOT, "tests", f), tmp_path / "tests")
-    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        "-k", PIN_FILTER[fname], "tests/test_oracle_pins.py"], cwd=tmp_path,
-                       capture_output=True, text=True, timeout=600)
+    sel = ["-k", PIN_FILTER[fname]] if PIN_FILTER[fname] else []
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider"] + sel +
+                       ["tests/" + pins], cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"planted mistake not caught: {name}\n{r.stdout[-2000:]}"
