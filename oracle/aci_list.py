@@ -20,7 +20,12 @@ Readings (beyond those listed in aci.py, which apply unchanged):
   (both are always in the same space: F and M are closed under the exchange);
 * on a CAS grid this is the grid version whenever E_P lies at or below every
   diagonal element H_mumu of the determinants outside F(P) (their eps is then 0 and
-  the grid version excludes them); the tests compare the two there.
+  the grid version excludes them); the tests compare the two there;
+* optional exchange-parity sector (n_alpha = n_beta; +1: even S, -1: odd S): the P
+  and M solves take the lowest state with c(mirror(D)) = parity c(D), in the basis
+  (|D> + parity |mirror(D)>)/sqrt(2) of mirror pairs and |D> for a determinant that is
+  its own mirror (even sector only); the start determinants must be able to carry
+  weight there (for -1, alpha string != beta string).
 """
 from __future__ import annotations
 
@@ -80,6 +85,33 @@ def hmat_list(norb, dets, h, eri):
     return sci_sigma(norb, np.asarray(dets, dtype=np.uint64), h, eri, np.eye(m))
 
 
+def _lowest(norb, dets, h, eri, parity):
+    """Lowest eigenpair of H over the list (in the exchange-parity sector when parity != 0);
+    the vector over the list."""
+    H = hmat_list(norb, dets, h, eri)
+    if parity == 0:
+        w, U = np.linalg.eigh(H)
+        return w[0], U[:, 0]
+    pos = {d: i for i, d in enumerate(dets)}
+    rows = []
+    for i, d in enumerate(dets):
+        j = pos[mirror(norb, d)]
+        if j < i:
+            continue
+        v = np.zeros(len(dets))
+        if j == i:
+            if parity < 0:
+                continue
+            v[i] = 1.0
+        else:
+            v[i] = 1.0 / np.sqrt(2.0)
+            v[j] = parity / np.sqrt(2.0)
+        rows.append(v)
+    Q = np.array(rows)
+    w, U = np.linalg.eigh(Q @ H @ Q.T)
+    return w[0], U[:, 0] @ Q
+
+
 def _mirror_max(vals, dets, norb, pair):
     if not pair:
         return vals
@@ -92,12 +124,14 @@ def _mirror_max(vals, dets, norb, pair):
     return out
 
 
-def aci_list(norb, nalpha, nbeta, h, eri, start, sigma, gamma=1.0, max_iter=50):
+def aci_list(norb, nalpha, nbeta, h, eri, start, sigma, gamma=1.0, max_iter=50, parity=0):
     """ACI from the start determinants `start` (words).  Returns dict(E=E_M,
     E_corrected=E_M + sum of the excluded eps, M=sorted words of the model space,
     P=sorted words of the last reference space, C=Psi_M over M, cycles)."""
     if not 1 <= norb <= 32:
         raise ValueError("determinant words hold at most 32 orbitals")
+    if parity and nalpha != nbeta:
+        raise ValueError("an exchange-parity sector needs n_alpha == n_beta")
     pair = nalpha == nbeta
     P = sorted(set(int(d) for d in start) | ({mirror(norb, int(d)) for d in start} if pair else set()))
     for d in P:
@@ -105,9 +139,7 @@ def aci_list(norb, nalpha, nbeta, h, eri, start, sigma, gamma=1.0, max_iter=50):
             raise ValueError("a start determinant is outside the (n_alpha, n_beta) sector")
     seen = []
     for cycle in range(1, max_iter + 1):
-        HP = hmat_list(norb, P, h, eri)
-        w, U = np.linalg.eigh(HP)
-        E_P, cP = w[0], U[:, 0]
+        E_P, cP = _lowest(norb, P, h, eri, parity)
         Pset = set(P)
         F = sorted(set().union(*(connected(norb, d) for d in P)) - Pset)
         # V_mu = <mu|H|Psi_P>: the list sigma over F + P of the vector (0 on F, c_P on P)
@@ -119,9 +151,8 @@ def aci_list(norb, nalpha, nbeta, h, eri, start, sigma, gamma=1.0, max_iter=50):
         eps = aci_epsilon(E_P, Hmm, V)
         excl = aci_excluded(_mirror_max(np.abs(eps), F, norb, pair), sigma)
         M = sorted(Pset | {d for d, e in zip(F, excl) if not e})
-        HM = hmat_list(norb, M, h, eri)
-        wM, UM = np.linalg.eigh(HM)
-        E_M, C = wM[0], _fix_sign(UM[:, 0])
+        E_M, C = _lowest(norb, M, h, eri, parity)
+        C = _fix_sign(C)
         keep = aci_reference(_mirror_max(C * C, M, norb, pair), gamma * sigma)
         newP = [d for d, k in zip(M, keep) if k]
         key = tuple(newP)

@@ -98,3 +98,32 @@ def test_beyond_a_small_grid_the_model_energy_is_variational_and_tracks_sigma():
         assert len(r["M"]) < math.comb(norb, na) * math.comb(norb, nb)
         errs.append(r["E"] - w[0])
     assert errs[1] < errs[0]
+
+
+def _grid_start_word_sector(norb, na, h, eri, parity):
+    # the grid version's start: lowest H_II, for the odd sector among alpha != beta
+    d = oracle.hdiag(norb, na, na, h, eri)
+    A = oracle.strings(norb, na)
+    N = len(A)
+    if parity < 0:
+        d = d.copy()
+        d[np.arange(N) * (N + 1)] = np.inf
+    i = int(np.argmin(d))
+    return int(A[i // N]) | (int(A[i % N]) << norb)
+
+
+@pytest.mark.parametrize("parity,sigma", [(1, 1e-3), (-1, 1e-3), (1, 0.0)])
+def test_list_aci_in_a_parity_sector_is_the_grid_aci(parity, sigma):
+    norb, na = 6, 3
+    h, eri = si.integrals(norb, 2 * norb, seed=1)
+    g = oracle.aci(norb, na, na, h, eri, sigma, parity=parity)
+    r = al.aci_list(norb, na, na, h, eri, [_grid_start_word_sector(norb, na, h, eri, parity)], sigma,
+                    parity=parity)
+    assert r["cycles"] == g["cycles"]
+    assert r["M"] == _grid_words(norb, na, na, g["M"])
+    assert abs(r["E"] - g["E"]) < 1e-11
+    if sigma == 0.0:
+        w = np.linalg.eigvalsh(oracle.hmat_dense(norb, na, na, h, eri))
+        Q = oracle.sector_basis(len(oracle.strings(norb, na)), parity)
+        ws = np.linalg.eigvalsh(Q @ oracle.hmat_dense(norb, na, na, h, eri) @ Q.T)
+        assert abs(r["E"] - ws[0]) < 1e-10 and r["E"] >= w[0] - 1e-12

@@ -61,6 +61,8 @@ MUTATIONS = {
         ("    for x in a1:\n        for y in b1:\n            out.add(x | (y << norb))\n", "", "aci_list.py"),
     "list coupling to the reference determinants without their coefficients":
         ("    x[len(F):] = cP\n", "    x[len(F):] = 1.0\n", "aci_list.py"),
+    "list parity sector with the opposite exchange sign":
+        ("            v[j] = parity / np.sqrt(2.0)\n", "            v[j] = -parity / np.sqrt(2.0)\n", "aci_list.py"),
     "list exclusion by the signed estimate":
         ("excl = aci_excluded(_mirror_max(np.abs(eps), F, norb, pair), sigma)",
          "excl = aci_excluded(_mirror_max(eps, F, norb, pair), sigma)", "aci_list.py"),
