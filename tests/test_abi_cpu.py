@@ -90,3 +90,51 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(fg, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         fg.library()
+
+
+def _prototypes():
+    """name -> (return type text, [parameter type texts]) from the header."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \t\*]*?)\b(forte_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text):
+        ps = [p.strip() for p in params.split(",") if p.strip()]
+        if ps == ["void"]:
+            ps = []
+        # drop the parameter name, keep the type
+        types = [re.sub(r"\b\w+$", "", p).strip() if not p.endswith("*") else p for p in ps]
+        out[name] = (ret.strip(), types)
+    return out
+
+
+def _ctype_kind(c):
+    if c in (ctypes.c_void_p, ctypes.c_char_p):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_double: "double", ctypes.c_longlong: "long long",
+            ctypes.c_ulonglong: "unsigned long long"}[c]
+
+
+def _decl_kind(t):
+    if "*" in t:
+        return "ptr"
+    t = t.replace("const", "").strip()
+    return t
+
+
+def test_binding_signatures_match_the_header(lib):
+    # a ctypes argument list that disagrees with the C prototype passes garbage silently
+    protos = _prototypes()
+    assert len(protos) >= len(declared_functions()) - 1
+    for name, (ret, params) in protos.items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, f"{name}: binding sets no argtypes"
+        got = [_ctype_kind(a) for a in f.argtypes]
+        want = [_decl_kind(p) for p in params]
+        assert got == want, f"{name}: binding {got} vs header {want}"
+        if "*" in ret:
+            assert f.restype in (ctypes.c_void_p, ctypes.c_char_p), name
+        elif ret.endswith("void"):
+            assert f.restype is None, name
+        else:
+            assert f.restype is ctypes.c_int, name
