@@ -88,37 +88,55 @@ enum {
  * The inputs are copied; the caller keeps ownership.  Returns NULL on error
  * (bad sizes, NULL pointers, NaN/Inf, integrals not symmetric to 1e-12,
  * allocation or CUDA failure); forte_last_error() tells why.  The context
- * uses the current CUDA device at the time of the call. */
+ * uses the current CUDA device at the time of the call.
+ * Paper: Eq. 1 (the Hamiltonian) and Sec. II.A.1 (alpha and beta strings, their
+ * addressing and single-replacement lists).
+ */
 forte_ctx *forte_cas_create(int norb, int nalpha, int nbeta, const double *h, const double *eri);
 
-/* Release every device and host resource of the context (NULL is a no-op). */
+/* Release every device and host resource of the context (NULL is a no-op).
+ * Control entry point: the paper has no counterpart.
+ */
 void forte_destroy(forte_ctx *ctx);
 
-/* Thread-local description of the last error ("" when none). */
+/* Thread-local description of the last error ("" when none).
+ * Control entry point: the paper has no counterpart.
+ */
 const char *forte_last_error(void);
 
 /* Queue subsequent work on this CUDA stream (a cudaStream_t; NULL = legacy
- * default stream). */
+ * default stream).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_set_stream(forte_ctx *ctx, void *cuda_stream);
 
 /* Select FORTE_FP64, FORTE_TF32, FORTE_BF16X2, FORTE_DF32 or FORTE_OZ64 for forte_sigma,
  * forte_davidson and forte_rdms (every mode but FORTE_FP64 forms the 2-RDM with
- * the tensor-core Gram).  Default FORTE_FP64.  FORTE_ERR_ARG for other values. */
+ * the tensor-core Gram).  Default FORTE_FP64.  FORTE_ERR_ARG for other values.
+ * The paper computes in FP64 (FORTE_FP64); the other modes extend it and have no
+ * counterpart there.
+ */
 int forte_set_precision(forte_ctx *ctx, int mode);
 
-/* N_alpha = C(n, nalpha), N_beta = C(n, nbeta) (host outputs, either may be NULL). */
+/* N_alpha = C(n, nalpha), N_beta = C(n, nbeta) (host outputs, either may be NULL).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_get_sizes(const forte_ctx *ctx, long long *n_alpha_str, long long *n_beta_str);
 
 /* Dense single-replacement table of one spin (0 = alpha, 1 = beta), host outputs:
  *   strings [N]        occupation masks, ascending (address = index)
  *   J       [N][n][n]  address of E_pq|I> (a+_p a_q on string I), -1 if it vanishes
  *   sgn     [N][n][n]  its phase (+1/-1), 0 if it vanishes
- * Any output may be NULL.  Phase: (-1)^(occupied orbitals strictly between p and q). */
+ * Any output may be NULL.  Phase: (-1)^(occupied orbitals strictly between p and q).
+ * Paper: Sec. II.A.1 (string lists and single-replacement lists).
+ */
 int forte_get_string_tables(const forte_ctx *ctx, int spin, unsigned *strings, int *J,
                             signed char *sgn);
 
 /* Determinant diagonal <I|H|I>, device output [N_alpha][N_beta]; +inf at the
- * determinants an occupation restriction (forte_set_gas) excludes. */
+ * determinants an occupation restriction (forte_set_gas) excludes.
+ * Paper: Sec. II.A.1 (the diagonal of H, the Davidson-Liu preconditioner).
+ */
 int forte_get_hdiag(const forte_ctx *ctx, double *hdiag);
 
 /* Occupation-restricted CI (GAS; RAS as its three-space case), Sec. II.A.1:
@@ -149,13 +167,17 @@ int forte_set_gas(forte_ctx *ctx, int nspace, const int *size, const int *gmin, 
 /* Route of the restricted sigma (see forte_set_gas): -1 timed choice (default),
  * 0 full-grid kernels + projection, 1 the kept-determinant kernel (for any
  * restriction with at most 64 beta occupation classes; otherwise the full grid).
- * Clears earlier timings.  FORTE_ERR_ARG for other values. */
+ * Clears earlier timings.  FORTE_ERR_ARG for other values.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_set_gas_route(forte_ctx *ctx, int route);
 
 /* Route the restricted sigma takes for FP64 and FP32 vectors (host outputs, may
  * be NULL): -1 no restriction or not yet timed, 0 full grid, 1 kept
  * determinants; ms (host [4], may be NULL): the timings of the choice, FP64 full
- * grid, FP64 kept, FP32 full grid, FP32 kept (0 when not timed). */
+ * grid, FP64 kept, FP32 full grid, FP32 kept (0 when not timed).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_get_gas_route(const forte_ctx *ctx, int *route_fp64, int *route_fp32, double *ms);
 
 /* Spin-parity sector of the Davidson solve (Sec. II.A.1: projection on states
@@ -229,23 +251,31 @@ int forte_sigma(forte_ctx *ctx, const double *C, double *S, int nvec);
  * residuals and energies are refined with FP64-class sigma builds
  * (Jacobi-Davidson whose inner solves use the mode's sigma) until the FP64
  * residual meets tol.  Results stay in the context (forte_get_roots).
- * Returns FORTE_ERR_NOT_CONVERGED when max_iter is reached (results kept). */
+ * Returns FORTE_ERR_NOT_CONVERGED when max_iter is reached (results kept).
+ * Paper: Sec. II.A.1 (Davidson-Liu).
+ */
 int forte_davidson(forte_ctx *ctx, int nroots, double tol);
 
 /* Davidson controls: subspace size and collapse size per root, iteration cap
- * and preconditioner guard.  Defaults 12, 2, 200, 1e-8. */
+ * and preconditioner guard.  Defaults 12, 2, 200, 1e-8.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_set_davidson_params(forte_ctx *ctx, int max_subspace_per_root, int collapse_per_root,
                               int max_iter, double denom_guard);
 
 /* Results of the last forte_davidson: energies (host [nroots], may be NULL),
  * eigenvectors (device [nroots][N_alpha][N_beta], may be NULL; normalised,
  * largest-|c| component positive), final FP64 residual norms (host
- * [nroots], may be NULL) and the iteration count (host, may be NULL). */
+ * [nroots], may be NULL) and the iteration count (host, may be NULL).
+ * Paper: Sec. II.A.1 (Davidson-Liu results).
+ */
 int forte_get_roots(const forte_ctx *ctx, double *E, double *C, double *rnorm, int *iters);
 
 /* Restart: use the nvec device vectors [nvec][N_alpha][N_beta] as the initial
  * Davidson subspace of the next forte_davidson call (copied; orthonormalised
- * there).  nvec = 0 restores the unit-vector guess. */
+ * there).  nvec = 0 restores the unit-vector guess.
+ * Paper: Sec. II.A.1 (Davidson-Liu guess vectors).
+ */
 int forte_set_guess(forte_ctx *ctx, const double *C, int nvec);
 
 /* Spin-free RDMs of one normalised state C (device [N_alpha][N_beta]):
@@ -341,13 +371,17 @@ int forte_batch_solve(int nprob, const int *norb, const int *nalpha, const int *
  * build of the class's first problems (one CTA each) with the chosen candidate,
  * the chosen path (0: class launch, 1: single-problem path), the measured time
  * (ms) of one single-problem-path Davidson iteration, the class's problem count
- * and the resident CTAs per SM of its launch. */
+ * and the resident CTAs per SM of its launch.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_batch_tuning(int max_classes, int *nclass, int *norb, int *nalpha, int *nbeta, int *threads, int *tile,
                        double *sigma_ms, int *path, double *single_iter_ms, int *problems, int *ctas_per_sm);
 
 /* Problem counts of the last forte_batch_solve (host outputs, may be NULL): solved
  * in class launches, sent to the single-problem path, and solved again on the
- * single-problem path after their in-CTA Davidson-Liu did not converge. */
+ * single-problem path after their in-CTA Davidson-Liu did not converge.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_batch_stats(int *class_launch, int *single_path, int *retried);
 
 /* FP64 sigma = H C that allocates no device memory (the paper has no
@@ -386,25 +420,35 @@ int forte_get_status(forte_ctx *ctx);
 /* Clock budget (cycles) of one pipeline wait of the context's tensor-core kernels;
  * 0 restores the default (4e9 cycles, about two seconds).  Meant for tests of the
  * failure path: a budget of a few cycles makes the waits expire.  Synchronises the
- * context stream. */
+ * context stream.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_set_wait_budget(forte_ctx *ctx, unsigned long long cycles);
 
 /* Kernel tracing.  While enabled, every kernel this library launches for the
  * context is bracketed by CUDA events on the context stream (on = 1 also
- * clears earlier records; on = 0 stops recording and keeps them). */
+ * clears earlier records; on = 0 stops recording and keeps them).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_profile_enable(forte_ctx *ctx, int on);
 
 /* Launch count and summed device time (ms) of the recorded launches whose
  * kernel name equals `kernel` (NULL: all kernels).  Synchronises the stream.
- * Host outputs; either may be NULL. */
+ * Host outputs; either may be NULL.
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_profile_query(forte_ctx *ctx, const char *kernel, int *launches, double *total_ms);
 
 /* Name of the i-th distinct recorded kernel (NULL when i is out of range);
- * the string lives as long as the library. */
+ * the string lives as long as the library.
+ * Control entry point: the paper has no counterpart.
+ */
 const char *forte_profile_kernel_name(forte_ctx *ctx, int i);
 
 /* Number of vectors pushed through the sigma build since the context was
- * created, in FP64 and in a reduced-precision mode (host outputs, may be NULL). */
+ * created, in FP64 and in a reduced-precision mode (host outputs, may be NULL).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_get_counters(const forte_ctx *ctx, long long *sigma_vectors_fp64,
                        long long *sigma_vectors_mixed);
 
@@ -417,8 +461,13 @@ int forte_get_counters(const forte_ctx *ctx, long long *sigma_vectors_fp64,
  * NULL (reason in forte_last_error) for a bad norb, NULL or non-finite integrals,
  * or a failed device allocation.  Release with forte_sci_destroy. */
 forte_sci *forte_sci_create(int norb, const double *h, const double *eri);
+/* Frees the list context and its device memory (NULL is accepted).
+ * Control entry point: the paper has no counterpart.
+ */
 void forte_sci_destroy(forte_sci *sci);
-/* Stream of the handle's work (default: the legacy default stream). */
+/* Stream of the handle's work (default: the legacy default stream).
+ * Control entry point: the paper has no counterpart.
+ */
 int forte_sci_set_stream(forte_sci *sci, void *cuda_stream);
 
 /* S[v][i] = sum_j <D_i|H|D_j> C[v][j] over a list of determinants (H of Eq. 1;
